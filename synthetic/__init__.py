@@ -1,0 +1,219 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds only input generators: surface meshes of the workload
+shapes, seeded random vectors and the material presets.  It contains none of
+the boundary element method's arithmetic (no kernels, no quadrature, no
+frequencies, no compression), so both the CPU oracle and the CUDA path may
+take their inputs from here without sharing any computation.
+
+Meshes are returned as ``(xyz, tri)``: ``xyz`` float64 (n_nodes, 3), ``tri``
+int32 (n_tris, 3), every triangle oriented counter-clockwise when seen from
+outside the solid (outward normal by the right-hand rule).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "STEEL", "PAPER_CUBE_MATERIAL", "lame_from_young",
+    "cube_grid", "paper_cube", "refine", "icosphere", "ellipsoid",
+    "splitmix64", "uniform01", "normal", "complex_normal",
+]
+
+
+# --------------------------------------------------------------------------
+# materials
+# --------------------------------------------------------------------------
+
+def lame_from_young(E: float, nu: float) -> tuple[float, float]:
+    """Lame constants (lambda, mu) from Young's modulus and Poisson's ratio."""
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    return lam, mu
+
+
+_steel_lam, _steel_mu = lame_from_young(210e9, 0.3)
+#: steel, rho = 7850 kg/m^3, E = 210 GPa, nu = 0.3 -> (rho, lambda, mu)
+STEEL = (7850.0, _steel_lam, _steel_mu)
+#: the paper's unit-cube material c1 = 1, c2 = sqrt(1/2), rho = 1 (Sec. 4.1):
+#: mu = rho c2^2 = 1/2, lambda = rho c1^2 - 2 mu = 0 (nu = 0)
+PAPER_CUBE_MATERIAL = (1.0, 0.0, 0.5)
+
+
+# --------------------------------------------------------------------------
+# meshes
+# --------------------------------------------------------------------------
+
+def _cube_face_frames():
+    # (origin corner, u axis, v axis) with u x v = outward normal, unit cube
+    # [-0.5, 0.5]^3
+    h = 0.5
+    return [
+        (np.array([h, -h, -h]), np.array([0, 1, 0.]), np.array([0, 0, 1.])),   # +x
+        (np.array([-h, -h, -h]), np.array([0, 0, 1.]), np.array([0, 1, 0.])),  # -x
+        (np.array([-h, h, -h]), np.array([0, 0, 1.]), np.array([1, 0, 0.])),   # +y
+        (np.array([-h, -h, -h]), np.array([1, 0, 0.]), np.array([0, 0, 1.])),  # -y
+        (np.array([-h, -h, h]), np.array([1, 0, 0.]), np.array([0, 1, 0.])),   # +z
+        (np.array([-h, -h, -h]), np.array([0, 1, 0.]), np.array([1, 0, 0.])),  # -z
+    ]
+
+
+class _NodeTable:
+    """Merges coincident points (exact rational grid coordinates)."""
+
+    def __init__(self, scale: int):
+        self.scale = scale
+        self.index: dict[tuple[int, int, int], int] = {}
+        self.xyz: list[np.ndarray] = []
+
+    def get(self, p: np.ndarray) -> int:
+        key = tuple(int(round(c * self.scale)) for c in p)
+        idx = self.index.get(key)
+        if idx is None:
+            idx = len(self.xyz)
+            self.index[key] = idx
+            self.xyz.append(np.asarray(p, dtype=np.float64))
+        return idx
+
+
+def cube_grid(n: int, size: float = 1.0) -> tuple[np.ndarray, np.ndarray]:
+    """Surface of the cube [-size/2, size/2]^3, each face an n x n grid of
+    squares, each square cut along its (i, j) -> (i+1, j+1) diagonal into two
+    triangles: 12 n^2 triangles, 6 n^2 + 2 nodes."""
+    nodes = _NodeTable(scale=4 * n)
+    tris = []
+    for origin, u, v in _cube_face_frames():
+        def pt(i, j):
+            return origin + (i / n) * u + (j / n) * v
+        for i in range(n):
+            for j in range(n):
+                a = nodes.get(pt(i, j))
+                b = nodes.get(pt(i + 1, j))
+                c = nodes.get(pt(i + 1, j + 1))
+                d = nodes.get(pt(i, j + 1))
+                tris.append((a, b, c))
+                tris.append((a, c, d))
+    xyz = np.array(nodes.xyz) * size
+    return xyz, np.array(tris, dtype=np.int32)
+
+
+def paper_cube(level: int) -> tuple[np.ndarray, np.ndarray]:
+    """The paper's unit-cube meshes (Sec. 4.1, Table 1): level 1 has 2 x 2
+    squares per face, each cut into four triangles by both diagonals (96
+    triangles, 50 nodes); every further level splits each triangle into four."""
+    nodes = _NodeTable(scale=8)
+    tris = []
+    for origin, u, v in _cube_face_frames():
+        def pt(x, y):
+            return origin + x * u + y * v
+        for i in range(2):
+            for j in range(2):
+                a = nodes.get(pt(i / 2, j / 2))
+                b = nodes.get(pt((i + 1) / 2, j / 2))
+                c = nodes.get(pt((i + 1) / 2, (j + 1) / 2))
+                d = nodes.get(pt(i / 2, (j + 1) / 2))
+                m = nodes.get(pt((i + 0.5) / 2, (j + 0.5) / 2))
+                tris += [(a, b, m), (b, c, m), (c, d, m), (d, a, m)]
+    xyz, tri = np.array(nodes.xyz), np.array(tris, dtype=np.int32)
+    for _ in range(level - 1):
+        xyz, tri = refine(xyz, tri)
+    return xyz, tri
+
+
+def refine(xyz: np.ndarray, tri: np.ndarray, project=None):
+    """Uniform 1 -> 4 split of every triangle at its edge midpoints.
+    ``project`` optionally maps new midpoints (e.g. onto a sphere)."""
+    xyz = [p for p in np.asarray(xyz, dtype=np.float64)]
+    mid: dict[tuple[int, int], int] = {}
+
+    def midpoint(a, b):
+        key = (min(a, b), max(a, b))
+        idx = mid.get(key)
+        if idx is None:
+            p = 0.5 * (xyz[a] + xyz[b])
+            if project is not None:
+                p = project(p)
+            idx = len(xyz)
+            xyz.append(p)
+            mid[key] = idx
+        return idx
+
+    out = []
+    for a, b, c in np.asarray(tri):
+        ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+        out += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]
+    return np.array(xyz), np.array(out, dtype=np.int32)
+
+
+def icosphere(level: int, radius: float = 1.0) -> tuple[np.ndarray, np.ndarray]:
+    """Icosahedron refined ``level`` times with midpoints projected to the
+    sphere: 20 * 4^level triangles, 10 * 4^level + 2 nodes."""
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    v = np.array([
+        [-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0],
+        [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+        [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]], dtype=np.float64)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    f = np.array([
+        [0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11],
+        [1, 5, 9], [5, 11, 4], [11, 10, 2], [10, 7, 6], [7, 1, 8],
+        [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9],
+        [4, 9, 5], [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], dtype=np.int32)
+
+    def project(p):
+        return p / np.linalg.norm(p)
+
+    for _ in range(level):
+        v, f = refine(v, f, project)
+    return v * radius, f
+
+
+def ellipsoid(level: int, axes=(2.0, 1.0, 1.0)) -> tuple[np.ndarray, np.ndarray]:
+    """Icosphere scaled to an ellipsoid with the given semi-axes."""
+    xyz, tri = icosphere(level)
+    return xyz * np.asarray(axes, dtype=np.float64), tri
+
+
+# --------------------------------------------------------------------------
+# seeded random numbers: splitmix64 counter stream -> uniforms -> Box-Muller
+# --------------------------------------------------------------------------
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """First n outputs of the splitmix64 generator started at ``seed``
+    (Steele, Lea, Flood 2014): state += 0x9E3779B97F4A7C15, then the
+    xor-shift-multiply finaliser.  Returned as uint64."""
+    with np.errstate(over="ignore"):
+        k = np.arange(1, n + 1, dtype=np.uint64)
+        z = np.uint64(seed & _M64) + k * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, n: int) -> np.ndarray:
+    """n uniforms in (0, 1): top 53 bits of splitmix64, offset by half a ulp."""
+    z = splitmix64(seed, n)
+    return ((z >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, n: int) -> np.ndarray:
+    """n standard normal float64 numbers by Box-Muller on uniform01 pairs."""
+    m = (n + 1) // 2
+    u = uniform01(seed, 2 * m)
+    u1, u2 = u[0::2], u[1::2]
+    rad = np.sqrt(-2.0 * np.log(u1))
+    out = np.empty(2 * m)
+    out[0::2] = rad * np.cos(2.0 * np.pi * u2)
+    out[1::2] = rad * np.sin(2.0 * np.pi * u2)
+    return out[:n]
+
+
+def complex_normal(seed: int, shape) -> np.ndarray:
+    """complex128 array, real and imaginary parts iid N(0, 1)."""
+    n = int(np.prod(shape))
+    x = normal(seed, 2 * n)
+    return (x[0::2] + 1j * x[1::2]).reshape(shape)
