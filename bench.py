@@ -1,0 +1,317 @@
+"""Benchmark of the multi-frequency Laplace-domain BEM operator on one B300.
+
+Workload (the sphere configuration): unit sphere, icosphere with 5,120 flat
+triangles (2,562 nodes), steel, K = 64 frequencies of BDF2 CQ with N = 64,
+dt = 2e-5 s; collocation at the nodes (Neumann rows); cluster trees with leaf
+32, admissibility eta = 2; 3D-ACA tolerance 1e-6.  One step = the whole hot
+path for both operators of the Neumann system (single layer V: 2,562 x 5,120
+blocks, double layer C + K: 2,562 x 2,562 blocks): entry generation,
+near-field blocks, batched 3D-ACA, then the batched apply Y_k = C(s_k) X_k to
+seeded N(0, 1) complex vectors of all K frequencies.
+
+Prints one JSON line (see the keys below).  `--impl reference` times the FP64
+CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+
+WORKLOAD = dict(workload="sphere-5120-K64", mesh="icosphere level 4, radius 1 m, 5120 triangles, 2562 nodes",
+                material="steel rho=7850 E=210GPa nu=0.3", N=64, dt=2e-5, K=64, leaf=32, eta=2.0, eps=1e-6,
+                rows="nodes (Neumann)", operators="V (SL) + C+K (DL)")
+METRIC = "3D-ACA tensor entries/s"
+UNIT = "block entries/s"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 3 + i and "Active" in s[3 + i]
+                          and "Not" not in s[3 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_sample(budget_s: float = 15.0):
+    """Entries/s of the oracle's dense assembly: single-layer node rows of the
+    sphere against all 5,120 elements at the first frequencies, row by row
+    until the time budget is spent."""
+    from oracle import bem
+    xyz, tri = syn.icosphere(4)
+    s = bem.freqs_bdf2(WORKLOAD["N"], WORKLOAD["dt"], WORKLOAD["K"])
+    op = bem.Operator(xyz, tri, syn.STEEL, rows=bem.ROWS_NODES, kernel=bem.KERNEL_SL)
+    rng = np.random.default_rng(11)
+    rows = rng.permutation(op.n_rows)
+    cols = np.arange(op.n_cols)
+    t0 = time.perf_counter()
+    n = 0
+    used = 0
+    while time.perf_counter() - t0 < budget_s and used < len(rows):
+        op.block(rows[used:used + 1], cols, s[:4])
+        n += op.n_cols * 4
+        used += 1
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
+    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{used} node rows x 5120 elements x 4 frequencies of V ({n} block entries, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(budget_s=2.0)
+    for _ in range(args.steps):
+        steps.append(cpu_oracle_sample(budget_s=10.0))
+    v = float(np.mean([s["value"] for s in steps]))
+    cb = dict(steps[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2607_15292_b300 as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    xyz, tri = syn.icosphere(4)
+    s = g.freqs_bdf2(WORKLOAD["N"], WORKLOAD["dt"], WORKLOAD["K"])
+    K = len(s)
+
+    def make(precision):
+        ctx = g.Context(eps=WORKLOAD["eps"], leaf=WORKLOAD["leaf"], eta=WORKLOAD["eta"], precision=precision,
+                        device=local)
+        ctx.material(*syn.STEEL)
+        ctx.freqs(s)
+        mesh = ctx.mesh(xyz, tri)
+        return ctx, mesh, mesh.tree(g.BEM_ROWS_NODES, g.BEM_SL), mesh.tree(g.BEM_ROWS_NODES, g.BEM_DL)
+
+    ctx, mesh, tV, tK = make(g.BEM_MIXED)
+    cdt = torch.complex64
+    XV = torch.tensor(syn.complex_normal(1, (K, len(tri), 3)), dtype=cdt, device=dev)
+    XK = torch.tensor(syn.complex_normal(2, (K, len(xyz), 3)), dtype=cdt, device=dev)
+    YV = torch.empty((K, len(xyz), 3), dtype=cdt, device=dev)
+    YK = torch.empty((K, len(xyz), 3), dtype=cdt, device=dev)
+
+    def step():
+        oV = tV.compress(stream)
+        oK = tK.compress(stream)
+        oV.apply(XV, YV, g.BEM_APPLY_BATCHED, stream)
+        oK.apply(XK, YK, g.BEM_APPLY_BATCHED, stream)
+        return oV, oK
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    entries = 0
+    face_ms = 0.0
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            oV, oK = step()
+            sv, sk = oV.stats(), oK.stats()
+            entries += sv.entries_evaluated + sk.entries_evaluated
+            face_ms += sv.t_entries_ms + sk.t_entries_ms
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        e = torch.tensor([float(entries)], device=dev)
+        torch.distributed.all_reduce(e)
+        entries = int(e.item())
+    value = entries / (ms / 1e3)
+
+    # apply throughput (algorithmic bytes / time) on the compressed operators
+    oV, oK = step()
+    torch.cuda.synchronize()
+    reps = 20
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        oV.apply(XV, YV, g.BEM_APPLY_BATCHED, stream)
+        oK.apply(XK, YK, g.BEM_APPLY_BATCHED, stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = a0.elapsed_time(a1) / reps
+    sv, sk = oV.stats(), oK.stats()
+    apply_bytes = sv.apply_bytes + sk.apply_bytes
+    apply_gbs = apply_bytes / (apply_ms / 1e3) / 1e9
+
+    extra = {"apply_gbs": apply_gbs, "apply_ms": apply_ms, "compression_rate_V": sv.compression_rate,
+             "compression_rate_K": sk.compression_rate, "rank_mean_V": sv.rank_mean, "rank_mean_K": sk.rank_mean,
+             "blocks_V": [sv.n_aca, sv.n_dense, sv.n_rank0], "blocks_K": [sk.n_aca, sk.n_dense, sk.n_rank0]}
+
+    # FP64 GPU form: same path in FP64, speedup and error of the mixed apply
+    if not args.no_fp64:
+        ctx64, mesh64, tV64, tK64 = make(g.BEM_FP64)
+        XV64, XK64 = XV.to(torch.complex128), XK.to(torch.complex128)
+        YV64 = torch.empty((K, len(xyz), 3), dtype=torch.complex128, device=dev)
+        YK64 = torch.empty_like(YV64)
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        oV64 = tV64.compress(stream)
+        oK64 = tK64.compress(stream)
+        oV64.apply(XV64, YV64, g.BEM_APPLY_BATCHED, stream)
+        oK64.apply(XK64, YK64, g.BEM_APPLY_BATCHED, stream)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = b0.elapsed_time(b1)
+        e64 = oV64.stats().entries_evaluated + oK64.stats().entries_evaluated
+        oV.apply(XV, YV, g.BEM_APPLY_BATCHED, stream)
+        oK.apply(XK, YK, g.BEM_APPLY_BATCHED, stream)
+        torch.cuda.synchronize()
+        errV = (torch.linalg.norm(YV.to(torch.complex128) - YV64) / torch.linalg.norm(YV64)).item()
+        errK = (torch.linalg.norm(YK.to(torch.complex128) - YK64) / torch.linalg.norm(YK64)).item()
+        extra.update({"fp64_entries_per_s": e64 / (ms64 / 1e3), "fp64_ms_per_step": ms64,
+                      "mixed_vs_fp64_speedup": (ms64 / 1e3) / (ms / args.steps / 1e3),
+                      "mixed_vs_fp64_rel_err_V": errV, "mixed_vs_fp64_rel_err_K": errK})
+        del oV64, oK64
+
+    # end to end through the public API with host buffers
+    XVh = torch.empty(XV.shape, dtype=cdt, pin_memory=True)
+    XVh.copy_(XV.cpu())
+    XKh = torch.empty(XK.shape, dtype=cdt, pin_memory=True)
+    XKh.copy_(XK.cpu())
+    YVh = torch.empty(YV.shape, dtype=cdt, pin_memory=True)
+    YKh = torch.empty(YK.shape, dtype=cdt, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_entries = 0
+    for _ in range(args.steps):
+        c2, m2, tv2, tk2 = make(g.BEM_MIXED)
+        XV.copy_(XVh, non_blocking=True)
+        XK.copy_(XKh, non_blocking=True)
+        o1 = tv2.compress(stream)
+        o2 = tk2.compress(stream)
+        o1.apply(XV, YV, g.BEM_APPLY_BATCHED, stream)
+        o2.apply(XK, YK, g.BEM_APPLY_BATCHED, stream)
+        YVh.copy_(YV, non_blocking=True)
+        YKh.copy_(YK, non_blocking=True)
+        torch.cuda.synchronize()
+        e_entries += o1.stats().entries_evaluated + o2.stats().entries_evaluated
+    e2e_s = time.perf_counter() - t0
+    h2d = (xyz.nbytes + tri.astype(np.int32).nbytes) + XV.numel() * 8 + XK.numel() * 8
+    d2h = YV.numel() * 8 + YK.numel() * 8
+
+    peaks = _peaks()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 (FP32) far field + FP64 near/singular, pivots, norms",
+            "data": "synthetic", "config": dict(WORKLOAD, l2="inputs larger than L2 (faces ~GB)"),
+            "clocks": clk.summary(),
+            "e2e": {"value": e_entries / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": None, **extra}
+    line["entry_kernel_ms_per_step"] = face_ms / args.steps
+    line["peaks_source"] = "MEASURED_PEAKS.json" if peaks else "fallback"
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(15.0)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * gcqbem.h -- C ABI of the B300 (sm_103a) library for the multi-frequency
+ * Laplace-domain operator of a 3D-ACA accelerated, convolution-quadrature
+ * time-domain collocation BEM for 3-D linear elastodynamics
+ * (arXiv 2607.15292).
+ *
+ * What the calls compute, in the paper's order:
+ *   material rho, lambda, mu -> wave speeds c1, c2            (Eq. (2.2))
+ *   time grid -> complex frequencies s_k                        (Sec. 2.4)
+ *   flat-triangle mesh, P0 traction / P1 displacement,
+ *   collocation rows at midpoints or nodes                      (Sec. 2.3)
+ *   Laplace-domain entries V[i,e](s_k), (C+K)[i,j](s_k)         (Eqs. (2.14)-(2.15), (2.22))
+ *   cluster trees, block cluster tree, admissibility            (Sec. 3.1, Eqs. (3.10)-(3.11))
+ *   3D-ACA of every block to tolerance eps                      (Algorithm 1, Eqs. (3.2)-(3.8))
+ *   apply of the compressed tensor to the vectors of all K
+ *   frequencies, batched or contracted over frequency           (Eq. (3.15))
+ *   uniform-step CQ forward / inverse transforms                (Sec. 2.4)
+ *
+ * Conventions
+ *  - Every call returns a bem_status; no call aborts, throws or exits.  The
+ *    text of the last error of a context is returned by bem_last_error().
+ *  - Handles (bem_ctx, bem_mesh, bem_tree, bem_op) are owned by the library;
+ *    *_destroy frees their host and device memory.  Destroying a NULL
+ *    handle is a no-op.  A tree keeps its mesh and an operator keeps its tree
+ *    alive until they are destroyed (reference counted).
+ *  - Host arrays passed in are copied; the caller may free them on return.
+ *  - Device buffers passed by pointer (X, Y, requests, outputs) belong to
+ *    the caller, must be 16-byte aligned, of the stated size and type, and
+ *    are accessed in the order of the given CUDA stream (cudaStream_t passed
+ *    as void*; NULL = legacy default stream).  Calls on a stream return
+ *    before the device work ends unless stated otherwise.
+ *  - Complex numbers are interleaved (re, im): c128 = 2 x double in FP64
+ *    precision, c64 = 2 x float in MIXED precision (bem_options.precision).
+ *  - 3x3 blocks are stored row-major: element [a*3 + b] is row component a
+ *    (collocation point), column component b (basis function).
+ *  - Vectors over all K frequencies are K x n x 3 arrays (frequency
+ *    slowest, then node/element, then xyz component): vector k is
+ *    contiguous.
+ */
+#ifndef GCQBEM_H
+#define GCQBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GCQBEM_ABI_VERSION 1
+
+typedef enum {
+  BEM_OK = 0,
+  BEM_ERR_ARG = 1,            /* invalid argument (NULL, size, enum, range) */
+  BEM_ERR_CUDA = 2,           /* a CUDA runtime call failed                 */
+  BEM_ERR_OOM = 3,            /* device or host allocation failed           */
+  BEM_ERR_MESH = 4,           /* degenerate mesh (zero area, bad index)     */
+  BEM_ERR_NOT_CONVERGED = 5,  /* an iteration hit its cap                   */
+  BEM_ERR_STATE = 6           /* call out of order (no frequencies, ...)    */
+} bem_status;
+
+typedef enum { BEM_FP64 = 0, BEM_MIXED = 1 } bem_precision;
+/* Collocation rows: element midpoints (Dirichlet rows) or nodes (Neumann
+ * rows), Sec. 2.3 after Eq. (2.15). */
+typedef enum { BEM_ROWS_CENTROIDS = 0, BEM_ROWS_NODES = 1 } bem_rows;
+/* Single layer V (columns = elements, P0) or double layer C + K (columns =
+ * nodes, P1; the integral-free term C of Eq. (2.7) included), Eq. (2.15). */
+typedef enum { BEM_SL = 0, BEM_DL = 1 } bem_kernel;
+/* Batched: Y_k = C(s_k) X_k for all k.  Contracted: y = sum_k C(s_k) X_k,
+ * the gCQ history sum of Eq. (3.15). */
+typedef enum { BEM_APPLY_BATCHED = 0, BEM_APPLY_CONTRACTED = 1 } bem_apply_mode;
+
+typedef struct {
+  double eps;             /* 3D-ACA tolerance of Algorithm 1 (default 1e-6)        */
+  double eps_aca;         /* face ACA tolerance, Eq. (3.12) (default eps / 100)    */
+  int32_t leaf;           /* b_min of the cluster trees, Sec. 3.1 (default 32)     */
+  double eta;             /* admissibility parameter of Eq. (3.11) (default 2)     */
+  int32_t precision;      /* bem_precision (default BEM_FP64)                       */
+  int32_t device;         /* CUDA device ordinal (default 0); -1 = host-only context:
+                             meshes and trees are built, device calls fail with
+                             BEM_ERR_STATE (lets host logic run without a GPU)    */
+  int32_t compress_faces; /* 1: far-block faces stored as U V^H (default 1)         */
+} bem_options;
+
+typedef struct bem_ctx bem_ctx;
+typedef struct bem_mesh bem_mesh;
+typedef struct bem_tree bem_tree;
+typedef struct bem_op bem_op;
+
+/* Fills *opt with the defaults listed above.  BEM_ERR_ARG if opt is NULL. */
+bem_status bem_options_default(bem_options* opt);
+
+/* Creates a context on opt->device (NULL opt = defaults).  Uploads the
+ * quadrature tables (Gauss-Legendre nodes by Newton's method; collapsed
+ * rules; Duffy rules).  *out is NULL on failure. */
+bem_status bem_ctx_create(const bem_options* opt, bem_ctx** out);
+void bem_ctx_destroy(bem_ctx* ctx);
+/* Text of the last failing call on ctx ("" if none).  Valid until the next
+ * call on ctx.  NULL ctx gives the text of the last failed bem_ctx_create. */
+const char* bem_last_error(const bem_ctx* ctx);
+/* Copies the options in use into *opt. */
+bem_status bem_ctx_options(const bem_ctx* ctx, bem_options* opt);
+
+/* Isotropic material (Eq. (2.2)): density rho > 0, Lame constants with
+ * mu > 0 and lambda + 2 mu > 0.  Writes c1, c2 to the optional outputs. */
+bem_status bem_material_set(bem_ctx* ctx, double rho, double lambda, double mu,
+                            double* c1, double* c2);
+
+/* Frequencies of uniform-step BDF2 convolution quadrature (Sec. 2.4 with
+ * constant steps): s_k = delta(zeta_k) / dt, delta(z) = (1-z) + (1-z)^2/2,
+ * zeta_k = lam exp(-2 pi i k / (N + 1)), lam = (1e-10)^(1/(2N)),
+ * k = 0..K-1, written to s_re_im (host, 2K doubles).  N >= 1, dt > 0,
+ * 1 <= K <= N + 1. */
+bem_status bem_freqs_bdf2(int32_t N, double dt, int32_t K, double* s_re_im);
+/* Sets the K frequencies (host array of 2K doubles) used by every later
+ * entry evaluation and compression on ctx.  Re(s) > 0 required. */
+bem_status bem_freqs_set(bem_ctx* ctx, const double* s_re_im, int32_t K);
+
+/* Surface mesh of flat triangles (Eq. (2.10)): xyz host n_nodes x 3 doubles,
+ * tri host n_tris x 3 int32 node indices, counter-clockwise seen from the
+ * side the normal points to (outward for the interior problem).
+ * BEM_ERR_MESH on an index out of range or a zero-area triangle. */
+bem_status bem_mesh_create(bem_ctx* ctx, const double* xyz, int64_t n_nodes,
+                           const int32_t* tri, int64_t n_tris, bem_mesh** out);
+void bem_mesh_destroy(bem_mesh* mesh);
+
+/* Raw entry evaluation (the ENTRY oracle of Algorithm 1): for request r,
+ * req[3r + 0] = row (collocation point index), req[3r + 1] = column
+ * (element for BEM_SL, node for BEM_DL), req[3r + 2] = frequency index k
+ * (0..K-1, or -1 for s = 0: static Kelvin kernels), all on the device.
+ * out (device) receives n 3x3 complex blocks, 9 c128 (FP64) or 9 c64
+ * (MIXED) each.  Indices are checked on the device; a request out of range
+ * yields a NaN block and BEM_ERR_ARG once the stream is synchronised
+ * (this call synchronises the stream). */
+bem_status bem_entries(bem_mesh* mesh, int32_t rows, int32_t kernel,
+                       const int32_t* req, int64_t n, void* out, void* stream);
+
+/* Row/column cluster trees by PCA bisection and the block cluster tree with
+ * the admissibility of Eq. (3.11) (host C++), for the given rows and
+ * kernel.  Deterministic. */
+bem_status bem_tree_build(bem_mesh* mesh, int32_t rows, int32_t kernel, bem_tree** out);
+void bem_tree_destroy(bem_tree* tree);
+/* Sizes: number of blocks, of far blocks, rows, columns. */
+bem_status bem_tree_sizes(const bem_tree* tree, int64_t* n_blocks, int64_t* n_far,
+                          int64_t* n_rows, int64_t* n_cols);
+/* Host copies: row_perm (n_rows) and col_perm (n_cols) give the original
+ * index at each cluster-ordered position; blocks (n_blocks x 5 int64):
+ * row offset, rows, column offset, columns (in cluster order), far flag. */
+bem_status bem_tree_export(const bem_tree* tree, int32_t* row_perm, int32_t* col_perm,
+                           int64_t* blocks);
+
+/* Compresses the K-frequency tensor of the tree's operator: per block,
+ * Algorithm 1 with faces evaluated densely on the device at the pivot
+ * frequencies, fibres over all K, dense fallback when no regular pivot
+ * exists; far-block faces then compressed by matrix-valued ACA + QR/SVD to
+ * eps_aca when options.compress_faces.  Synchronises the stream on return.
+ * BEM_ERR_STATE if no frequencies or material are set. */
+bem_status bem_op_compress(bem_tree* tree, void* stream, bem_op** out);
+void bem_op_destroy(bem_op* op);
+
+/* Apply (Eq. (3.15)).  BATCHED: X device K x n_cols x 3 complex,
+ * Y device K x n_rows x 3 complex, Y_k = C(s_k) X_k (Y overwritten).
+ * CONTRACTED: X as above, Y device n_rows x 3 complex, Y = sum_k C(s_k) X_k.
+ * Complex type c128 (FP64) or c64 (MIXED).  transpose = 0 only (reserved).
+ * Asynchronous on the stream; no host synchronisation. */
+bem_status bem_op_apply(bem_op* op, int32_t mode, int32_t transpose,
+                        const void* X, void* Y, void* stream);
+
+/* Dense reconstruction of the compressed tensor (for checks on small
+ * meshes): out device n_rows x n_cols x K 3x3 complex blocks, original
+ * (not cluster) ordering.  Synchronises the stream. */
+bem_status bem_op_dense(bem_op* op, void* out, void* stream);
+
+typedef struct {
+  int64_t n_blocks, n_far, n_aca, n_dense, n_rank0;
+  int64_t rank_min, rank_max;
+  double rank_mean;             /* over 3D-ACA compressed blocks           */
+  double stored_bytes;          /* faces + fibres + dense blocks           */
+  double dense_bytes;           /* n_rows * n_cols * K * 9 complex          */
+  double compression_rate;      /* stored / dense (Sec. 4.1)                */
+  int64_t entries_evaluated;    /* 3x3 block entries computed in compress  */
+  double t_entries_ms;          /* device time of the entry kernels        */
+  double t_compress_ms;         /* wall time of bem_op_compress             */
+  int64_t apply_bytes;          /* algorithmic bytes read+written per apply */
+} bem_op_stats;
+bem_status bem_op_stats_get(const bem_op* op, bem_op_stats* st);
+
+/* Per-block results (host, n_blocks x 4 int64): kind (0 aca, 1 dense,
+ * 2 rank0), rank, first pivot frequency k_1 (-1 if none), face storage
+ * (0 dense faces, 1 low rank).  Blocks in bem_tree_export order. */
+bem_status bem_op_blocks(const bem_op* op, int64_t* info);
+
+/* Uniform-step CQ (BDF2) transforms over L = N + 1 time levels for nvec
+ * complex128 values per level (device, L x nvec):
+ *   forward: g^_k = sum_j lam^j g_j exp(-2 pi i j k / L)
+ *   inverse: y_n  = lam^-n / L sum_k y^_k exp(2 pi i n k / L)
+ * lam = (1e-10)^(1/(2N)).  in and out must not overlap. */
+bem_status bem_cq_forward(int32_t N, int64_t nvec, const void* in, void* out, void* stream);
+bem_status bem_cq_inverse(int32_t N, int64_t nvec, const void* in, void* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCQBEM_H */

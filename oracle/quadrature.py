@@ -9,7 +9,10 @@ used on both sides of the parity tests:
   triangle, xi = u, eta = v (1 - u), weight w_u w_v (1 - u); exact for
   polynomials of total degree <= 2n - 2.
 * Order by distance: n = 3 if |x - centroid| >= 4 h, n = 5 if >= 2 h,
-  n = 8 if >= h, else n = 16, with h the longest edge of the element.
+  n = 8 if >= h, else n = 16, with h the longest edge of the element.  The
+  comparisons carry a relative band of 1e-12 (dist >= D h (1 - 1e-12)) so
+  that distances lying exactly on a threshold in exact arithmetic (regular
+  grids) give the same order whatever the rounding of dist and h.
 * Singular (the collocation point lies on the closed element): split the
   element into sub-triangles with apex at the point and use the Duffy map
   y = A + u ((B - A) + v (C - B)), dy = 2 |ABC| u du dv, 16 x 16
@@ -60,11 +63,12 @@ def triangle_rule(n: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
 
 def order_for(dist: float, h: float) -> int:
     """Regular-rule order n from the distance ratio dist / h."""
-    if dist >= D_FAR * h:
+    band = 1.0 - 1e-12
+    if dist >= D_FAR * h * band:
         return N_FAR
-    if dist >= D_MID * h:
+    if dist >= D_MID * h * band:
         return N_MID
-    if dist >= D_NEAR * h:
+    if dist >= D_NEAR * h * band:
         return N_NEAR
     return N_CLOSE
 

@@ -1,0 +1,286 @@
+"""Python binding of libgcqbem, the B300 (sm_103a) library for the
+multi-frequency Laplace-domain operator of a 3D-ACA accelerated
+convolution-quadrature BEM for 3-D elastodynamics (arXiv 2607.15292).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library behind the C ABI of ``include/gcqbem.h``.  Device buffers are
+PyTorch tensors (their ``data_ptr()`` is passed); streams are PyTorch CUDA
+streams.  Importing fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgcqbem.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libgcqbem.so not found at {LIB_PATH}: build it with "
+        "`python -m paper_2607_15292_b300.build` (nvcc, sm_103a)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+BEM_OK, BEM_ERR_ARG, BEM_ERR_CUDA, BEM_ERR_OOM, BEM_ERR_MESH, BEM_ERR_NOT_CONVERGED, BEM_ERR_STATE = range(7)
+BEM_FP64, BEM_MIXED = 0, 1
+BEM_ROWS_CENTROIDS, BEM_ROWS_NODES = 0, 1
+BEM_SL, BEM_DL = 0, 1
+BEM_APPLY_BATCHED, BEM_APPLY_CONTRACTED = 0, 1
+
+_STATUS = {0: "BEM_OK", 1: "BEM_ERR_ARG", 2: "BEM_ERR_CUDA", 3: "BEM_ERR_OOM", 4: "BEM_ERR_MESH",
+           5: "BEM_ERR_NOT_CONVERGED", 6: "BEM_ERR_STATE"}
+
+
+class bem_options(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("eps_aca", ctypes.c_double), ("leaf", ctypes.c_int32),
+                ("eta", ctypes.c_double), ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("compress_faces", ctypes.c_int32)]
+
+
+class bem_op_stats(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int64), ("n_far", ctypes.c_int64), ("n_aca", ctypes.c_int64),
+                ("n_dense", ctypes.c_int64), ("n_rank0", ctypes.c_int64), ("rank_min", ctypes.c_int64),
+                ("rank_max", ctypes.c_int64), ("rank_mean", ctypes.c_double),
+                ("stored_bytes", ctypes.c_double), ("dense_bytes", ctypes.c_double),
+                ("compression_rate", ctypes.c_double), ("entries_evaluated", ctypes.c_int64),
+                ("t_entries_ms", ctypes.c_double), ("t_compress_ms", ctypes.c_double),
+                ("apply_bytes", ctypes.c_int64)]
+
+
+_vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_P = ctypes.POINTER
+_SIGS = {
+    "bem_options_default": (_i32, [_P(bem_options)]),
+    "bem_ctx_create": (_i32, [_P(bem_options), _P(_vp)]),
+    "bem_ctx_destroy": (None, [_vp]),
+    "bem_last_error": (ctypes.c_char_p, [_vp]),
+    "bem_ctx_options": (_i32, [_vp, _P(bem_options)]),
+    "bem_material_set": (_i32, [_vp, _dbl, _dbl, _dbl, _P(_dbl), _P(_dbl)]),
+    "bem_freqs_bdf2": (_i32, [_i32, _dbl, _i32, _P(_dbl)]),
+    "bem_freqs_set": (_i32, [_vp, _P(_dbl), _i32]),
+    "bem_mesh_create": (_i32, [_vp, _P(_dbl), _i64, _P(_i32), _i64, _P(_vp)]),
+    "bem_mesh_destroy": (None, [_vp]),
+    "bem_entries": (_i32, [_vp, _i32, _i32, _vp, _i64, _vp, _vp]),
+    "bem_tree_build": (_i32, [_vp, _i32, _i32, _P(_vp)]),
+    "bem_tree_destroy": (None, [_vp]),
+    "bem_tree_sizes": (_i32, [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64)]),
+    "bem_tree_export": (_i32, [_vp, _P(_i32), _P(_i32), _P(_i64)]),
+    "bem_op_compress": (_i32, [_vp, _vp, _P(_vp)]),
+    "bem_op_destroy": (None, [_vp]),
+    "bem_op_apply": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
+    "bem_op_dense": (_i32, [_vp, _vp, _vp]),
+    "bem_op_stats_get": (_i32, [_vp, _P(bem_op_stats)]),
+    "bem_op_blocks": (_i32, [_vp, _P(_i64)]),
+    "bem_cq_forward": (_i32, [_i32, _i64, _vp, _vp, _vp]),
+    "bem_cq_inverse": (_i32, [_i32, _i64, _vp, _vp, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class BemError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st: int, ctx_ptr=None):
+    if st != BEM_OK:
+        msg = _lib.bem_last_error(ctx_ptr)
+        raise BemError(st, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def options_default() -> bem_options:
+    o = bem_options()
+    _check(_lib.bem_options_default(ctypes.byref(o)))
+    return o
+
+
+def freqs_bdf2(N: int, dt: float, K: int) -> np.ndarray:
+    """Frequencies of uniform BDF2 CQ (complex128, computed by the library)."""
+    out = np.zeros(2 * K, dtype=np.float64)
+    _check(_lib.bem_freqs_bdf2(N, dt, K, out.ctypes.data_as(_P(_dbl))))
+    return out[0::2] + 1j * out[1::2]
+
+
+def cq_forward(N: int, nvec: int, x, out, stream=None):
+    _check(_lib.bem_cq_forward(N, nvec, _dptr(x), _dptr(out), _stream_ptr(stream)))
+
+
+def cq_inverse(N: int, nvec: int, x, out, stream=None):
+    _check(_lib.bem_cq_inverse(N, nvec, _dptr(x), _dptr(out), _stream_ptr(stream)))
+
+
+class Context:
+    """bem_ctx: options, material, frequencies (one CUDA device)."""
+
+    def __init__(self, eps=1e-6, eps_aca=None, leaf=32, eta=2.0, precision=BEM_FP64, device=0,
+                 compress_faces=1):
+        o = options_default()
+        o.eps = eps
+        o.eps_aca = eps / 100.0 if eps_aca is None else eps_aca
+        o.leaf, o.eta, o.precision, o.device, o.compress_faces = leaf, eta, precision, device, compress_faces
+        self._p = ctypes.c_void_p()
+        _check(_lib.bem_ctx_create(ctypes.byref(o), ctypes.byref(self._p)), None)
+        self.precision = precision
+        self.K = 0
+
+    @property
+    def ptr(self):
+        return self._p
+
+    def close(self):
+        if self._p:
+            _lib.bem_ctx_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def material(self, rho, lam, mu):
+        c1, c2 = _dbl(), _dbl()
+        _check(_lib.bem_material_set(self._p, rho, lam, mu, ctypes.byref(c1), ctypes.byref(c2)), self._p)
+        return c1.value, c2.value
+
+    def freqs(self, s):
+        s = np.asarray(s, dtype=np.complex128)
+        buf = np.empty(2 * len(s))
+        buf[0::2], buf[1::2] = s.real, s.imag
+        _check(_lib.bem_freqs_set(self._p, buf.ctypes.data_as(_P(_dbl)), len(s)), self._p)
+        self.K = len(s)
+
+    def mesh(self, xyz, tri) -> "Mesh":
+        return Mesh(self, xyz, tri)
+
+
+class Mesh:
+    def __init__(self, ctx: Context, xyz, tri):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        self.ctx = ctx
+        self.n_nodes, self.n_tris = len(xyz), len(tri)
+        self._p = ctypes.c_void_p()
+        _check(_lib.bem_mesh_create(ctx.ptr, xyz.ctypes.data_as(_P(_dbl)), len(xyz),
+                                    tri.ctypes.data_as(_P(_i32)), len(tri), ctypes.byref(self._p)), ctx.ptr)
+
+    def __del__(self):
+        try:
+            if self._p:
+                _lib.bem_mesh_destroy(self._p)
+        except Exception:
+            pass
+
+    def entries(self, rows: int, kernel: int, req, out, stream=None):
+        """req: int32 CUDA tensor (n, 3) of (row, col, k); out: complex CUDA
+        tensor (n, 3, 3) (complex128 in FP64, complex64 in MIXED)."""
+        n = req.shape[0]
+        _check(_lib.bem_entries(self._p, rows, kernel, _dptr(req), n, _dptr(out), _stream_ptr(stream)),
+               self.ctx.ptr)
+
+    def tree(self, rows: int, kernel: int) -> "Tree":
+        return Tree(self, rows, kernel)
+
+
+class Tree:
+    def __init__(self, mesh: Mesh, rows: int, kernel: int):
+        self.mesh, self.rows, self.kernel = mesh, rows, kernel
+        self._p = ctypes.c_void_p()
+        _check(_lib.bem_tree_build(mesh._p, rows, kernel, ctypes.byref(self._p)), mesh.ctx.ptr)
+        nb, nf, nr, nc = _i64(), _i64(), _i64(), _i64()
+        _check(_lib.bem_tree_sizes(self._p, ctypes.byref(nb), ctypes.byref(nf), ctypes.byref(nr), ctypes.byref(nc)))
+        self.n_blocks, self.n_far, self.n_rows, self.n_cols = nb.value, nf.value, nr.value, nc.value
+
+    def __del__(self):
+        try:
+            if self._p:
+                _lib.bem_tree_destroy(self._p)
+        except Exception:
+            pass
+
+    def export(self):
+        rp = np.zeros(self.n_rows, dtype=np.int32)
+        cp = np.zeros(self.n_cols, dtype=np.int32)
+        bl = np.zeros((self.n_blocks, 5), dtype=np.int64)
+        _check(_lib.bem_tree_export(self._p, rp.ctypes.data_as(_P(_i32)), cp.ctypes.data_as(_P(_i32)),
+                                    bl.ctypes.data_as(_P(_i64))))
+        return rp, cp, bl
+
+    def compress(self, stream=None) -> "Operator":
+        return Operator(self, stream)
+
+
+@dataclass
+class Stats:
+    n_blocks: int
+    n_far: int
+    n_aca: int
+    n_dense: int
+    n_rank0: int
+    rank_min: int
+    rank_max: int
+    rank_mean: float
+    stored_bytes: float
+    dense_bytes: float
+    compression_rate: float
+    entries_evaluated: int
+    t_entries_ms: float
+    t_compress_ms: float
+    apply_bytes: int
+
+
+class Operator:
+    """Compressed K-frequency tensor (bem_op)."""
+
+    def __init__(self, tree: Tree, stream=None):
+        self.tree = tree
+        self.ctx = tree.mesh.ctx
+        self.K = self.ctx.K
+        self._p = ctypes.c_void_p()
+        _check(_lib.bem_op_compress(tree._p, _stream_ptr(stream), ctypes.byref(self._p)), self.ctx.ptr)
+
+    def __del__(self):
+        try:
+            if self._p:
+                _lib.bem_op_destroy(self._p)
+        except Exception:
+            pass
+
+    def apply(self, X, Y, mode: int = BEM_APPLY_BATCHED, stream=None):
+        _check(_lib.bem_op_apply(self._p, mode, 0, _dptr(X), _dptr(Y), _stream_ptr(stream)), self.ctx.ptr)
+
+    def dense(self, out, stream=None):
+        _check(_lib.bem_op_dense(self._p, _dptr(out), _stream_ptr(stream)), self.ctx.ptr)
+
+    def stats(self) -> Stats:
+        s = bem_op_stats()
+        _check(_lib.bem_op_stats_get(self._p, ctypes.byref(s)))
+        return Stats(*[getattr(s, f) for f, _ in bem_op_stats._fields_])
+
+    def blocks(self) -> np.ndarray:
+        out = np.zeros((self.tree.n_blocks, 4), dtype=np.int64)
+        _check(_lib.bem_op_blocks(self._p, out.ctypes.data_as(_P(_i64))))
+        return out

@@ -1,0 +1,52 @@
+"""Builds libgcqbem.so in-tree for B300 (sm_103a) with nvcc.
+
+    python -m paper_2607_15292_b300.build [--ptxas-v]
+
+The library is plain C ABI (include/gcqbem.h); no PyTorch headers are used.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+LIB = os.path.join(HERE, "libgcqbem.so")
+SOURCES = ["host.cpp", "gcqbem.cu"]
+DEPS = ["internal.h", "entry.cuh", "aca3d.cuh", "apply.cuh"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if cand and (os.path.isabs(cand) and os.path.exists(cand) or not os.path.isabs(cand)):
+            return cand
+    return "nvcc"
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    files = [os.path.join(CSRC, f) for f in SOURCES + DEPS] + [os.path.join(ROOT, "include", "gcqbem.h")]
+    return any(os.path.getmtime(f) > t for f in files)
+
+
+def build(force: bool = False, ptxas_verbose: bool = False) -> str:
+    if not force and not _stale():
+        return LIB
+    cmd = [nvcc(), "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-O3", "-shared",
+           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "--expt-relaxed-constexpr",
+           *(os.path.join(CSRC, f) for f in SOURCES), "-o", LIB + ".tmp", "-lcudart"]
+    if ptxas_verbose:
+        cmd[1:1] = ["-Xptxas", "-v"]
+    subprocess.run(cmd, check=True)
+    os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force=True, ptxas_verbose="--ptxas-v" in sys.argv)
+    print(LIB)

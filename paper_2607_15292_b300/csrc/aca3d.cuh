@@ -1,0 +1,894 @@
+// Batched 3D-ACA (Algorithm 1) over every block of the block cluster tree.
+//
+// One iteration d advances all active blocks by one face-fibre pair:
+//   k_face        H_d[i,j] = ENTRY(i,j,k_d) - sum_{p<d} H_p[i,j] f_p[k_d]
+//                 (all entries of all active blocks, one thread per entry),
+//                 per-tile partials of max sigma_3, ||H_d||^2 and the Gram
+//                 blocks M_pd = sum_ij H_p[i,j]^H H_d[i,j] (p <= d);
+//   k_block_red   per block: pivot (i_d, j_d) = argmax sigma_3 (smallest
+//                 flat index on ties), ||H_d||_F, M_pd;
+//   k_fibre_step  per block, one thread per frequency:
+//                 f_d[k] = H_d[i_d,j_d]^{-1} (ENTRY(i_d,j_d,k) - sum_p H_p[i_d,j_d] f_p[k]),
+//                 ||C^(d)||_F^2 by the recursion of Eq. (3.3) (matrix form),
+//                 the stop test ||H_d|| ||f_d|| <= eps ||C^(d)|| (pair discarded),
+//                 k_{d+1} = argmax over unused k of sigma_3(f_d[k]) (Eq. (3.8)),
+//                 dense fallback when no regular pivot exists.
+// Faces are stored densely per block ([i][j][3][3], cluster order), fibres
+// [k][3][3]; slot tables are [slot][block].
+#pragma once
+
+namespace gcq {
+
+enum : int32_t { ST_ACTIVE = 0, ST_DONE = 1, ST_DENSE = 2, ST_RANK0 = 3 };
+
+constexpr double kPivTol = 1e-13;   // no regular pivot: sigma_3 <= kPivTol ||.||_F
+constexpr double kTiny = 1e-14;     // vanishing face residual
+constexpr int kTile = 256;          // entries per tile (= threads per CTA)
+
+struct BlkDev {
+  int64_t r0, m, c0, n;
+  int32_t far, status, rank, k_cur;
+  int64_t piv;          // flat pivot index li * n + lj of the current face
+  double norm2;         // ||C^(rank)||_F^2
+  double h2;            // ||H_d||_F^2 of the current face
+  double s3max;
+  double f2;
+  int32_t t0, t1;       // tile range of the current iteration
+};
+
+struct Tile {
+  int32_t blk;
+  int32_t k;            // frequency (dense fill) or -1
+  int64_t start;        // first flat entry
+};
+
+struct OpData {
+  int K = 0, prec = 0, rows = 0, kernel = 0;
+  int64_t n_blocks = 0, n_rows = 0, n_cols = 0;
+  std::vector<BlkDev> h_blk;
+  BlkDev* d_blk = nullptr;
+  int32_t* d_row_perm = nullptr;
+  int32_t* d_col_perm = nullptr;
+  void** d_face = nullptr;     // [K][n_blocks] slot -> face
+  void** d_fib = nullptr;      // [K][n_blocks] slot -> fibre
+  void** d_dense = nullptr;    // [n_blocks] dense K x m x n x 9, or null
+  std::vector<void*> h_face, h_fib, h_dense;
+  std::vector<void*> allocs;   // device chunks owned by the operator
+  int32_t* d_ks = nullptr;     // [n_blocks][K] pivot frequencies
+  uint8_t* d_used = nullptr;   // [n_blocks][K]
+  double2* d_M = nullptr;      // [n_blocks][K][9] Gram of the current face
+  int64_t entries = 0;
+  double t_entries_ms = 0, t_compress_ms = 0;
+  int64_t apply_bytes = 0;
+  // apply work lists
+  int32_t* d_apply_items = nullptr;  // (block, row tile, k tile) for aca blocks
+  int64_t n_apply_items = 0;
+  int32_t* d_dense_list = nullptr;   // dense block ids
+  int64_t n_dense = 0;
+  int32_t* d_aca_list = nullptr;     // aca block ids (rank > 0)
+  int64_t n_aca = 0;
+  void* d_z = nullptr;               // contracted-apply scratch
+  int64_t* d_zoff = nullptr;         // per aca block offset into d_z (faces x n x 3)
+  int32_t* d_zitems = nullptr;       // contracted-apply z work items (int4)
+  int64_t n_zitems = 0;
+  int64_t z_elems = 0;
+};
+
+// ---- 3x3 complex helpers (FP64) ----------------------------------------------
+template <typename W>
+__device__ __forceinline__ void cof3(const cx<W>* E, cx<W>* C) {
+  // cofactor matrix C[a][b] = (-1)^{a+b} minor_ab
+  C[0] = E[4] * E[8] - E[5] * E[7];
+  C[1] = E[5] * E[6] - E[3] * E[8];
+  C[2] = E[3] * E[7] - E[4] * E[6];
+  C[3] = E[2] * E[7] - E[1] * E[8];
+  C[4] = E[0] * E[8] - E[2] * E[6];
+  C[5] = E[1] * E[6] - E[0] * E[7];
+  C[6] = E[1] * E[5] - E[2] * E[4];
+  C[7] = E[2] * E[3] - E[0] * E[5];
+  C[8] = E[0] * E[4] - E[1] * E[3];
+}
+
+// smallest singular value of a 3x3 complex matrix: smallest root of the
+// characteristic polynomial of E^H E, lambda^3 - e1 lambda^2 + e2 lambda - e3,
+// whose coefficients are the invariants ||E||_F^2, ||cof E||_F^2, |det E|^2
+// (all formed directly from E, so a tiny sigma_3 keeps its relative accuracy);
+// Newton's method from lambda = 0 increases monotonically to that root.  E is
+// scaled by its largest component first (no under/overflow of the invariants).
+template <typename W>
+__device__ W sigma3(const cx<W>* Ein) {
+  W mx = W(0);
+  for (int c = 0; c < 9; ++c) mx = fmax(mx, fmax(fabs(Ein[c].x), fabs(Ein[c].y)));
+  if (!(mx > W(0))) return W(0);
+  const W inv = W(1) / mx;
+  cx<W> E[9];
+  for (int c = 0; c < 9; ++c) E[c] = inv * Ein[c];
+  cx<W> C[9];
+  cof3(E, C);
+  W e1 = 0, e2 = 0;
+  for (int c = 0; c < 9; ++c) {
+    e1 += E[c].x * E[c].x + E[c].y * E[c].y;
+    e2 += C[c].x * C[c].x + C[c].y * C[c].y;
+  }
+  cx<W> det = E[0] * C[0] + E[1] * C[1] + E[2] * C[2];
+  W e3 = det.x * det.x + det.y * det.y;
+  if (!(e2 > W(0)) || !(e3 > W(0))) return W(0);
+  const W tol = sizeof(W) == 8 ? W(1e-15) : W(1e-7);
+  W lam = W(0);
+  for (int it = 0; it < 80; ++it) {
+    W p = ((lam - e1) * lam + e2) * lam - e3;
+    W dp = (W(3) * lam - W(2) * e1) * lam + e2;
+    if (!(dp > W(0))) break;
+    W dl = p / dp;
+    lam -= dl;
+    if (fabs(dl) <= tol * lam) break;
+  }
+  return sqrt(fmax(lam, W(0))) * mx;
+}
+
+__device__ __forceinline__ bool inv3(const cx<double>* P, cx<double>* Pi) {
+  cx<double> C[9];
+  cof3(P, C);
+  cx<double> det = P[0] * C[0] + P[1] * C[1] + P[2] * C[2];
+  double dd = det.x * det.x + det.y * det.y;
+  if (!(dd > 0.0)) return false;
+  cx<double> id = {det.x / dd, -det.y / dd};
+  // inverse = adj / det, adj = C^T
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Pi[3 * a + b] = C[3 * b + a] * id;
+  return true;
+}
+
+__device__ __forceinline__ void mm3(const cx<double>* A, const cx<double>* B, cx<double>* C) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      cx<double> s = {0, 0};
+      for (int c = 0; c < 3; ++c) s = cfma(A[3 * a + c], B[3 * c + b], s);
+      C[3 * a + b] = s;
+    }
+}
+
+// block-wide sum of NV values (blockDim.x a multiple of 32, <= 1024): warp
+// stage in T, cross-warp stage in double; result (double) valid in thread 0.
+// Fixed order: deterministic.
+template <int NV, typename T>
+__device__ __forceinline__ void block_sum(const T* v, double* out, double* sh /* >= 32 * NV */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  for (int c = 0; c < NV; ++c) {
+    T x = v[c];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[c * 32 + wid] = (double)x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    for (int c = 0; c < NV; ++c) {
+      double x = lane < nw ? sh[c * 32 + lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      out[c] = x;
+    }
+  }
+  __syncthreads();
+}
+template <int NV>
+__device__ __forceinline__ void block_sum(double* v, double* sh) {
+  block_sum<NV, double>(v, v, sh);
+}
+
+// block-wide argmax (value desc, index asc); result in thread 0
+__device__ __forceinline__ void block_argmax(double& val, int64_t& idx, double* shv, int64_t* shi) {
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_down_sync(0xffffffffu, val, o);
+    int64_t oi = __shfl_down_sync(0xffffffffu, idx, o);
+    if (ov > val || (ov == val && oi < idx)) {
+      val = ov;
+      idx = oi;
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    shv[wid] = val;
+    shi[wid] = idx;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    val = lane < nw ? shv[lane] : -1.0;
+    idx = lane < nw ? shi[lane] : INT64_MAX;
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, val, o);
+      int64_t oi = __shfl_down_sync(0xffffffffu, idx, o);
+      if (ov > val || (ov == val && oi < idx)) {
+        val = ov;
+        idx = oi;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ---- face kernel -------------------------------------------------------------
+// FP64 mode: faces/fibres in c128, residual, pivot criterion and Gram products
+// in double.  MIXED mode: faces/fibres in complex float-float (float4), the
+// residual E - sum_p H_p f_p accumulated with error-free products (FMA) and
+// compensated sums (its terms cancel heavily as the rank grows, and FP32
+// rounding of the ACA state inflates the rank); pivot criterion and Gram
+// products from the high parts in FP32, Gram sums in double.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (h, l) -= (ah + al)(bh + bl), dropping al*bl (below 2^-48 relative)
+__device__ __forceinline__ void ff_sub_prod(float& h, float& l, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  float q = fmaf(ah, bh, -p);
+  q = fmaf(ah, bl, q);
+  q = fmaf(al, bh, q);
+  float s, e;
+  two_sum(h, -p, s, e);
+  h = s;
+  l += e - q;
+}
+
+template <typename S>
+struct WorkOf;
+template <>
+struct WorkOf<double2> {
+  using W = double;
+};
+template <>
+struct WorkOf<float4> {
+  using W = float;
+};
+
+template <typename R, typename S, int KERN, int ROWS>
+__global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restrict__ tiles,
+                                                BlkDev* __restrict__ blk, S* const* __restrict__ face_tab,
+                                                S* const* __restrict__ fib_tab, int64_t nb, int slot,
+                                                const int32_t* __restrict__ row_perm,
+                                                const int32_t* __restrict__ col_perm, double* __restrict__ p_s3,
+                                                int64_t* __restrict__ p_idx, double* __restrict__ p_h2,
+                                                double2* __restrict__ p_M, int K) {
+  using W = typename WorkOf<S>::W;
+  __shared__ S sf[64 * 9];     // f_p[k_d] for p < slot, in chunks of 64
+  __shared__ double shv[32 * 18];
+  __shared__ int64_t shi[32];
+  const Tile t = tiles[blockIdx.x];
+  const BlkDev& B = blk[t.blk];
+  const int64_t e = t.start + threadIdx.x;
+  const bool ok = e < B.m * B.n;
+  const int kd = B.k_cur;
+  constexpr bool FF = sizeof(S) == sizeof(float4) && sizeof(W) == sizeof(float);
+  float fh[18], fl[18];           // float-float accumulators (MIXED)
+  cx<double> Hd64[9];             // double accumulators (FP64)
+  int i = 0, j = 0;
+  if (ok) {
+    const int64_t li = e / B.n, lj = e - (e / B.n) * B.n;
+    i = row_perm[B.r0 + li];
+    j = col_perm[B.c0 + lj];
+  }
+  cx<double> is2;
+  const cx<double> s = freq(v, kd, is2);
+  if constexpr (FF) {
+    // FP32 entries: light ones one per thread, heavy ones (near/singular
+    // rules) shared by the warp (lanes over quadrature points)
+    const cx<float> sf32 = {(float)s.x, (float)s.y}, is32 = {(float)is2.x, (float)is2.y};
+    for (int c = 0; c < 18; ++c) {
+      fh[c] = 0.f;
+      fl[c] = 0.f;
+    }
+    const bool heavy = ok && entry_heavy<KERN, ROWS>(v, i, j);
+    if (ok && !heavy) entry_f<KERN, ROWS>(v, i, j, sf32, is32, 0, 1, fh);
+    unsigned hm = __ballot_sync(0xffffffffu, heavy);
+    const int lane = threadIdx.x & 31;
+    while (hm) {
+      const int L = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const int iL = __shfl_sync(0xffffffffu, i, L), jL = __shfl_sync(0xffffffffu, j, L);
+      float part[18];
+      entry_f_warp<KERN, ROWS>(v, iL, jL, sf32, is32, part);
+      if (lane == L)
+        for (int c = 0; c < 18; ++c) fh[c] = part[c];
+    }
+  } else {
+    for (int c = 0; c < 9; ++c) Hd64[c] = {0, 0};
+    if (ok) entry<R, KERN, ROWS>(v, i, j, s, is2, Hd64);
+  }
+  // residual: H = E - sum_p H_p[i,j] f_p[k_d]
+  for (int p0 = 0; p0 < slot; p0 += 64) {
+    const int np = min(64, slot - p0);
+    __syncthreads();
+    for (int c = threadIdx.x; c < np * 9; c += blockDim.x) {
+      const int p = p0 + c / 9;
+      sf[c] = fib_tab[(int64_t)p * nb + t.blk][(int64_t)kd * 9 + c % 9];
+    }
+    __syncthreads();
+    if (ok)
+      for (int p = 0; p < np; ++p) {
+        const S* Hp = face_tab[(int64_t)(p0 + p) * nb + t.blk] + e * 9;
+        const S* f = sf + 9 * p;
+        if constexpr (FF) {
+          float4 hp[9];
+          for (int c = 0; c < 9; ++c) hp[c] = reinterpret_cast<const float4*>(Hp)[c];
+          for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) {
+              const float4 x = hp[3 * a + c];
+              for (int b = 0; b < 3; ++b) {
+                const float4 y = reinterpret_cast<const float4*>(f)[3 * c + b];
+                float& rh = fh[2 * (3 * a + b)];
+                float& rl = fl[2 * (3 * a + b)];
+                float& ih = fh[2 * (3 * a + b) + 1];
+                float& il = fl[2 * (3 * a + b) + 1];
+                // (re) -= x.re y.re - x.im y.im ; (im) -= x.re y.im + x.im y.re
+                ff_sub_prod(rh, rl, x.x, x.z, y.x, y.z);
+                ff_sub_prod(rh, rl, -x.y, -x.w, y.y, y.w);
+                ff_sub_prod(ih, il, x.x, x.z, y.y, y.w);
+                ff_sub_prod(ih, il, x.y, x.w, y.x, y.z);
+              }
+            }
+        } else {
+          cx<double> hp[9], ff[9];
+          for (int c = 0; c < 9; ++c) {
+            hp[c] = St<S>::ld(Hp + c);
+            ff[c] = St<S>::ld(f + c);
+          }
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+              cx<double> acc = Hd64[3 * a + b];
+              for (int c = 0; c < 3; ++c) acc = acc - hp[3 * a + c] * ff[3 * c + b];
+              Hd64[3 * a + b] = acc;
+            }
+        }
+      }
+  }
+  S* Hd = face_tab[(int64_t)slot * nb + t.blk];
+  cx<W> H[9];   // working copy for the pivot criterion and the Gram
+  if (ok) {
+    for (int c = 0; c < 9; ++c) {
+      if constexpr (FF) {
+        // renormalise (h, l) and store
+        float rh = fh[2 * c] + fl[2 * c];
+        float rl = fl[2 * c] - (rh - fh[2 * c]);
+        float ih = fh[2 * c + 1] + fl[2 * c + 1];
+        float il = fl[2 * c + 1] - (ih - fh[2 * c + 1]);
+        reinterpret_cast<float4*>(Hd)[e * 9 + c] = make_float4(rh, ih, rl, il);
+        H[c] = {(W)rh, (W)ih};
+      } else {
+        St<S>::st(Hd + e * 9 + c, Hd64[c]);
+        H[c] = {(W)Hd64[c].x, (W)Hd64[c].y};
+      }
+    }
+  } else {
+    for (int c = 0; c < 9; ++c) H[c] = {W(0), W(0)};
+  }
+  double s3 = ok ? (double)sigma3<W>(H) : -1.0;
+  int64_t idx = ok ? e : INT64_MAX;
+  block_argmax(s3, idx, shv, shi);
+  W h2[1] = {W(0)};
+  if (ok)
+    for (int c = 0; c < 9; ++c) h2[0] += H[c].x * H[c].x + H[c].y * H[c].y;
+  double h2s[1];
+  block_sum<1, W>(h2, h2s, shv);
+  if (threadIdx.x == 0) {
+    p_s3[blockIdx.x] = s3;
+    p_idx[blockIdx.x] = idx;
+    p_h2[blockIdx.x] = h2s[0];
+  }
+  // Gram blocks M_pd = sum_ij H_p[i,j]^H H_d[i,j], p = 0..slot
+  for (int p = 0; p <= slot; ++p) {
+    W g[18];
+    for (int c = 0; c < 18; ++c) g[c] = W(0);
+    if (ok) {
+      const S* Hp = face_tab[(int64_t)p * nb + t.blk] + e * 9;
+      cx<W> hp[9];
+      for (int c = 0; c < 9; ++c) {
+        if constexpr (FF) {
+          const float4 x = reinterpret_cast<const float4*>(Hp)[c];
+          hp[c] = {(W)x.x, (W)x.y};
+        } else {
+          const cx<double> x = St<S>::ld(Hp + c);
+          hp[c] = {(W)x.x, (W)x.y};
+        }
+      }
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          cx<W> acc = {W(0), W(0)};
+          for (int c = 0; c < 3; ++c) acc = cfma(conj(hp[3 * c + a]), H[3 * c + b], acc);
+          g[2 * (3 * a + b)] = acc.x;
+          g[2 * (3 * a + b) + 1] = acc.y;
+        }
+    }
+    double gs[18];
+    block_sum<18, W>(g, gs, shv);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 9; ++c) p_M[((int64_t)blockIdx.x * K + p) * 9 + c] = make_double2(gs[2 * c], gs[2 * c + 1]);
+  }
+}
+
+// ---- per-block reduction of the tile partials --------------------------------
+__global__ void k_block_red(BlkDev* __restrict__ blk, const int32_t* __restrict__ active, int slot,
+                            const double* __restrict__ p_s3, const int64_t* __restrict__ p_idx,
+                            const double* __restrict__ p_h2, const double2* __restrict__ p_M,
+                            double2* __restrict__ M, int K) {
+  __shared__ double shv[32 * 18];
+  __shared__ int64_t shi[32];
+  const int b = active[blockIdx.x];
+  BlkDev& B = blk[b];
+  double s3 = -1.0;
+  int64_t idx = INT64_MAX;
+  double h2 = 0.0;
+  for (int t = B.t0 + threadIdx.x; t < B.t1; t += blockDim.x) {
+    double v = p_s3[t];
+    int64_t i = p_idx[t];
+    if (v > s3 || (v == s3 && i < idx)) {
+      s3 = v;
+      idx = i;
+    }
+  }
+  // tiles are visited in a fixed order per thread; reduce deterministically
+  double hv[1] = {0.0};
+  for (int t = B.t0 + threadIdx.x; t < B.t1; t += blockDim.x) hv[0] += p_h2[t];
+  block_argmax(s3, idx, shv, shi);
+  block_sum<1>(hv, shv);
+  h2 = hv[0];
+  if (threadIdx.x == 0) {
+    B.s3max = s3;
+    B.piv = idx;
+    B.h2 = h2;
+  }
+  for (int p = 0; p <= slot; ++p) {
+    double g[18];
+    for (int c = 0; c < 18; ++c) g[c] = 0.0;
+    for (int t = B.t0 + threadIdx.x; t < B.t1; t += blockDim.x)
+      for (int c = 0; c < 9; ++c) {
+        double2 z = p_M[((int64_t)t * K + p) * 9 + c];
+        g[2 * c] += z.x;
+        g[2 * c + 1] += z.y;
+      }
+    block_sum<18>(g, shv);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 9; ++c) M[((int64_t)b * K + p) * 9 + c] = make_double2(g[2 * c], g[2 * c + 1]);
+  }
+}
+
+// ---- fibre + norm + stop test + next frequency (one CTA per block) -----------
+template <typename R, typename S, int KERN, int ROWS>
+__global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
+                             const int32_t* __restrict__ active, S* const* __restrict__ face_tab,
+                             S* const* __restrict__ fib_tab, int64_t nb, int slot,
+                             const int32_t* __restrict__ row_perm, const int32_t* __restrict__ col_perm,
+                             const double2* __restrict__ M, int32_t* __restrict__ ks, uint8_t* __restrict__ used,
+                             int K, double eps) {
+  __shared__ double shv[32 * 18];
+  __shared__ int64_t shi[32];
+  __shared__ int decision;
+  __shared__ cx<double> sP[9];
+  const int b = active[blockIdx.x];
+  BlkDev& B = blk[b];
+  if (threadIdx.x == 0) {
+    const double hn = sqrt(B.h2);
+    int dec = 0;
+    if (slot == 0 && B.h2 == 0.0)
+      dec = ST_RANK0;
+    else if (slot > 0 && hn <= kTiny * sqrt(B.norm2))
+      dec = ST_DONE;
+    else if (!(B.s3max > kPivTol * hn))
+      dec = ST_DENSE;
+    decision = dec;
+    if (dec) B.status = dec;
+  }
+  __syncthreads();
+  if (decision) return;
+  const int64_t li = B.piv / B.n, lj = B.piv - (B.piv / B.n) * B.n;
+  const int i = row_perm[B.r0 + li], j = col_perm[B.c0 + lj];
+  const S* Hd = face_tab[(int64_t)slot * nb + b];
+  if (threadIdx.x < 9) sP[threadIdx.x] = St<S>::ld(Hd + B.piv * 9 + threadIdx.x);
+  __syncthreads();
+  cx<double> Pi[9];
+  bool inv_ok = inv3(sP, Pi);
+  const int k = threadIdx.x;
+  const bool ok = k < K;
+  cx<double> f[9];
+  for (int c = 0; c < 9; ++c) f[c] = {0, 0};
+  S* fd = fib_tab[(int64_t)slot * nb + b];
+  if (ok) {
+    cx<double> E[9];
+    cx<double> is2;
+    cx<double> s = freq(v, k, is2);
+    entry<R, KERN, ROWS>(v, i, j, s, is2, E);
+    for (int p = 0; p < slot; ++p) {
+      const S* Hp = face_tab[(int64_t)p * nb + b] + B.piv * 9;
+      const S* fp = fib_tab[(int64_t)p * nb + b] + (int64_t)k * 9;
+      cx<double> hp[9], ff[9], t9[9];
+      for (int c = 0; c < 9; ++c) {
+        hp[c] = St<S>::ld(Hp + c);
+        ff[c] = St<S>::ld(fp + c);
+      }
+      mm3(hp, ff, t9);
+      for (int c = 0; c < 9; ++c) E[c] = E[c] - t9[c];
+    }
+    mm3(Pi, E, f);
+    for (int c = 0; c < 9; ++c) St<S>::st(fd + (int64_t)k * 9 + c, f[c]);
+    for (int c = 0; c < 9; ++c) f[c] = St<S>::ld(fd + (int64_t)k * 9 + c);
+  }
+  // ||f_d||^2
+  double f2[1] = {0.0};
+  if (ok)
+    for (int c = 0; c < 9; ++c) f2[0] += f[c].x * f[c].x + f[c].y * f[c].y;
+  block_sum<1>(f2, shv);
+  // cross terms: sum_p tr(M_pd N_dp), N_dp = sum_k f_d[k] f_p[k]^H
+  double cross = 0.0, self = 0.0;
+  for (int p = 0; p <= slot; ++p) {
+    double g[18];
+    for (int c = 0; c < 18; ++c) g[c] = 0.0;
+    if (ok) {
+      const S* fp = fib_tab[(int64_t)p * nb + b] + (int64_t)k * 9;
+      cx<double> ff[9];
+      for (int c = 0; c < 9; ++c) ff[c] = St<S>::ld(fp + c);
+      for (int a = 0; a < 3; ++a)
+        for (int c2 = 0; c2 < 3; ++c2) {
+          cx<double> acc = {0, 0};
+          for (int c = 0; c < 3; ++c) acc = cfma(f[3 * a + c], conj(ff[3 * c2 + c]), acc);
+          g[2 * (3 * a + c2)] = acc.x;
+          g[2 * (3 * a + c2) + 1] = acc.y;
+        }
+    }
+    block_sum<18>(g, shv);
+    if (threadIdx.x == 0) {
+      // tr(M_pd N_dp)
+      const double2* Mp = M + ((int64_t)b * K + p) * 9;
+      double tr = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+          double2 m = Mp[3 * a + c];
+          double nr = g[2 * (3 * c + a)], ni = g[2 * (3 * c + a) + 1];
+          tr += m.x * nr - m.y * ni;
+        }
+      if (p < slot)
+        cross += tr;
+      else
+        self = tr;
+    }
+  }
+  __shared__ int stop;
+  if (threadIdx.x == 0) {
+    double norm2 = B.norm2 + 2.0 * cross + self;
+    B.f2 = f2[0];
+    int st = ST_ACTIVE;
+    if (!inv_ok) {
+      st = ST_DENSE;
+    } else if (sqrt(B.h2) * sqrt(f2[0]) <= eps * sqrt(fmax(norm2, 0.0))) {
+      st = ST_DONE;  // r = d - 1: the pair just computed is discarded
+    } else {
+      B.norm2 = norm2;
+      ks[(int64_t)b * K + slot] = B.k_cur;
+      used[(int64_t)b * K + B.k_cur] = 1;
+      B.rank = slot + 1;
+      if (B.rank == K) st = ST_DENSE;
+    }
+    B.status = st;
+    stop = st != ST_ACTIVE;
+  }
+  __syncthreads();
+  if (stop) return;
+  // next frequency: argmax over unused k of sigma_3(f_d[k])
+  double s3 = -1.0;
+  int64_t idx = INT64_MAX;
+  if (ok && !used[(int64_t)b * K + k]) {
+    s3 = sigma3<double>(f);
+    idx = k;
+  }
+  block_argmax(s3, idx, shv, shi);
+  if (threadIdx.x == 0) {
+    if (!(s3 > kPivTol * sqrt(f2[0])))
+      B.status = ST_DENSE;
+    else
+      B.k_cur = (int32_t)idx;
+  }
+}
+
+// ---- dense fill of fallback blocks: D[k][i][j] = ENTRY(i, j, k) ---------------
+template <typename R, typename S, int KERN, int ROWS>
+__global__ void __launch_bounds__(kTile) k_dense_fill(EntryView v, const Tile* __restrict__ tiles,
+                                                      const BlkDev* __restrict__ blk, S* const* __restrict__ dense,
+                                                      const int32_t* __restrict__ row_perm,
+                                                      const int32_t* __restrict__ col_perm) {
+  const Tile t = tiles[blockIdx.x];
+  const BlkDev& B = blk[t.blk];
+  const int64_t e = t.start + threadIdx.x;
+  if (e >= B.m * B.n) return;
+  const int64_t li = e / B.n, lj = e - (e / B.n) * B.n;
+  const int i = row_perm[B.r0 + li], j = col_perm[B.c0 + lj];
+  cx<double> is2;
+  cx<double> s = freq(v, t.k, is2);
+  cx<double> H[9];
+  entry<R, KERN, ROWS>(v, i, j, s, is2, H);
+  S* out = dense[t.blk] + ((int64_t)t.k * B.m * B.n + e) * 9;
+  for (int c = 0; c < 9; ++c) St<S>::st(out + c, H[c]);
+}
+
+// ---- host driver ---------------------------------------------------------------
+template <typename T>
+static cudaError_t dmalloc(T** p, size_t bytes, std::vector<void*>* owner) {
+  cudaError_t e = cudaMalloc((void**)p, bytes > 0 ? bytes : 16);
+  if (e == cudaSuccess && owner) owner->push_back((void*)*p);
+  return e;
+}
+
+void free_op(OpData* d) {
+  if (!d) return;
+  for (void* p : d->allocs) cudaFree(p);
+  delete d;
+}
+
+bem_status build_apply_lists(bem_ctx* ctx, OpData* d);
+
+// storage conversion of the accepted faces and fibres (compression-time
+// float-float -> final c64 in MIXED mode)
+struct Seg {
+  const float4* src;
+  float2* dst;
+  int64_t n;
+};
+__global__ void k_convert(const Seg* __restrict__ segs) {
+  const Seg g = segs[blockIdx.x];
+  for (int64_t i = threadIdx.x; i < g.n; i += blockDim.x) {
+    const float4 v = g.src[i];
+    g.dst[i] = make_float2(v.x + v.z, v.y + v.w);
+  }
+}
+
+// R: compute type of regular far-field entries; SC: storage of faces and
+// fibres during Algorithm 1; SF: final storage used by the apply
+template <typename R, typename SC, typename SF>
+static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
+  using S = SC;
+  bem_mesh* mesh = tree->mesh;
+  bem_ctx* ctx = mesh->ctx;
+  const int K = ctx->K;
+  const int64_t nb = (int64_t)tree->blocks.size();
+  auto t_start = std::chrono::steady_clock::now();
+  if (tree->kernel == BEM_DL && tree->rows == BEM_ROWS_NODES) {
+    bem_status s = ensure_rigid_body(mesh, st);
+    if (s != BEM_OK) return s;
+  }
+  EntryView v = make_view(mesh);
+  d->K = K;
+  d->prec = ctx->opt.precision;
+  d->rows = tree->rows;
+  d->kernel = tree->kernel;
+  d->n_blocks = nb;
+  d->n_rows = tree->n_rows;
+  d->n_cols = tree->n_cols;
+  d->h_blk.resize(nb);
+  int64_t n_tiles_all = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const BlockDesc& bd = tree->blocks[b];
+    BlkDev& B = d->h_blk[b];
+    std::memset(&B, 0, sizeof(B));
+    B.r0 = bd.r0;
+    B.m = bd.m;
+    B.c0 = bd.c0;
+    B.n = bd.n;
+    B.far = bd.far;
+    B.status = ST_ACTIVE;
+    B.k_cur = 0;  // k_1 = 0
+    n_tiles_all += (bd.m * bd.n + kTile - 1) / kTile;
+  }
+  std::vector<void*>* own = &d->allocs;
+  GCQ_CUDA(ctx, dmalloc(&d->d_blk, sizeof(BlkDev) * nb, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_row_perm, sizeof(int32_t) * tree->n_rows, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_col_perm, sizeof(int32_t) * tree->n_cols, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_face, sizeof(void*) * nb * K, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_fib, sizeof(void*) * nb * K, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_dense, sizeof(void*) * nb, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_ks, sizeof(int32_t) * nb * K, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_used, nb * K, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_M, sizeof(double2) * nb * K * 9, own));
+  GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_blk, d->h_blk.data(), sizeof(BlkDev) * nb, cudaMemcpyHostToDevice, st));
+  GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_row_perm, tree->row_perm.data(), sizeof(int32_t) * tree->n_rows,
+                                cudaMemcpyHostToDevice, st));
+  GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_col_perm, tree->col_perm.data(), sizeof(int32_t) * tree->n_cols,
+                                cudaMemcpyHostToDevice, st));
+  GCQ_CUDA(ctx, cudaMemsetAsync(d->d_face, 0, sizeof(void*) * nb * K, st));
+  GCQ_CUDA(ctx, cudaMemsetAsync(d->d_fib, 0, sizeof(void*) * nb * K, st));
+  GCQ_CUDA(ctx, cudaMemsetAsync(d->d_dense, 0, sizeof(void*) * nb, st));
+  GCQ_CUDA(ctx, cudaMemsetAsync(d->d_ks, 0xff, sizeof(int32_t) * nb * K, st));
+  GCQ_CUDA(ctx, cudaMemsetAsync(d->d_used, 0, nb * K, st));
+  d->h_face.assign(nb * K, nullptr);
+  d->h_fib.assign(nb * K, nullptr);
+  d->h_dense.assign(nb, nullptr);
+  // per-iteration scratch (freed at the end)
+  std::vector<void*> scratch;
+  Tile* d_tiles = nullptr;
+  int32_t* d_active = nullptr;
+  double *p_s3 = nullptr, *p_h2 = nullptr;
+  int64_t* p_idx = nullptr;
+  double2* p_M = nullptr;
+  GCQ_CUDA(ctx, dmalloc(&d_tiles, sizeof(Tile) * n_tiles_all, &scratch));
+  GCQ_CUDA(ctx, dmalloc(&d_active, sizeof(int32_t) * nb, &scratch));
+  GCQ_CUDA(ctx, dmalloc(&p_s3, sizeof(double) * n_tiles_all, &scratch));
+  GCQ_CUDA(ctx, dmalloc(&p_h2, sizeof(double) * n_tiles_all, &scratch));
+  GCQ_CUDA(ctx, dmalloc(&p_idx, sizeof(int64_t) * n_tiles_all, &scratch));
+  GCQ_CUDA(ctx, dmalloc(&p_M, sizeof(double2) * n_tiles_all * K * 9, &scratch));
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  float t_ent = 0.f;
+  std::vector<Tile> tiles;
+  std::vector<int32_t> active;
+  std::vector<void*> slot_chunks;   // compression-time storage when SC != SF
+  bem_status result = BEM_OK;
+  for (int slot = 0; slot < K && result == BEM_OK; ++slot) {
+    active.clear();
+    tiles.clear();
+    size_t face_bytes = 0, fib_bytes = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+      BlkDev& B = d->h_blk[b];
+      if (B.status != ST_ACTIVE) continue;
+      active.push_back((int32_t)b);
+      B.t0 = (int32_t)tiles.size();
+      for (int64_t s0 = 0; s0 < B.m * B.n; s0 += kTile) tiles.push_back(Tile{(int32_t)b, -1, s0});
+      B.t1 = (int32_t)tiles.size();
+      face_bytes += sizeof(S) * 9 * B.m * B.n;
+      fib_bytes += sizeof(S) * 9 * K;
+    }
+    if (active.empty()) break;
+    // slot storage: one chunk for all faces + fibres of this slot
+    char* chunk = nullptr;
+    if (dmalloc(&chunk, face_bytes + fib_bytes, std::is_same<SC, SF>::value ? own : &slot_chunks) != cudaSuccess) {
+      result = set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for 3D-ACA faces");
+      break;
+    }
+    size_t off = 0;
+    for (int32_t b : active) {
+      const BlkDev& B = d->h_blk[b];
+      d->h_face[(int64_t)slot * nb + b] = chunk + off;
+      off += sizeof(S) * 9 * B.m * B.n;
+    }
+    for (int32_t b : active) {
+      d->h_fib[(int64_t)slot * nb + b] = chunk + off;
+      off += sizeof(S) * 9 * K;
+    }
+    GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_face + (int64_t)slot * nb, d->h_face.data() + (int64_t)slot * nb,
+                                  sizeof(void*) * nb, cudaMemcpyHostToDevice, st));
+    GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_fib + (int64_t)slot * nb, d->h_fib.data() + (int64_t)slot * nb,
+                                  sizeof(void*) * nb, cudaMemcpyHostToDevice, st));
+    GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_blk, d->h_blk.data(), sizeof(BlkDev) * nb, cudaMemcpyHostToDevice, st));
+    GCQ_CUDA(ctx, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, st));
+    GCQ_CUDA(ctx, cudaMemcpyAsync(d_active, active.data(), sizeof(int32_t) * active.size(), cudaMemcpyHostToDevice,
+                                  st));
+    cudaEventRecord(ev0, st);
+    GCQ_DISPATCH(d->kernel, d->rows,
+                 (k_face<R, SC, KK, RR><<<(unsigned)tiles.size(), kTile, 0, st>>>(
+                     v, d_tiles, d->d_blk, (S* const*)d->d_face, (S* const*)d->d_fib, nb, slot, d->d_row_perm,
+                     d->d_col_perm, p_s3, p_idx, p_h2, p_M, K)));
+    GCQ_CUDA(ctx, cudaGetLastError());
+    k_block_red<<<(unsigned)active.size(), 256, 0, st>>>(d->d_blk, d_active, slot, p_s3, p_idx, p_h2, p_M, d->d_M,
+                                                         K);
+    GCQ_CUDA(ctx, cudaGetLastError());
+    const int tb = std::max(32, ((K + 31) / 32) * 32);
+    GCQ_DISPATCH(d->kernel, d->rows,
+                 (k_fibre_step<R, S, KK, RR><<<(unsigned)active.size(), tb, 0, st>>>(
+                     v, d->d_blk, d_active, (S* const*)d->d_face, (S* const*)d->d_fib, nb, slot, d->d_row_perm,
+                     d->d_col_perm, d->d_M, d->d_ks, d->d_used, K, ctx->opt.eps)));
+    GCQ_CUDA(ctx, cudaGetLastError());
+    cudaEventRecord(ev1, st);
+    GCQ_CUDA(ctx, cudaMemcpyAsync(d->h_blk.data(), d->d_blk, sizeof(BlkDev) * nb, cudaMemcpyDeviceToHost, st));
+    GCQ_CUDA(ctx, cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    t_ent += ms;
+    for (int32_t b : active) d->entries += d->h_blk[b].m * d->h_blk[b].n + K;
+  }
+  // dense fallback blocks: all K faces
+  if (result == BEM_OK) {
+    tiles.clear();
+    for (int64_t b = 0; b < nb; ++b) {
+      BlkDev& B = d->h_blk[b];
+      if (B.status == ST_ACTIVE) B.status = ST_DENSE;   // cannot happen (rank == K -> dense)
+      if (B.status != ST_DENSE) continue;
+      B.rank = 0;
+      void* p = nullptr;
+      if (dmalloc(&p, sizeof(SF) * 9 * K * B.m * B.n, own) != cudaSuccess) {
+        result = set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for dense blocks");
+        break;
+      }
+      d->h_dense[b] = p;
+      for (int k = 0; k < K; ++k)
+        for (int64_t s0 = 0; s0 < B.m * B.n; s0 += kTile) tiles.push_back(Tile{(int32_t)b, k, s0});
+      d->entries += (int64_t)K * B.m * B.n;
+    }
+    if (result == BEM_OK && !tiles.empty()) {
+      Tile* d_t2 = nullptr;
+      GCQ_CUDA(ctx, dmalloc(&d_t2, sizeof(Tile) * tiles.size(), &scratch));
+      GCQ_CUDA(ctx, cudaMemcpyAsync(d_t2, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, st));
+      GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_dense, d->h_dense.data(), sizeof(void*) * nb, cudaMemcpyHostToDevice, st));
+      GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_blk, d->h_blk.data(), sizeof(BlkDev) * nb, cudaMemcpyHostToDevice, st));
+      cudaEventRecord(ev0, st);
+      // grid may exceed 2^31-1 CTAs only for > 5e11 entries: not reachable
+      GCQ_DISPATCH(d->kernel, d->rows,
+                   (k_dense_fill<R, SF, KK, RR><<<(unsigned)tiles.size(), kTile, 0, st>>>(
+                       v, d_t2, d->d_blk, (SF* const*)d->d_dense, d->d_row_perm, d->d_col_perm)));
+      GCQ_CUDA(ctx, cudaGetLastError());
+      cudaEventRecord(ev1, st);
+      GCQ_CUDA(ctx, cudaStreamSynchronize(st));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev0, ev1);
+      t_ent += ms;
+    }
+  }
+  // final storage of the accepted pairs
+  if (result == BEM_OK && !std::is_same<SC, SF>::value) {
+    size_t bytes = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+      const BlkDev& B = d->h_blk[b];
+      if (B.status == ST_DONE) bytes += sizeof(SF) * 9 * (size_t)B.rank * (B.m * B.n + K);
+    }
+    char* fin = nullptr;
+    if (dmalloc(&fin, bytes, own) != cudaSuccess) {
+      result = set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for the compressed tensor");
+    } else {
+      std::vector<Seg> segs;
+      size_t off = 0;
+      for (int64_t b = 0; b < nb; ++b) {
+        const BlkDev& B = d->h_blk[b];
+        for (int p = 0; p < K; ++p) {
+          void*& hf = d->h_face[(int64_t)p * nb + b];
+          void*& hb = d->h_fib[(int64_t)p * nb + b];
+          if (B.status != ST_DONE || p >= B.rank) {
+            hf = nullptr;
+            hb = nullptr;
+            continue;
+          }
+          segs.push_back(Seg{(const float4*)hf, (float2*)(fin + off), 9 * B.m * B.n});
+          hf = fin + off;
+          off += sizeof(SF) * 9 * B.m * B.n;
+          segs.push_back(Seg{(const float4*)hb, (float2*)(fin + off), 9 * (int64_t)K});
+          hb = fin + off;
+          off += sizeof(SF) * 9 * K;
+        }
+      }
+      if (!segs.empty()) {
+        Seg* d_segs = nullptr;
+        GCQ_CUDA(ctx, dmalloc(&d_segs, sizeof(Seg) * segs.size(), &scratch));
+        GCQ_CUDA(ctx, cudaMemcpyAsync(d_segs, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice, st));
+        k_convert<<<(unsigned)segs.size(), 256, 0, st>>>(d_segs);
+        GCQ_CUDA(ctx, cudaGetLastError());
+      }
+      GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_face, d->h_face.data(), sizeof(void*) * nb * K, cudaMemcpyHostToDevice, st));
+      GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_fib, d->h_fib.data(), sizeof(void*) * nb * K, cudaMemcpyHostToDevice, st));
+      GCQ_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+  }
+  for (void* p : slot_chunks) cudaFree(p);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  for (void* p : scratch) cudaFree(p);
+  if (result != BEM_OK) return result;
+  GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_blk, d->h_blk.data(), sizeof(BlkDev) * nb, cudaMemcpyHostToDevice, st));
+  bem_status s = build_apply_lists(ctx, d);
+  if (s != BEM_OK) return s;
+  GCQ_CUDA(ctx, cudaStreamSynchronize(st));
+  d->t_entries_ms = t_ent;
+  d->t_compress_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  return BEM_OK;
+}
+
+bem_status compress(bem_tree* tree, cudaStream_t st, OpData** out) {
+  auto* d = new (std::nothrow) OpData;
+  if (!d) return set_err(tree->mesh->ctx, BEM_ERR_OOM, "bem_op_compress: host allocation");
+  bem_status s = tree->mesh->ctx->opt.precision == BEM_FP64 ? compress_t<double, double2, double2>(tree, st, d)
+                                                            : compress_t<float, float4, float2>(tree, st, d);
+  if (s != BEM_OK) {
+    cudaStreamSynchronize(st);
+    free_op(d);
+    return s;
+  }
+  *out = d;
+  return BEM_OK;
+}
+
+}  // namespace gcq

@@ -1,0 +1,443 @@
+// Apply of the 3D-ACA compressed tensor (Eq. (3.15)) to the vectors of all
+// K frequencies, dense reconstruction for checks, statistics, and the CQ
+// transforms (Sec. 2.4 with uniform steps).
+//
+// Batched:     Y_k = sum_blocks sum_p H_p (I (x) f_p[k]) X_k       (+ dense blocks D_k X_k)
+// Contracted:  y   = sum_blocks sum_p H_p z_p,  z_p = sum_k (I (x) f_p[k]) X_k
+// Block rows/columns are in cluster order; X and Y are in the original
+// ordering (row_perm / col_perm gather and scatter).
+#pragma once
+
+namespace gcq {
+
+constexpr int kAT = 16;   // rows per apply tile
+constexpr int kAK = 16;   // frequencies per apply tile
+constexpr int kAJ = 8;    // columns per smem chunk
+
+template <typename A>
+__device__ __forceinline__ void atomic_add_c(A* p, cx<A> v) {
+  atomicAdd(p, v.x);
+  atomicAdd(p + 1, v.y);
+}
+
+template <typename S, typename A>
+struct Ld;
+template <>
+struct Ld<double2, double> {
+  static __device__ __forceinline__ cx<double> ld(const double2* p) {
+    double2 v = *p;
+    return {v.x, v.y};
+  }
+};
+template <>
+struct Ld<float2, float> {
+  static __device__ __forceinline__ cx<float> ld(const float2* p) {
+    float2 v = *p;
+    return {v.x, v.y};
+  }
+};
+
+// items: (block, row tile, k tile, 0)
+template <typename S, typename A>
+__global__ void __launch_bounds__(kAT* kAK) k_apply_aca(const BlkDev* __restrict__ blk, const int4* __restrict__ items,
+                                                        S* const* __restrict__ face_tab, S* const* __restrict__ fib_tab,
+                                                        int64_t nb, const int32_t* __restrict__ row_perm,
+                                                        const int32_t* __restrict__ col_perm, const S* __restrict__ X,
+                                                        S* __restrict__ Y, int K, int64_t n_rows, int64_t n_cols) {
+  __shared__ cx<A> sH[kAT][kAJ][9];
+  __shared__ cx<A> sZ[kAJ][kAK][3];
+  __shared__ cx<A> sF[kAK][9];
+  const int4 it = items[blockIdx.x];
+  const BlkDev& B = blk[it.x];
+  const int ti = threadIdx.x / kAK, tk = threadIdx.x % kAK;
+  const int64_t li = (int64_t)it.y * kAT + ti;
+  const int k = it.z * kAK + tk;
+  cx<A> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int p = 0; p < B.rank; ++p) {
+    const S* H = face_tab[(int64_t)p * nb + it.x];
+    const S* f = fib_tab[(int64_t)p * nb + it.x];
+    __syncthreads();
+    for (int c = threadIdx.x; c < kAK * 9; c += blockDim.x) {
+      const int kk = it.z * kAK + c / 9;
+      sF[c / 9][c % 9] = kk < K ? Ld<S, A>::ld(f + (int64_t)kk * 9 + c % 9) : cx<A>{0, 0};
+    }
+    for (int64_t j0 = 0; j0 < B.n; j0 += kAJ) {
+      __syncthreads();
+      for (int c = threadIdx.x; c < kAT * kAJ * 9; c += blockDim.x) {
+        const int r = c / (kAJ * 9), rem = c % (kAJ * 9), jj = rem / 9, q = rem % 9;
+        const int64_t gi = (int64_t)it.y * kAT + r, gj = j0 + jj;
+        sH[r][jj][q] = (gi < B.m && gj < B.n) ? Ld<S, A>::ld(H + (gi * B.n + gj) * 9 + q) : cx<A>{0, 0};
+      }
+      for (int c = threadIdx.x; c < kAJ * kAK; c += blockDim.x) {
+        const int kk = c / kAJ, jj = c % kAJ;
+        const int64_t gj = j0 + jj;
+        const int kg = it.z * kAK + kk;
+        cx<A> x[3] = {{0, 0}, {0, 0}, {0, 0}};
+        if (gj < B.n && kg < K) {
+          const S* xp = X + ((int64_t)kg * n_cols + col_perm[B.c0 + gj]) * 3;
+          for (int b = 0; b < 3; ++b) x[b] = Ld<S, A>::ld(xp + b);
+        }
+        for (int a = 0; a < 3; ++a) {
+          cx<A> z = {0, 0};
+          for (int b = 0; b < 3; ++b) z = cfma(sF[kk][3 * a + b], x[b], z);
+          sZ[jj][kk][a] = z;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int jj = 0; jj < kAJ; ++jj)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const cx<A> z = sZ[jj][tk][b];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) acc[a] = cfma(sH[ti][jj][3 * a + b], z, acc[a]);
+        }
+    }
+  }
+  if (li < B.m && k < K) {
+    A* y = (A*)(Y + ((int64_t)k * n_rows + row_perm[B.r0 + li]) * 3);
+    for (int a = 0; a < 3; ++a) atomic_add_c(y + 2 * a, acc[a]);
+  }
+}
+
+// dense fallback blocks: Y_k[rows] += D_k X_k[cols]; CTA per (block, k), warp per row
+template <typename S, typename A>
+__global__ void k_apply_dense(const BlkDev* __restrict__ blk, const int32_t* __restrict__ list,
+                              S* const* __restrict__ dense, const int32_t* __restrict__ row_perm,
+                              const int32_t* __restrict__ col_perm, const S* __restrict__ X, S* __restrict__ Y, int K,
+                              int64_t n_rows, int64_t n_cols, int contracted) {
+  const int b = list[blockIdx.x];
+  const int k = blockIdx.y;
+  const BlkDev& B = blk[b];
+  const S* D = dense[b] + (int64_t)k * B.m * B.n * 9;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t li = w; li < B.m; li += nw) {
+    cx<A> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int64_t lj = lane; lj < B.n; lj += 32) {
+      const S* xp = X + ((int64_t)k * n_cols + col_perm[B.c0 + lj]) * 3;
+      cx<A> x[3];
+      for (int c = 0; c < 3; ++c) x[c] = Ld<S, A>::ld(xp + c);
+      const S* d = D + (li * B.n + lj) * 9;
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) acc[a] = cfma(Ld<S, A>::ld(d + 3 * a + c), x[c], acc[a]);
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[a].x += __shfl_down_sync(0xffffffffu, acc[a].x, o);
+        acc[a].y += __shfl_down_sync(0xffffffffu, acc[a].y, o);
+      }
+    if (lane == 0) {
+      const int64_t row = row_perm[B.r0 + li];
+      A* y = (A*)(Y + (contracted ? row * 3 : ((int64_t)k * n_rows + row) * 3));
+      for (int a = 0; a < 3; ++a) atomic_add_c(y + 2 * a, acc[a]);
+    }
+  }
+}
+
+// contracted: z[b][p][lj] = sum_k f_p[k] x_k[col(lj)]   (thread per (b, p, lj))
+template <typename S, typename A>
+__global__ void k_contract_z(const BlkDev* __restrict__ blk, const int4* __restrict__ items,
+                             S* const* __restrict__ fib_tab, int64_t nb, const int64_t* __restrict__ zoff,
+                             const int32_t* __restrict__ col_perm, const S* __restrict__ X, cx<A>* __restrict__ Z,
+                             int K, int64_t n_cols) {
+  const int4 it = items[blockIdx.x];   // (block, face, column chunk start / 128, aca index)
+  const BlkDev& B = blk[it.x];
+  const int64_t lj = (int64_t)it.z * blockDim.x + threadIdx.x;
+  if (lj >= B.n) return;
+  const S* f = fib_tab[(int64_t)it.y * nb + it.x];
+  const int64_t col = col_perm[B.c0 + lj];
+  cx<A> z[3] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int k = 0; k < K; ++k) {
+    const S* xp = X + ((int64_t)k * n_cols + col) * 3;
+    cx<A> x[3];
+    for (int c = 0; c < 3; ++c) x[c] = Ld<S, A>::ld(xp + c);
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) z[a] = cfma(Ld<S, A>::ld(f + (int64_t)k * 9 + 3 * a + c), x[c], z[a]);
+  }
+  cx<A>* zp = Z + zoff[it.w] + ((int64_t)it.y * B.n + lj) * 3;
+  for (int a = 0; a < 3; ++a) zp[a] = z[a];
+}
+
+// contracted: y[row(li)] += sum_p sum_lj H_p[li][lj] z_p[lj]   (warp per row)
+template <typename S, typename A>
+__global__ void k_contract_apply(const BlkDev* __restrict__ blk, const int32_t* __restrict__ list,
+                                 S* const* __restrict__ face_tab, int64_t nb, const int64_t* __restrict__ zoff,
+                                 const int32_t* __restrict__ row_perm, const cx<A>* __restrict__ Z,
+                                 S* __restrict__ Y) {
+  const int ai = blockIdx.x;
+  const int b = list[ai];
+  const BlkDev& B = blk[b];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t li = (int64_t)blockIdx.y * nw + w; li < B.m; li += (int64_t)gridDim.y * nw) {
+    cx<A> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int p = 0; p < B.rank; ++p) {
+      const S* H = face_tab[(int64_t)p * nb + b];
+      const cx<A>* z = Z + zoff[ai] + (int64_t)p * B.n * 3;
+      for (int64_t lj = lane; lj < B.n; lj += 32) {
+        const S* h = H + (li * B.n + lj) * 9;
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) acc[a] = cfma(Ld<S, A>::ld(h + 3 * a + c), z[lj * 3 + c], acc[a]);
+      }
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[a].x += __shfl_down_sync(0xffffffffu, acc[a].x, o);
+        acc[a].y += __shfl_down_sync(0xffffffffu, acc[a].y, o);
+      }
+    if (lane == 0) {
+      A* y = (A*)(Y + (int64_t)row_perm[B.r0 + li] * 3);
+      for (int a = 0; a < 3; ++a) atomic_add_c(y + 2 * a, acc[a]);
+    }
+  }
+}
+
+bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
+  std::vector<int4> items;
+  std::vector<int32_t> dense, aca;
+  std::vector<int64_t> zoff;
+  std::vector<int4> zitems;   // (block, face, 128-column chunk, aca index)
+  int64_t z = 0;
+  const int nkt = (d->K + kAK - 1) / kAK;
+  for (int64_t b = 0; b < d->n_blocks; ++b) {
+    const BlkDev& B = d->h_blk[b];
+    if (B.status == ST_DENSE) dense.push_back((int32_t)b);
+    if (B.status == ST_DONE && B.rank > 0) {
+      for (int p = 0; p < B.rank; ++p)
+        for (int64_t c = 0; c * 128 < B.n; ++c) zitems.push_back(make_int4((int)b, p, (int)c, (int)aca.size()));
+      aca.push_back((int32_t)b);
+      zoff.push_back(z);
+      z += (int64_t)B.rank * B.n * 3;
+      for (int64_t rt = 0; rt * kAT < B.m; ++rt)
+        for (int kt = 0; kt < nkt; ++kt) items.push_back(make_int4((int)b, (int)rt, kt, 0));
+    }
+  }
+  std::vector<void*>* own = &d->allocs;
+  d->n_apply_items = (int64_t)items.size();
+  d->n_dense = (int64_t)dense.size();
+  d->n_aca = (int64_t)aca.size();
+  d->z_elems = z;
+  GCQ_CUDA(ctx, dmalloc(&d->d_apply_items, sizeof(int4) * std::max<size_t>(1, items.size()), own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_dense_list, sizeof(int32_t) * std::max<size_t>(1, dense.size()), own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_aca_list, sizeof(int32_t) * std::max<size_t>(1, aca.size()), own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_zoff, sizeof(int64_t) * std::max<size_t>(1, zoff.size()), own));
+  d->n_zitems = (int64_t)zitems.size();
+  GCQ_CUDA(ctx, dmalloc(&d->d_zitems, sizeof(int4) * std::max<size_t>(1, zitems.size()), own));
+  if (!zitems.empty())
+    GCQ_CUDA(ctx, cudaMemcpy(d->d_zitems, zitems.data(), sizeof(int4) * zitems.size(), cudaMemcpyHostToDevice));
+  const size_t zb = (d->prec == BEM_FP64 ? sizeof(double2) : sizeof(float2)) * std::max<int64_t>(1, z);
+  GCQ_CUDA(ctx, dmalloc(&d->d_z, zb, own));
+  if (!items.empty())
+    GCQ_CUDA(ctx, cudaMemcpy(d->d_apply_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+  if (!dense.empty())
+    GCQ_CUDA(ctx, cudaMemcpy(d->d_dense_list, dense.data(), sizeof(int32_t) * dense.size(), cudaMemcpyHostToDevice));
+  if (!aca.empty()) {
+    GCQ_CUDA(ctx, cudaMemcpy(d->d_aca_list, aca.data(), sizeof(int32_t) * aca.size(), cudaMemcpyHostToDevice));
+    GCQ_CUDA(ctx, cudaMemcpy(d->d_zoff, zoff.data(), sizeof(int64_t) * zoff.size(), cudaMemcpyHostToDevice));
+  }
+  // algorithmic bytes of one batched apply: stored operator + X + Y
+  const int64_t es = d->prec == BEM_FP64 ? 16 : 8;
+  int64_t stored = 0;
+  for (int64_t b = 0; b < d->n_blocks; ++b) {
+    const BlkDev& B = d->h_blk[b];
+    if (B.status == ST_DENSE) stored += (int64_t)d->K * B.m * B.n * 9 * es;
+    if (B.status == ST_DONE) stored += (int64_t)B.rank * (B.m * B.n + d->K) * 9 * es;
+  }
+  d->apply_bytes = stored + (int64_t)d->K * (d->n_rows + d->n_cols) * 3 * es;
+  return BEM_OK;
+}
+
+template <typename S, typename A>
+static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaStream_t st) {
+  OpData* d = op->d;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  const S* X = (const S*)Xv;
+  S* Y = (S*)Yv;
+  const int64_t ny = mode == BEM_APPLY_BATCHED ? (int64_t)d->K * d->n_rows * 3 : d->n_rows * 3;
+  GCQ_CUDA(ctx, cudaMemsetAsync(Y, 0, sizeof(S) * ny, st));
+  if (mode == BEM_APPLY_BATCHED) {
+    if (d->n_apply_items > 0) {
+      k_apply_aca<S, A><<<(unsigned)d->n_apply_items, kAT * kAK, 0, st>>>(
+          d->d_blk, (const int4*)d->d_apply_items, (S* const*)d->d_face, (S* const*)d->d_fib, d->n_blocks,
+          d->d_row_perm, d->d_col_perm, X, Y, d->K, d->n_rows, d->n_cols);
+      GCQ_CUDA(ctx, cudaGetLastError());
+    }
+    if (d->n_dense > 0) {
+      dim3 g((unsigned)d->n_dense, (unsigned)d->K);
+      k_apply_dense<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense, d->d_row_perm,
+                                             d->d_col_perm, X, Y, d->K, d->n_rows, d->n_cols, 0);
+      GCQ_CUDA(ctx, cudaGetLastError());
+    }
+    return BEM_OK;
+  }
+  // contracted
+  if (d->n_zitems > 0) {
+    k_contract_z<S, A><<<(unsigned)d->n_zitems, 128, 0, st>>>(d->d_blk, (const int4*)d->d_zitems,
+                                                              (S* const*)d->d_fib, d->n_blocks, d->d_zoff,
+                                                              d->d_col_perm, X, (cx<A>*)d->d_z, d->K, d->n_cols);
+    GCQ_CUDA(ctx, cudaGetLastError());
+    dim3 g((unsigned)d->n_aca, 8);
+    k_contract_apply<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_aca_list, (S* const*)d->d_face, d->n_blocks, d->d_zoff,
+                                              d->d_row_perm, (const cx<A>*)d->d_z, Y);
+    GCQ_CUDA(ctx, cudaGetLastError());
+  }
+  if (d->n_dense > 0) {
+    dim3 g((unsigned)d->n_dense, (unsigned)d->K);
+    k_apply_dense<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense, d->d_row_perm,
+                                           d->d_col_perm, X, Y, d->K, d->n_rows, d->n_cols, 1);
+    GCQ_CUDA(ctx, cudaGetLastError());
+  }
+  return BEM_OK;
+}
+
+bem_status apply(bem_op* op, int mode, const void* X, void* Y, cudaStream_t st) {
+  return op->d->prec == BEM_FP64 ? apply_t<double2, double>(op, mode, X, Y, st)
+                                 : apply_t<float2, float>(op, mode, X, Y, st);
+}
+
+// ---- dense reconstruction: out[(i * n_cols + j) * K + k] -----------------------
+template <typename S>
+__global__ void k_op_dense(const BlkDev* __restrict__ blk, const Tile* __restrict__ tiles,
+                           S* const* __restrict__ face_tab, S* const* __restrict__ fib_tab,
+                           S* const* __restrict__ dense, int64_t nb, const int32_t* __restrict__ row_perm,
+                           const int32_t* __restrict__ col_perm, S* __restrict__ out, int K, int64_t n_cols) {
+  const Tile t = tiles[blockIdx.x];
+  const BlkDev& B = blk[t.blk];
+  const int64_t e = t.start + threadIdx.x;
+  if (e >= B.m * B.n) return;
+  const int64_t li = e / B.n, lj = e - (e / B.n) * B.n;
+  const int64_t i = row_perm[B.r0 + li], j = col_perm[B.c0 + lj];
+  S* o = out + (i * n_cols + j) * K * 9;
+  for (int k = 0; k < K; ++k) {
+    cx<double> v[9];
+    for (int c = 0; c < 9; ++c) v[c] = {0, 0};
+    if (B.status == ST_DENSE) {
+      const S* dp = dense[t.blk] + ((int64_t)k * B.m * B.n + e) * 9;
+      for (int c = 0; c < 9; ++c) v[c] = St<S>::ld(dp + c);
+    } else if (B.status == ST_DONE) {
+      for (int p = 0; p < B.rank; ++p) {
+        cx<double> h[9], f[9], hf[9];
+        const S* hp = face_tab[(int64_t)p * nb + t.blk] + e * 9;
+        const S* fp = fib_tab[(int64_t)p * nb + t.blk] + (int64_t)k * 9;
+        for (int c = 0; c < 9; ++c) {
+          h[c] = St<S>::ld(hp + c);
+          f[c] = St<S>::ld(fp + c);
+        }
+        mm3(h, f, hf);
+        for (int c = 0; c < 9; ++c) v[c] = v[c] + hf[c];
+      }
+    }
+    for (int c = 0; c < 9; ++c) St<S>::st(o + (int64_t)k * 9 + c, v[c]);
+  }
+}
+
+template <typename S>
+static bem_status op_dense_t(bem_op* op, void* out, cudaStream_t st) {
+  OpData* d = op->d;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  std::vector<Tile> tiles;
+  for (int64_t b = 0; b < d->n_blocks; ++b) {
+    const BlkDev& B = d->h_blk[b];
+    for (int64_t s0 = 0; s0 < B.m * B.n; s0 += kTile) tiles.push_back(Tile{(int32_t)b, -1, s0});
+  }
+  Tile* dt = nullptr;
+  GCQ_CUDA(ctx, cudaMalloc(&dt, sizeof(Tile) * tiles.size()));
+  cudaError_t e = cudaMemcpyAsync(dt, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_op_dense<S><<<(unsigned)tiles.size(), kTile, 0, st>>>(d->d_blk, dt, (S* const*)d->d_face, (S* const*)d->d_fib,
+                                                           (S* const*)d->d_dense, d->n_blocks, d->d_row_perm,
+                                                           d->d_col_perm, (S*)out, d->K, d->n_cols);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dt);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "bem_op_dense");
+  return BEM_OK;
+}
+
+bem_status op_dense(bem_op* op, void* out, cudaStream_t st) {
+  return op->d->prec == BEM_FP64 ? op_dense_t<double2>(op, out, st) : op_dense_t<float2>(op, out, st);
+}
+
+bem_status op_stats(const bem_op* op, bem_op_stats* s) {
+  const OpData* d = op->d;
+  std::memset(s, 0, sizeof(*s));
+  const double es = d->prec == BEM_FP64 ? 16.0 : 8.0;
+  s->n_blocks = d->n_blocks;
+  s->rank_min = INT64_MAX;
+  double rank_sum = 0.0;
+  for (const BlkDev& B : d->h_blk) {
+    s->n_far += B.far;
+    if (B.status == ST_DENSE) {
+      s->n_dense++;
+      s->stored_bytes += es * 9.0 * d->K * B.m * B.n;
+    } else if (B.status == ST_RANK0) {
+      s->n_rank0++;
+    } else {
+      s->n_aca++;
+      s->rank_min = std::min<int64_t>(s->rank_min, B.rank);
+      s->rank_max = std::max<int64_t>(s->rank_max, B.rank);
+      rank_sum += B.rank;
+      s->stored_bytes += es * 9.0 * B.rank * ((double)B.m * B.n + d->K);
+    }
+  }
+  if (s->n_aca == 0) s->rank_min = 0;
+  s->rank_mean = s->n_aca ? rank_sum / s->n_aca : 0.0;
+  s->dense_bytes = es * 9.0 * d->K * (double)d->n_rows * (double)d->n_cols;
+  s->compression_rate = s->stored_bytes / s->dense_bytes;
+  s->entries_evaluated = d->entries;
+  s->t_entries_ms = d->t_entries_ms;
+  s->t_compress_ms = d->t_compress_ms;
+  s->apply_bytes = d->apply_bytes;
+  return BEM_OK;
+}
+
+bem_status op_blocks(const bem_op* op, int64_t* info) {
+  const OpData* d = op->d;
+  std::vector<int32_t> ks((size_t)d->n_blocks * d->K);
+  cudaError_t e = cudaMemcpy(ks.data(), d->d_ks, sizeof(int32_t) * ks.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(op->tree->mesh->ctx, e, "bem_op_blocks");
+  for (int64_t b = 0; b < d->n_blocks; ++b) {
+    const BlkDev& B = d->h_blk[b];
+    info[4 * b + 0] = B.status == ST_DENSE ? 1 : (B.status == ST_RANK0 ? 2 : 0);
+    info[4 * b + 1] = B.status == ST_DENSE ? d->K : B.rank;
+    info[4 * b + 2] = B.status == ST_DONE && B.rank > 0 ? ks[(size_t)b * d->K] : -1;
+    info[4 * b + 3] = 0;
+  }
+  return BEM_OK;
+}
+
+// ---- CQ transforms (direct scaled DFT over L = N + 1 levels) ------------------
+__global__ void k_cq(int L, double lnlam, int64_t nvec, const double2* __restrict__ in, double2* __restrict__ out,
+                     int inverse) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int n = blockIdx.y;
+  if (v >= nvec) return;
+  double ar = 0.0, ai = 0.0;
+  for (int j = 0; j < L; ++j) {
+    // phase 2 pi (n j mod L) / L, exact integer reduction
+    const int64_t r = ((int64_t)n * j) % L;
+    double sn, cs;
+    sincospi(2.0 * (double)r / (double)L, &sn, &cs);
+    if (!inverse) sn = -sn;
+    const double sc = inverse ? 1.0 : exp(lnlam * j);
+    const double2 x = in[(int64_t)j * nvec + v];
+    ar += sc * (x.x * cs - x.y * sn);
+    ai += sc * (x.x * sn + x.y * cs);
+  }
+  if (inverse) {
+    const double sc = exp(-lnlam * n) / L;
+    ar *= sc;
+    ai *= sc;
+  }
+  out[(int64_t)n * nvec + v] = make_double2(ar, ai);
+}
+
+bem_status cq_transform(int N, int64_t nvec, const void* in, void* out, bool inverse, cudaStream_t st) {
+  const int L = N + 1;
+  const double lnlam = std::log(1e-10) / (2.0 * N);
+  dim3 g((unsigned)((nvec + 127) / 128), (unsigned)L);
+  k_cq<<<g, 128, 0, st>>>(L, lnlam, nvec, (const double2*)in, (double2*)out, inverse ? 1 : 0);
+  return cudaGetLastError() == cudaSuccess ? BEM_OK : BEM_ERR_CUDA;
+}
+
+}  // namespace gcq

@@ -1,0 +1,345 @@
+// FP32 evaluation of the collocation entries (MIXED precision).
+//
+// Same rules and singular treatments as the FP64 functions of entry.cuh
+// (Sec. 2.3; Duffy for x on the element, CPV and free term for centroid
+// rows, rigid-body static diagonal for node rows), with every quadrature
+// point in FP32: B300 issues about 2 FP64 FMA per clock per SM against 128
+// FP32, and the near/singular rules (64-768 points) are the costliest
+// entries.  Accuracy is kept by (i) the series branch up to |s| r / c2 < 2,
+// (ii) geometry relative to the collocation point (differences formed once
+// per element in FP64, then rounded), (iii) two-level summation: plain FP32
+// over at most 16 points, then compensated (Kahan) accumulation.
+//
+// Every function sums the points q = lane, lane + nl, ... of the entry's
+// rules, so that a warp can share one heavy entry (lanes over quadrature
+// points, shuffle reduction) while light entries run one per thread
+// (lane = 0, nl = 1).  Terms that do not depend on a quadrature point (free
+// term, CPV, rigid-body diagonal) are added by lane 0 only.
+#pragma once
+
+namespace gcq {
+
+// running sums: block of <= 16 terms in t, then Kahan into (s, c)
+template <int N>
+struct FAcc {
+  float t[N], s[N], c[N];
+  int cnt;
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int i = 0; i < N; ++i) t[i] = s[i] = c[i] = 0.f;
+    cnt = 0;
+  }
+  __device__ __forceinline__ void flush() {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const float y = t[i] - c[i];
+      const float u = s[i] + y;
+      c[i] = (u - s[i]) - y;
+      s[i] = u;
+      t[i] = 0.f;
+    }
+    cnt = 0;
+  }
+  __device__ __forceinline__ void tick() {
+    if (++cnt == 16) flush();
+  }
+  __device__ __forceinline__ void add_const(int i, float x) {
+    const float y = x - c[i];
+    const float u = s[i] + y;
+    c[i] = (u - s[i]) - y;
+    s[i] = u;
+  }
+};
+
+// FP64 rule decision with the tie band (same as the oracle), no square root
+__device__ __forceinline__ int rule_index2(const ElemGeo& g, const double* x) {
+  const double dx = g.c[0] - x[0], dy = g.c[1] - x[1], dz = g.c[2] - x[2];
+  const double d2 = dx * dx + dy * dy + dz * dz;
+  const double hb = g.h * (1.0 - 1e-12);
+  const double h2 = hb * hb;
+  if (d2 >= rule_dist(0) * rule_dist(0) * h2) return 0;
+  if (d2 >= rule_dist(1) * rule_dist(1) * h2) return 1;
+  if (d2 >= rule_dist(2) * rule_dist(2) * h2) return 2;
+  return 3;
+}
+
+// CPV int_e rh / r^2 dA in FP32, x inside the flat element (closed form per
+// sub-triangle, as cpv_rh_r2); vertices relative to p0, x relative to p0
+__device__ void cpv_rh_r2_f(const float* e1, const float* e2, const float* xr, float* G) {
+  float P[3][3] = {{0.f, 0.f, 0.f}, {e1[0], e1[1], e1[2]}, {e2[0], e2[1], e2[2]}};
+  G[0] = G[1] = G[2] = 0.f;
+  for (int a = 0; a < 3; ++a) {
+    const float* Pa = P[a];
+    const float* Pb = P[(a + 1) % 3];
+    float t[3] = {Pb[0] - Pa[0], Pb[1] - Pa[1], Pb[2] - Pa[2]};
+    const float tl = sqrtf(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    for (int k = 0; k < 3; ++k) t[k] /= tl;
+    const float xa = (xr[0] - Pa[0]) * t[0] + (xr[1] - Pa[1]) * t[1] + (xr[2] - Pa[2]) * t[2];
+    float e0[3] = {Pa[0] + xa * t[0] - xr[0], Pa[1] + xa * t[1] - xr[1], Pa[2] + xa * t[2] - xr[2]};
+    const float h = sqrtf(e0[0] * e0[0] + e0[1] * e0[1] + e0[2] * e0[2]);
+    for (int k = 0; k < 3; ++k) e0[k] /= h;
+    const float ta = -xa, tb = tl - xa;   // tangential coordinates of Pa, Pb from the foot
+    const float Ra = sqrtf(h * h + ta * ta), Rb = sqrtf(h * h + tb * tb);
+    const float p0 = (tb / Rb) * (logf(Rb) + 1.f) - asinhf(tb / h) - ((ta / Ra) * (logf(Ra) + 1.f) - asinhf(ta / h));
+    const float p1 = -(h / Rb) * (logf(Rb) + 1.f) + (h / Ra) * (logf(Ra) + 1.f);
+    for (int k = 0; k < 3; ++k) G[k] += e0[k] * p0 + t[k] * p1;
+  }
+}
+
+// element frame in FP32 relative to the collocation point
+struct FrameF {
+  float d0[3];   // p0 - x
+  float e1[3], e2[3], n[3];
+  float area2;
+};
+__device__ __forceinline__ FrameF frame_f(const ElemGeo& g, const double* x) {
+  FrameF f;
+  for (int k = 0; k < 3; ++k) {
+    f.d0[k] = (float)(g.p0[k] - x[k]);
+    f.e1[k] = (float)g.e1[k];
+    f.e2[k] = (float)g.e2[k];
+    f.n[k] = (float)g.n[k];
+  }
+  f.area2 = (float)g.area2;
+  return f;
+}
+
+// Duffy sub-triangle (apex at x): edges ba = B - A, cb = C - B, 2 * area
+struct SubF {
+  float ba[3], cb[3], ar2;
+};
+__device__ __forceinline__ SubF sub_f(const float* A, const float* B, const float* C) {
+  SubF s;
+  float ca[3];
+  for (int k = 0; k < 3; ++k) {
+    s.ba[k] = B[k] - A[k];
+    s.cb[k] = C[k] - B[k];
+    ca[k] = C[k] - A[k];
+  }
+  const float c0 = s.ba[1] * ca[2] - s.ba[2] * ca[1], c1 = s.ba[2] * ca[0] - s.ba[0] * ca[2],
+              c2 = s.ba[0] * ca[1] - s.ba[1] * ca[0];
+  s.ar2 = sqrtf(c0 * c0 + c1 * c1 + c2 * c2);
+  return s;
+}
+
+// vertices of element e relative to p0 (P0 = 0, P1 = e1, P2 = e2)
+__device__ __forceinline__ void vert_f(const FrameF& f, int a, float* P) {
+  for (int k = 0; k < 3; ++k) P[k] = a == 0 ? 0.f : (a == 1 ? f.e1[k] : f.e2[k]);
+}
+
+// ---- single layer: V[i, e] partial sum over points lane, lane + nl, ... -------
+template <int ROWS>
+__device__ void entry_sl_f(const EntryView& v, int i, int e, cx<float> s, cx<float> is2, int lane, int nl,
+                           float* out18) {
+  const ElemGeo& g = v.geo[e];
+  const double* x = row_point<ROWS>(v, i);
+  const int32_t* t = v.tri + 3 * (int64_t)e;
+  int apex = -1;
+  if (ROWS == BEM_ROWS_NODES)
+    apex = (t[0] == i) ? 0 : (t[1] == i) ? 1 : (t[2] == i) ? 2 : -1;
+  else if (e == i)
+    apex = 3;
+  FAcc<14> acc;   // SA (2) + SB[6] (12)
+  acc.init();
+  cx<float>* SA = reinterpret_cast<cx<float>*>(acc.t);
+  cx<float>* SB = reinterpret_cast<cx<float>*>(acc.t + 2);
+  const FrameF f = frame_f(g, x);
+  if (apex >= 0) {
+    // sub-triangles with apex x, coordinates relative to p0; x - p0 = -d0
+    const float xr[3] = {-f.d0[0], -f.d0[1], -f.d0[2]};
+    const int nsub = apex == 3 ? 3 : 1;
+    for (int q = lane; q < nsub * 256; q += nl) {
+      const int sb = q >> 8, a = (q >> 4) & 15, b = q & 15;
+      float A[3], Bv[3], Cv[3];
+      if (apex == 3) {
+        for (int k = 0; k < 3; ++k) A[k] = xr[k];
+        vert_f(f, sb, Bv);
+        vert_f(f, (sb + 1) % 3, Cv);
+      } else {
+        vert_f(f, apex, A);
+        vert_f(f, (apex + 1) % 3, Bv);
+        vert_f(f, (apex + 2) % 3, Cv);
+      }
+      const SubF st = sub_f(A, Bv, Cv);
+      const float u = c_gl16_f[a], wu = c_gl16_f[16 + a];
+      const float vv = c_gl16_f[b], wv = c_gl16_f[16 + b];
+      // y - x = (A - x) + u (ba + v cb) with A = x
+      acc_U<float>(v.kf, wu * wv * st.ar2 * u, u * (st.ba[0] + vv * st.cb[0]), u * (st.ba[1] + vv * st.cb[1]),
+                   u * (st.ba[2] + vv * st.cb[2]), s, is2, *SA, SB);
+      acc.tick();
+    }
+  } else {
+    const int ri = rule_index2(g, x);
+    const int q0 = rule_offset(ri), q1 = rule_offset(ri + 1);
+    for (int q = q0 + lane; q < q1; q += nl) {
+      const float xi = c_rule_f[3 * q], et = c_rule_f[3 * q + 1];
+      const float wq = c_rule_f[3 * q + 2] * f.area2;
+      acc_U<float>(v.kf, wq, f.d0[0] + xi * f.e1[0] + et * f.e2[0], f.d0[1] + xi * f.e1[1] + et * f.e2[1],
+                   f.d0[2] + xi * f.e1[2] + et * f.e2[2], s, is2, *SA, SB);
+      acc.tick();
+    }
+  }
+  acc.flush();
+  const float c = v.kf.inv4pirho;
+  const cx<float> sa = {acc.s[0], acc.s[1]};
+  cx<float> sbv[6];
+  for (int k = 0; k < 6; ++k) sbv[k] = {acc.s[2 + 2 * k], acc.s[3 + 2 * k]};
+  const cx<float> o[9] = {c * (sa + sbv[0]), c * sbv[1], c * sbv[2], c * sbv[1], c * (sa + sbv[3]),
+                          c * sbv[4], c * sbv[2], c * sbv[4], c * (sa + sbv[5])};
+  for (int k = 0; k < 9; ++k) {
+    out18[2 * k] = o[k].x;
+    out18[2 * k + 1] = o[k].y;
+  }
+}
+
+// ---- double layer (C + K)[i, j] partial sum ---------------------------------
+template <int ROWS>
+__device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<float> is2, int lane, int nl,
+                           float* out18) {
+  const double* x = row_point<ROWS>(v, i);
+  FAcc<18> acc;
+  acc.init();
+  cx<float>* A9 = reinterpret_cast<cx<float>*>(acc.t);
+  float st0[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // static parts (point-independent or T0)
+  const float nu = (float)v.nu;
+  const int p0 = v.ne_ptr[j], p1 = v.ne_ptr[j + 1];
+  for (int p = p0; p < p1; ++p) {
+    const int e = v.ne_elem[p];
+    const int a = v.ne_loc[p];   // local vertex of column node j in e
+    const ElemGeo& g = v.geo[e];
+    const int32_t* t = v.tri + 3 * (int64_t)e;
+    int apex = -1;
+    if (ROWS == BEM_ROWS_NODES)
+      apex = (t[0] == i) ? 0 : (t[1] == i) ? 1 : (t[2] == i) ? 2 : -1;
+    else if (e == i)
+      apex = 3;
+    const FrameF f = frame_f(g, x);
+    if (apex < 0) {
+      const int ri = rule_index2(g, x);
+      const int q0 = rule_offset(ri), q1 = rule_offset(ri + 1);
+      for (int q = q0 + lane; q < q1; q += nl) {
+        const float xi = c_rule_f[3 * q], et = c_rule_f[3 * q + 1];
+        const float phi = a == 0 ? 1.f - xi - et : (a == 1 ? xi : et);
+        const float wq = c_rule_f[3 * q + 2] * f.area2 * phi;
+        acc_TT<float, false>(v.kf, wq, f.d0[0] + xi * f.e1[0] + et * f.e2[0], f.d0[1] + xi * f.e1[1] + et * f.e2[1],
+                             f.d0[2] + xi * f.e1[2] + et * f.e2[2], f.n, s, is2, A9);
+        acc.tick();
+      }
+      continue;
+    }
+    const float xr[3] = {-f.d0[0], -f.d0[1], -f.d0[2]};
+    const int nsub = apex == 3 ? 3 : 1;
+    for (int q = lane; q < nsub * 256; q += nl) {
+      const int sb = q >> 8, qa = (q >> 4) & 15, qb = q & 15;
+      float A[3], Bv[3], Cv[3];
+      int lb, lc;
+      if (apex == 3) {
+        lb = sb;
+        lc = (sb + 1) % 3;
+        for (int k = 0; k < 3; ++k) A[k] = xr[k];
+      } else {
+        lb = (apex + 1) % 3;
+        lc = (apex + 2) % 3;
+        vert_f(f, apex, A);
+      }
+      vert_f(f, lb, Bv);
+      vert_f(f, lc, Cv);
+      const SubF sbf = sub_f(A, Bv, Cv);
+      const float u = c_gl16_f[qa], wu = c_gl16_f[16 + qa];
+      const float vv = c_gl16_f[qb], wv = c_gl16_f[16 + qb];
+      const float d0 = u * (sbf.ba[0] + vv * sbf.cb[0]);
+      const float d1 = u * (sbf.ba[1] + vv * sbf.cb[1]);
+      const float d2 = u * (sbf.ba[2] + vv * sbf.cb[2]);
+      const float wq = wu * wv * sbf.ar2 * u;
+      const float lam_b = u * (1.f - vv), lam_c = u * vv;
+      float phi;
+      if (apex == 3)
+        phi = (1.f - u) * (1.f / 3.f) + (a == lb ? lam_b : 0.f) + (a == lc ? lam_c : 0.f);
+      else
+        phi = (a == apex) ? 1.f - u : (a == lb ? lam_b : lam_c);
+      if (apex == 3) {
+        acc_TT<float, true>(v.kf, wq * phi, d0, d1, d2, f.n, s, is2, A9);
+        acc_T0T<float>(nu, wq * (phi - 1.f / 3.f), d0, d1, d2, f.n, st0);
+      } else if (a == apex) {
+        acc_TT<float, true>(v.kf, wq * phi, d0, d1, d2, f.n, s, is2, A9);
+      } else {
+        acc_TT<float, false>(v.kf, wq * phi, d0, d1, d2, f.n, s, is2, A9);
+      }
+      acc.tick();
+    }
+    if (apex == 3 && lane == 0) {
+      float G[3];
+      cpv_rh_r2_f(f.e1, f.e2, xr, G);
+      const float fc = -(1.f - 2.f * nu) / (8.f * (float)M_PI * (1.f - nu)) / 3.f;
+      for (int aa = 0; aa < 3; ++aa)
+        for (int bb = 0; bb < 3; ++bb)
+          st0[3 * aa + bb] += fc * (G[bb] * f.n[aa] - f.n[bb] * G[aa]) + (aa == bb ? 1.f / 6.f : 0.f);
+    }
+  }
+  acc.flush();
+  if (ROWS == BEM_ROWS_NODES && j == i && v.rb && lane == 0)
+    for (int c = 0; c < 9; ++c) st0[c] += (float)v.rb[9 * (int64_t)i + c];
+  for (int c = 0; c < 9; ++c) {
+    acc.add_const(2 * c, st0[c]);
+    out18[2 * c] = acc.s[2 * c];
+    out18[2 * c + 1] = acc.s[2 * c + 1];
+  }
+}
+
+// does the entry use a rule of 64 or more points (near or singular)?
+template <int KERN, int ROWS>
+__device__ __forceinline__ bool entry_heavy(const EntryView& v, int i, int j) {
+  const double* x = row_point<ROWS>(v, i);
+  if (KERN == BEM_SL) {
+    const int32_t* t = v.tri + 3 * (int64_t)j;
+    if (ROWS == BEM_ROWS_NODES ? (t[0] == i || t[1] == i || t[2] == i) : j == i) return true;
+    return rule_index2(v.geo[j], x) >= 2;
+  }
+  for (int p = v.ne_ptr[j]; p < v.ne_ptr[j + 1]; ++p) {
+    const int e = v.ne_elem[p];
+    const int32_t* t = v.tri + 3 * (int64_t)e;
+    if (ROWS == BEM_ROWS_NODES ? (t[0] == i || t[1] == i || t[2] == i) : e == i) return true;
+    if (rule_index2(v.geo[e], x) >= 2) return true;
+  }
+  return false;
+}
+
+template <int KERN, int ROWS>
+__device__ __forceinline__ void entry_f(const EntryView& v, int i, int j, cx<float> s, cx<float> is2, int lane,
+                                        int nl, float* out18) {
+  if (KERN == BEM_SL)
+    entry_sl_f<ROWS>(v, i, j, s, is2, lane, nl, out18);
+  else
+    entry_dl_f<ROWS>(v, i, j, s, is2, lane, nl, out18);
+}
+
+// warp-cooperative evaluation: every lane of the warp calls this with the
+// same (i, j, s); the sum over all points is returned in all lanes
+template <int KERN, int ROWS>
+__device__ __forceinline__ void entry_f_warp(const EntryView& v, int i, int j, cx<float> s, cx<float> is2,
+                                             float* out18) {
+  const int lane = threadIdx.x & 31;
+  entry_f<KERN, ROWS>(v, i, j, s, is2, lane, 32, out18);
+#pragma unroll
+  for (int c = 0; c < 18; ++c)
+    for (int o = 16; o > 0; o >>= 1) out18[c] += __shfl_xor_sync(0xffffffffu, out18[c], o);
+}
+
+// entry in the precision of the context: FP64 (entry.cuh) or FP32 (above,
+// one thread for all points); result in double
+template <typename R, int KERN, int ROWS>
+__device__ __forceinline__ void entry(const EntryView& v, int i, int j, cx<double> s, cx<double> is2,
+                                      cx<double>* out) {
+  if constexpr (sizeof(R) == sizeof(float)) {
+    float o[18];
+    entry_f<KERN, ROWS>(v, i, j, cx<float>{(float)s.x, (float)s.y}, cx<float>{(float)is2.x, (float)is2.y}, 0, 1, o);
+    for (int c = 0; c < 9; ++c) out[c] = {(double)o[2 * c], (double)o[2 * c + 1]};
+  } else {
+    if (KERN == BEM_SL)
+      entry_sl<double, ROWS>(v, i, j, s, is2, out);
+    else
+      entry_dl<double, ROWS>(v, i, j, s, is2, out);
+  }
+}
+
+}  // namespace gcq

@@ -1,0 +1,148 @@
+// Internal declarations of libgcqbem (host + device).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gcqbem.h"
+
+namespace gcq {
+
+// ---------------------------------------------------------------------------
+// quadrature rules (Sec. 2.3: regular collapsed Gauss, Duffy for x on the
+// element).  Orders by distance ratio |x - centroid| / h_e.
+// ---------------------------------------------------------------------------
+constexpr int kNumRules = 4;                       // n = 3, 5, 8, 16
+constexpr int kRuleN[kNumRules] = {3, 5, 8, 16};
+constexpr int kSingN = 16;                          // Duffy rule per sub-triangle
+// >= 4h: n = 3, >= 2h: n = 5, >= h: n = 8, else n = 16
+__host__ __device__ constexpr double rule_dist(int r) { return r == 0 ? 4.0 : (r == 1 ? 2.0 : 1.0); }
+// first point of rule r in the packed table (9 + 25 + 64 + 256 points)
+__host__ __device__ constexpr int rule_offset(int r) {
+  return r <= 0 ? 0 : (r == 1 ? 9 : (r == 2 ? 34 : (r == 3 ? 98 : 354)));
+}
+constexpr int kSeriesTerms = 26;
+constexpr double kSeriesZ = 1.0;                    // series where |s| r / c2 < 1
+
+// Gauss-Legendre on [0, 1] by Newton's method on P_n.
+void gauss_legendre01(int n, double* x, double* w);
+
+// One element of the mesh, 20 doubles (160 B, 32 B aligned).
+struct __align__(32) ElemGeo {
+  double p0[3];      // vertex 0
+  double e1[3];      // p1 - p0
+  double e2[3];      // p2 - p0
+  double n[3];       // unit normal
+  double area2;      // 2 * area (Jacobian of the reference map)
+  double h;          // longest edge
+  double c[3];       // centroid
+  double pad[3];
+};
+
+// Material + series tables passed by value to the kernels.
+struct Material {
+  double rho, lam, mu, c1, c2, nu;
+  double ta[kSeriesTerms];   // A series coefficients (see kernels)
+  double tb[kSeriesTerms];   // B series coefficients
+};
+
+struct DeviceBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace gcq
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+struct bem_ctx {
+  bem_options opt{};
+  int device = 0;
+  std::string err;
+  bool has_material = false;
+  gcq::Material mat{};
+  int32_t K = 0;
+  std::vector<double> s;          // 2K
+  double2* d_s = nullptr;         // s_k
+  double2* d_inv_s2 = nullptr;    // 1 / s_k^2
+};
+
+struct bem_mesh {
+  bem_ctx* ctx = nullptr;
+  std::atomic<int> refs{1};
+  int64_t n_nodes = 0, n_tris = 0;
+  std::vector<double> xyz;        // host copy
+  std::vector<int32_t> tri;
+  std::vector<gcq::ElemGeo> geo;  // host geometry
+  // node -> incident (element, local vertex) CSR
+  std::vector<int32_t> ne_ptr, ne_elem, ne_loc;
+  // device
+  gcq::ElemGeo* d_geo = nullptr;
+  int32_t* d_tri = nullptr;
+  double* d_nodes = nullptr;      // n_nodes x 3
+  double* d_cent = nullptr;       // n_tris x 3
+  int32_t* d_ne_ptr = nullptr;
+  int32_t* d_ne_elem = nullptr;
+  int32_t* d_ne_loc = nullptr;
+  double* d_rb = nullptr;         // rigid-body static diagonal (node rows), n_nodes x 9, lazily
+};
+
+struct BlockDesc {
+  int64_t r0, m, c0, n;  // offsets/sizes in cluster order
+  int32_t far;
+};
+
+struct bem_tree {
+  bem_mesh* mesh = nullptr;
+  std::atomic<int> refs{1};
+  int32_t rows = 0, kernel = 0;
+  int64_t n_rows = 0, n_cols = 0;
+  std::vector<int32_t> row_perm, col_perm;  // cluster position -> original index
+  std::vector<BlockDesc> blocks;
+  int64_t n_far = 0;
+};
+
+namespace gcq {
+struct OpData;
+}
+
+struct bem_op {
+  bem_tree* tree = nullptr;
+  gcq::OpData* d = nullptr;
+};
+
+namespace gcq {
+
+// error helpers -------------------------------------------------------------
+bem_status set_err(bem_ctx* ctx, bem_status st, const std::string& msg);
+bem_status cuda_err(bem_ctx* ctx, cudaError_t e, const char* what);
+
+#define GCQ_CUDA(ctx, call)                                         \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return ::gcq::cuda_err((ctx), e_, #call); \
+  } while (0)
+
+// host-side building blocks (host.cpp) ----------------------------------------
+void series_tables(double c1, double c2, double* ta, double* tb);
+bem_status build_trees(bem_tree* t);
+
+// device-side entry points (entry.cu, aca3d.cu, apply.cu, cq.cu) ---------------
+bem_status upload_quadrature(bem_ctx* ctx);
+bem_status ensure_rigid_body(bem_mesh* mesh, cudaStream_t st);
+bem_status launch_entries(bem_mesh* mesh, int rows, int kernel, const int32_t* req, int64_t n,
+                          void* out, int* d_flag, cudaStream_t st);
+bem_status compress(bem_tree* tree, cudaStream_t st, OpData** out);
+void free_op(OpData* d);
+bem_status apply(bem_op* op, int mode, const void* X, void* Y, cudaStream_t st);
+bem_status op_dense(bem_op* op, void* out, cudaStream_t st);
+bem_status op_stats(const bem_op* op, bem_op_stats* st);
+bem_status op_blocks(const bem_op* op, int64_t* info);
+bem_status cq_transform(int N, int64_t nvec, const void* in, void* out, bool inverse, cudaStream_t st);
+
+}  // namespace gcq
