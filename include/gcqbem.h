@@ -112,7 +112,8 @@ bem_status bem_material_set(bem_ctx* ctx, double rho, double lambda, double mu,
  * 1 <= K <= N + 1. */
 bem_status bem_freqs_bdf2(int32_t N, double dt, int32_t K, double* s_re_im);
 /* Sets the K frequencies (host array of 2K doubles) used by every later
- * entry evaluation and compression on ctx.  Re(s) > 0 required. */
+ * entry evaluation and compression on ctx.  Re(s) > 0 and 1 <= K <= 256
+ * required (one CTA of K threads evaluates a fibre). */
 bem_status bem_freqs_set(bem_ctx* ctx, const double* s_re_im, int32_t K);
 
 /* Surface mesh of flat triangles (Eq. (2.10)): xyz host n_nodes x 3 doubles,

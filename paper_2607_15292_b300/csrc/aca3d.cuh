@@ -207,6 +207,24 @@ __device__ __forceinline__ void block_argmax(double& val, int64_t& idx, double* 
   __syncthreads();
 }
 
+// sum of v[0..31] over the 32 lanes of a warp, returned in lane l for value
+// l (31 shuffles instead of 5 per value); v is destroyed
+template <typename T>
+__device__ __forceinline__ T warp_transpose_sum(T* v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < o; ++k) {
+      const T send = up ? v[k] : v[k + o];
+      const T recv = __shfl_xor_sync(0xffffffffu, send, o);
+      v[k] = (up ? v[k + o] : v[k]) + recv;
+    }
+  }
+  return v[0];
+}
+
 // ---- face kernel -------------------------------------------------------------
 // FP64 mode: faces/fibres in c128, residual, pivot criterion and Gram products
 // in double.  MIXED mode: faces/fibres in complex float-float (float4), the
@@ -304,16 +322,24 @@ __global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restr
       sf[c] = fib_tab[(int64_t)p * nb + t.blk][(int64_t)kd * 9 + c % 9];
     }
     __syncthreads();
-    if (ok)
+    if (ok) {
+      S nxt[9];
+      {
+        const S* Hp = face_tab[(int64_t)p0 * nb + t.blk] + e * 9;
+        for (int c = 0; c < 9; ++c) nxt[c] = Hp[c];
+      }
       for (int p = 0; p < np; ++p) {
-        const S* Hp = face_tab[(int64_t)(p0 + p) * nb + t.blk] + e * 9;
+        S cur[9];
+        for (int c = 0; c < 9; ++c) cur[c] = nxt[c];
+        if (p + 1 < np) {   // prefetch the next face while this one is used
+          const S* Hn = face_tab[(int64_t)(p0 + p + 1) * nb + t.blk] + e * 9;
+          for (int c = 0; c < 9; ++c) nxt[c] = Hn[c];
+        }
         const S* f = sf + 9 * p;
         if constexpr (FF) {
-          float4 hp[9];
-          for (int c = 0; c < 9; ++c) hp[c] = reinterpret_cast<const float4*>(Hp)[c];
           for (int a = 0; a < 3; ++a)
             for (int c = 0; c < 3; ++c) {
-              const float4 x = hp[3 * a + c];
+              const float4 x = reinterpret_cast<const float4*>(cur)[3 * a + c];
               for (int b = 0; b < 3; ++b) {
                 const float4 y = reinterpret_cast<const float4*>(f)[3 * c + b];
                 float& rh = fh[2 * (3 * a + b)];
@@ -330,7 +356,7 @@ __global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restr
         } else {
           cx<double> hp[9], ff[9];
           for (int c = 0; c < 9; ++c) {
-            hp[c] = St<S>::ld(Hp + c);
+            hp[c] = St<S>::ld(cur + c);
             ff[c] = St<S>::ld(f + c);
           }
           for (int a = 0; a < 3; ++a)
@@ -341,6 +367,7 @@ __global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restr
             }
         }
       }
+    }
   }
   S* Hd = face_tab[(int64_t)slot * nb + t.blk];
   cx<W> H[9];   // working copy for the pivot criterion and the Gram
@@ -375,34 +402,56 @@ __global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restr
     p_idx[blockIdx.x] = idx;
     p_h2[blockIdx.x] = h2s[0];
   }
-  // Gram blocks M_pd = sum_ij H_p[i,j]^H H_d[i,j], p = 0..slot
-  for (int p = 0; p <= slot; ++p) {
-    W g[18];
-    for (int c = 0; c < 18; ++c) g[c] = W(0);
-    if (ok) {
-      const S* Hp = face_tab[(int64_t)p * nb + t.blk] + e * 9;
-      cx<W> hp[9];
-      for (int c = 0; c < 9; ++c) {
-        if constexpr (FF) {
-          const float4 x = reinterpret_cast<const float4*>(Hp)[c];
-          hp[c] = {(W)x.x, (W)x.y};
-        } else {
-          const cx<double> x = St<S>::ld(Hp + c);
-          hp[c] = {(W)x.x, (W)x.y};
+  // Gram blocks M_pd = sum_ij H_p[i,j]^H H_d[i,j], p = 0..slot: per-warp
+  // transpose sums into shared memory, then a fixed-order sum over the warps
+  __shared__ W gw[kTile / 32][16][18];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  S nxt[9];
+  if (ok) {
+    const S* Hp = face_tab[t.blk] + e * 9;
+    for (int c = 0; c < 9; ++c) nxt[c] = Hp[c];
+  }
+  for (int p0 = 0; p0 <= slot; p0 += 16) {
+    const int np = min(16, slot + 1 - p0);
+    for (int pp = 0; pp < np; ++pp) {
+      const int p = p0 + pp;
+      W g[32];
+      for (int c = 0; c < 32; ++c) g[c] = W(0);
+      if (ok) {
+        cx<W> hp[9];
+        for (int c = 0; c < 9; ++c) {
+          if constexpr (FF) {
+            const float4 x = reinterpret_cast<const float4*>(nxt)[c];
+            hp[c] = {(W)x.x, (W)x.y};
+          } else {
+            const cx<double> x = St<S>::ld(nxt + c);
+            hp[c] = {(W)x.x, (W)x.y};
+          }
         }
+        if (p + 1 <= slot) {
+          const S* Hn = face_tab[(int64_t)(p + 1) * nb + t.blk] + e * 9;
+          for (int c = 0; c < 9; ++c) nxt[c] = Hn[c];
+        }
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            cx<W> acc = {W(0), W(0)};
+            for (int c = 0; c < 3; ++c) acc = cfma(conj(hp[3 * c + a]), H[3 * c + b], acc);
+            g[2 * (3 * a + b)] = acc.x;
+            g[2 * (3 * a + b) + 1] = acc.y;
+          }
       }
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-          cx<W> acc = {W(0), W(0)};
-          for (int c = 0; c < 3; ++c) acc = cfma(conj(hp[3 * c + a]), H[3 * c + b], acc);
-          g[2 * (3 * a + b)] = acc.x;
-          g[2 * (3 * a + b) + 1] = acc.y;
-        }
+      const W tot = warp_transpose_sum<W>(g);
+      if (lane < 18) gw[wid][pp][lane] = tot;
     }
-    double gs[18];
-    block_sum<18, W>(g, gs, shv);
-    if (threadIdx.x == 0)
-      for (int c = 0; c < 9; ++c) p_M[((int64_t)blockIdx.x * K + p) * 9 + c] = make_double2(gs[2 * c], gs[2 * c + 1]);
+    __syncthreads();
+    double* pm = reinterpret_cast<double*>(p_M);
+    for (int q = threadIdx.x; q < np * 18; q += blockDim.x) {
+      const int pp = q / 18, c = q % 18;
+      double sum = 0.0;
+      for (int w = 0; w < kTile / 32; ++w) sum += (double)gw[w][pp][c];
+      pm[((int64_t)blockIdx.x * K + p0 + pp) * 18 + c] = sum;
+    }
+    __syncthreads();
   }
 }
 
@@ -437,18 +486,14 @@ __global__ void k_block_red(BlkDev* __restrict__ blk, const int32_t* __restrict_
     B.piv = idx;
     B.h2 = h2;
   }
-  for (int p = 0; p <= slot; ++p) {
-    double g[18];
-    for (int c = 0; c < 18; ++c) g[c] = 0.0;
-    for (int t = B.t0 + threadIdx.x; t < B.t1; t += blockDim.x)
-      for (int c = 0; c < 9; ++c) {
-        double2 z = p_M[((int64_t)t * K + p) * 9 + c];
-        g[2 * c] += z.x;
-        g[2 * c + 1] += z.y;
-      }
-    block_sum<18>(g, shv);
-    if (threadIdx.x == 0)
-      for (int c = 0; c < 9; ++c) M[((int64_t)b * K + p) * 9 + c] = make_double2(g[2 * c], g[2 * c + 1]);
+  // Gram blocks: thread per (face p, real component), fixed tile order
+  const double* pm = reinterpret_cast<const double*>(p_M);
+  double* mo = reinterpret_cast<double*>(M);
+  for (int q = threadIdx.x; q < (slot + 1) * 18; q += blockDim.x) {
+    const int p = q / 18, c = q % 18;
+    double sum = 0.0;
+    for (int t = B.t0; t < B.t1; ++t) sum += pm[((int64_t)t * K + p) * 18 + c];
+    mo[((int64_t)b * K + p) * 18 + c] = sum;
   }
 }
 
@@ -512,45 +557,36 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
     for (int c = 0; c < 9; ++c) St<S>::st(fd + (int64_t)k * 9 + c, f[c]);
     for (int c = 0; c < 9; ++c) f[c] = St<S>::ld(fd + (int64_t)k * 9 + c);
   }
-  // ||f_d||^2
-  double f2[1] = {0.0};
+  // ||f_d||^2 and the norm recursion: N_dp = sum_k f_d[k] f_p[k]^H with one
+  // thread per (face p, entry (a, c2)) reading f_d from shared memory, then
+  // tr(M_pd N_dp) accumulated per thread; one block reduction at the end
+  extern __shared__ double2 sfd[];   // K x 9 (f_d), from the launch
   if (ok)
-    for (int c = 0; c < 9; ++c) f2[0] += f[c].x * f[c].x + f[c].y * f[c].y;
-  block_sum<1>(f2, shv);
-  // cross terms: sum_p tr(M_pd N_dp), N_dp = sum_k f_d[k] f_p[k]^H
-  double cross = 0.0, self = 0.0;
-  for (int p = 0; p <= slot; ++p) {
-    double g[18];
-    for (int c = 0; c < 18; ++c) g[c] = 0.0;
-    if (ok) {
-      const S* fp = fib_tab[(int64_t)p * nb + b] + (int64_t)k * 9;
-      cx<double> ff[9];
-      for (int c = 0; c < 9; ++c) ff[c] = St<S>::ld(fp + c);
-      for (int a = 0; a < 3; ++a)
-        for (int c2 = 0; c2 < 3; ++c2) {
-          cx<double> acc = {0, 0};
-          for (int c = 0; c < 3; ++c) acc = cfma(f[3 * a + c], conj(ff[3 * c2 + c]), acc);
-          g[2 * (3 * a + c2)] = acc.x;
-          g[2 * (3 * a + c2) + 1] = acc.y;
-        }
-    }
-    block_sum<18>(g, shv);
-    if (threadIdx.x == 0) {
-      // tr(M_pd N_dp)
-      const double2* Mp = M + ((int64_t)b * K + p) * 9;
-      double tr = 0.0;
-      for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) {
-          double2 m = Mp[3 * a + c];
-          double nr = g[2 * (3 * c + a)], ni = g[2 * (3 * c + a) + 1];
-          tr += m.x * nr - m.y * ni;
-        }
-      if (p < slot)
-        cross += tr;
-      else
-        self = tr;
-    }
+    for (int c = 0; c < 9; ++c) sfd[(int64_t)k * 9 + c] = make_double2(f[c].x, f[c].y);
+  __syncthreads();
+  double part[3] = {0.0, 0.0, 0.0};   // ||f_d||^2, cross, self
+  if (ok)
+    for (int c = 0; c < 9; ++c) part[0] += f[c].x * f[c].x + f[c].y * f[c].y;
+  for (int q = threadIdx.x; q < (slot + 1) * 9; q += blockDim.x) {
+    const int p = q / 9, a = (q % 9) / 3, c2 = q % 3;
+    const S* fp = fib_tab[(int64_t)p * nb + b];
+    cx<double> acc = {0, 0};
+    for (int kk = 0; kk < K; ++kk)
+      for (int c = 0; c < 3; ++c) {
+        const double2 x = sfd[(int64_t)kk * 9 + 3 * a + c];
+        acc = cfma(cx<double>{x.x, x.y}, conj(St<S>::ld(fp + (int64_t)kk * 9 + 3 * c2 + c)), acc);
+      }
+    // contribution of N_dp[a][c2] to tr(M_pd N_dp) = sum M_pd[c2][a] N_dp[a][c2]
+    const double2 m = M[((int64_t)b * K + p) * 9 + 3 * c2 + a];
+    const double tr = m.x * acc.x - m.y * acc.y;
+    if (p < slot)
+      part[1] += tr;
+    else
+      part[2] += tr;
   }
+  block_sum<3>(part, shv);
+  double f2[1] = {part[0]};
+  const double cross = part[1], self = part[2];
   __shared__ int stop;
   if (threadIdx.x == 0) {
     double norm2 = B.norm2 + 2.0 * cross + self;
@@ -769,8 +805,11 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
                                                          K);
     GCQ_CUDA(ctx, cudaGetLastError());
     const int tb = std::max(32, ((K + 31) / 32) * 32);
+    const size_t fsm = sizeof(double2) * 9 * (size_t)K;
     GCQ_DISPATCH(d->kernel, d->rows,
-                 (k_fibre_step<R, S, KK, RR><<<(unsigned)active.size(), tb, 0, st>>>(
+                 (cudaFuncSetAttribute(k_fibre_step<R, S, KK, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fsm),
+                  k_fibre_step<R, S, KK, RR><<<(unsigned)active.size(), tb, fsm, st>>>(
                      v, d->d_blk, d_active, (S* const*)d->d_face, (S* const*)d->d_fib, nb, slot, d->d_row_perm,
                      d->d_col_perm, d->d_M, d->d_ks, d->d_used, K, ctx->opt.eps)));
     GCQ_CUDA(ctx, cudaGetLastError());

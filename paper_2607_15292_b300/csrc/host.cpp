@@ -436,7 +436,7 @@ bem_status bem_freqs_bdf2(int32_t N, double dt, int32_t K, double* s) {
 
 bem_status bem_freqs_set(bem_ctx* ctx, const double* s, int32_t K) {
   if (!ctx) return BEM_ERR_ARG;
-  if (!s || K < 1) return set_err(ctx, BEM_ERR_ARG, "bem_freqs_set: need K >= 1 frequencies");
+  if (!s || K < 1 || K > 256) return set_err(ctx, BEM_ERR_ARG, "bem_freqs_set: need 1 <= K <= 256 frequencies");
   for (int k = 0; k < K; ++k)
     if (!(s[2 * k] > 0) || !std::isfinite(s[2 * k + 1]))
       return set_err(ctx, BEM_ERR_ARG, "bem_freqs_set: Re(s) must be > 0");
