@@ -201,16 +201,23 @@ def main():
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     entries = 0
-    face_ms = 0.0
+    entry_ms = 0.0
+    face = {"ms": 0.0, "launches": 0, "bytes": 0.0}
+    l0 = g.kernel_launches()
     with Clocks(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
             oV, oK = step()
             sv, sk = oV.stats(), oK.stats()
             entries += sv.entries_evaluated + sk.entries_evaluated
-            face_ms += sv.t_entries_ms + sk.t_entries_ms
+            entry_ms += sv.t_entries_ms + sk.t_entries_ms
+            for st_ in (sv, sk):
+                face["ms"] += st_.t_face_ms
+                face["launches"] += st_.face_launches
+                face["bytes"] += st_.face_alg_bytes
         ev1.record(stream)
         barrier()
+    launches = g.kernel_launches() - l0
     ms = ev0.elapsed_time(ev1)
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -295,6 +302,15 @@ def main():
     d2h = YV.numel() * 8 + YK.numel() * 8
 
     peaks = _peaks()
+    hbm = peaks.get("hbm_gbs") or 6400.0
+    face_gbs = face["bytes"] / (face["ms"] / 1e3) / 1e9 if face["ms"] > 0 else None
+    roofline = {"kernel": "k_face (3D-ACA face: entries + residual + Gram), MIXED",
+                "bound": "hbm", "achieved": face_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": (face_gbs / hbm) if face_gbs else None,
+                "traffic": None, "launches": face["launches"],
+                "avg_launch_ms": face["ms"] / max(1, face["launches"]),
+                "algorithmic_bytes_per_launch": face["bytes"] / max(1, face["launches"]),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.4 TB/s"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64 (FP32) far field + FP64 near/singular, pivots, norms",
@@ -302,8 +318,8 @@ def main():
             "clocks": clk.summary(),
             "e2e": {"value": e_entries / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": None, **extra}
-    line["entry_kernel_ms_per_step"] = face_ms / args.steps
+            "gpu_launches": launches, "roofline": roofline, **extra}
+    line["entry_kernels_ms_per_step"] = entry_ms / args.steps
     line["peaks_source"] = "MEASURED_PEAKS.json" if peaks else "fallback"
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(15.0)

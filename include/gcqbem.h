@@ -182,6 +182,12 @@ typedef struct {
   double t_entries_ms;          /* device time of the entry kernels        */
   double t_compress_ms;         /* wall time of bem_op_compress             */
   int64_t apply_bytes;          /* algorithmic bytes read+written per apply */
+  double t_face_ms;             /* device time of the face kernel (CUDA events) */
+  int64_t face_launches;        /* launches of the face kernel              */
+  double face_alg_bytes;        /* its algorithmic bytes: for every entry of
+                                   an active block, the previous faces read
+                                   once and the new face written once       */
+  int64_t launches;             /* kernels launched by the compression     */
 } bem_op_stats;
 bem_status bem_op_stats_get(const bem_op* op, bem_op_stats* st);
 
@@ -189,6 +195,10 @@ bem_status bem_op_stats_get(const bem_op* op, bem_op_stats* st);
  * 2 rank0), rank, first pivot frequency k_1 (-1 if none), face storage
  * (0 dense faces, 1 low rank).  Blocks in bem_tree_export order. */
 bem_status bem_op_blocks(const bem_op* op, int64_t* info);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts); used to count the device work of a timed region. */
+int64_t bem_kernel_launches(void);
 
 /* Uniform-step CQ (BDF2) transforms over L = N + 1 time levels for nvec
  * complex128 values per level (device, L x nvec):

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libgcqbem.so")
 if not os.path.exists(LIB_PATH):
     raise ImportError(
         f"libgcqbem.so not found at {LIB_PATH}: build it with "
-        "`python -m paper_2607_15292_b300.build` (nvcc, sm_103a)")
+        "`python paper_2607_15292_b300/build.py` (nvcc, sm_103a)")
 
 _lib = ctypes.CDLL(LIB_PATH)
 
@@ -48,7 +48,9 @@ class bem_op_stats(ctypes.Structure):
                 ("stored_bytes", ctypes.c_double), ("dense_bytes", ctypes.c_double),
                 ("compression_rate", ctypes.c_double), ("entries_evaluated", ctypes.c_int64),
                 ("t_entries_ms", ctypes.c_double), ("t_compress_ms", ctypes.c_double),
-                ("apply_bytes", ctypes.c_int64)]
+                ("apply_bytes", ctypes.c_int64), ("t_face_ms", ctypes.c_double),
+                ("face_launches", ctypes.c_int64), ("face_alg_bytes", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
 
 
 _vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -75,6 +77,7 @@ _SIGS = {
     "bem_op_dense": (_i32, [_vp, _vp, _vp]),
     "bem_op_stats_get": (_i32, [_vp, _P(bem_op_stats)]),
     "bem_op_blocks": (_i32, [_vp, _P(_i64)]),
+    "bem_kernel_launches": (_i64, []),
     "bem_cq_forward": (_i32, [_i32, _i64, _vp, _vp, _vp]),
     "bem_cq_inverse": (_i32, [_i32, _i64, _vp, _vp, _vp]),
 }
@@ -115,6 +118,11 @@ def options_default() -> bem_options:
     o = bem_options()
     _check(_lib.bem_options_default(ctypes.byref(o)))
     return o
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(_lib.bem_kernel_launches())
 
 
 def freqs_bdf2(N: int, dt: float, K: int) -> np.ndarray:
@@ -250,6 +258,10 @@ class Stats:
     t_entries_ms: float
     t_compress_ms: float
     apply_bytes: int
+    t_face_ms: float
+    face_launches: int
+    face_alg_bytes: float
+    launches: int
 
 
 class Operator:

@@ -1,6 +1,8 @@
 """Builds libgcqbem.so in-tree for B300 (sm_103a) with nvcc.
 
-    python -m paper_2607_15292_b300.build [--ptxas-v]
+    python paper_2607_15292_b300/build.py [--ptxas-v]
+
+Run as a script (not through the package, whose import loads the library).
 
 The library is plain C ABI (include/gcqbem.h); no PyTorch headers are used.
 """

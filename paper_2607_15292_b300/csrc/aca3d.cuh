@@ -60,6 +60,10 @@ struct OpData {
   int64_t entries = 0;
   double t_entries_ms = 0, t_compress_ms = 0;
   int64_t apply_bytes = 0;
+  double t_face_ms = 0;          // k_face device time (events on the stream)
+  int64_t face_launches = 0;
+  double face_alg_bytes = 0;     // algorithmic bytes of k_face: (slot + 1) faces per entry
+  int64_t launches = 0;          // kernels launched by the compression
   // apply work lists
   int32_t* d_apply_items = nullptr;  // (block, row tile, k tile) for aca blocks
   int64_t n_apply_items = 0;
@@ -748,9 +752,10 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   GCQ_CUDA(ctx, dmalloc(&p_h2, sizeof(double) * n_tiles_all, &scratch));
   GCQ_CUDA(ctx, dmalloc(&p_idx, sizeof(int64_t) * n_tiles_all, &scratch));
   GCQ_CUDA(ctx, dmalloc(&p_M, sizeof(double2) * n_tiles_all * K * 9, &scratch));
-  cudaEvent_t ev0, ev1;
+  cudaEvent_t ev0, ev1, evf;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
+  cudaEventCreate(&evf);
   float t_ent = 0.f;
   std::vector<Tile> tiles;
   std::vector<int32_t> active;
@@ -801,6 +806,12 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
                      v, d_tiles, d->d_blk, (S* const*)d->d_face, (S* const*)d->d_fib, nb, slot, d->d_row_perm,
                      d->d_col_perm, p_s3, p_idx, p_h2, p_M, K)));
     GCQ_CUDA(ctx, cudaGetLastError());
+    cudaEventRecord(evf, st);
+    d->face_launches++;
+    d->launches += 3;
+    count_launches(3);
+    for (int32_t b : active)
+      d->face_alg_bytes += (double)(slot + 1) * sizeof(SC) * 9.0 * (double)(d->h_blk[b].m * d->h_blk[b].n);
     k_block_red<<<(unsigned)active.size(), 256, 0, st>>>(d->d_blk, d_active, slot, p_s3, p_idx, p_h2, p_M, d->d_M,
                                                          K);
     GCQ_CUDA(ctx, cudaGetLastError());
@@ -819,6 +830,9 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     t_ent += ms;
+    float fms = 0.f;
+    cudaEventElapsedTime(&fms, ev0, evf);
+    d->t_face_ms += fms;
     for (int32_t b : active) d->entries += d->h_blk[b].m * d->h_blk[b].n + K;
   }
   // dense fallback blocks: all K faces
@@ -851,6 +865,8 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
                    (k_dense_fill<R, SF, KK, RR><<<(unsigned)tiles.size(), kTile, 0, st>>>(
                        v, d_t2, d->d_blk, (SF* const*)d->d_dense, d->d_row_perm, d->d_col_perm)));
       GCQ_CUDA(ctx, cudaGetLastError());
+      d->launches++;
+      count_launches(1);
       cudaEventRecord(ev1, st);
       GCQ_CUDA(ctx, cudaStreamSynchronize(st));
       float ms = 0.f;
@@ -895,6 +911,8 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
         GCQ_CUDA(ctx, cudaMemcpyAsync(d_segs, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice, st));
         k_convert<<<(unsigned)segs.size(), 256, 0, st>>>(d_segs);
         GCQ_CUDA(ctx, cudaGetLastError());
+        d->launches++;
+        count_launches(1);
       }
       GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_face, d->h_face.data(), sizeof(void*) * nb * K, cudaMemcpyHostToDevice, st));
       GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_fib, d->h_fib.data(), sizeof(void*) * nb * K, cudaMemcpyHostToDevice, st));
@@ -904,6 +922,7 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   for (void* p : slot_chunks) cudaFree(p);
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
+  cudaEventDestroy(evf);
   for (void* p : scratch) cudaFree(p);
   if (result != BEM_OK) return result;
   GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_blk, d->h_blk.data(), sizeof(BlkDev) * nb, cudaMemcpyHostToDevice, st));

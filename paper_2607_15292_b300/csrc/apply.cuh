@@ -260,12 +260,14 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
           d->d_blk, (const int4*)d->d_apply_items, (S* const*)d->d_face, (S* const*)d->d_fib, d->n_blocks,
           d->d_row_perm, d->d_col_perm, X, Y, d->K, d->n_rows, d->n_cols);
       GCQ_CUDA(ctx, cudaGetLastError());
+      count_launches(1);
     }
     if (d->n_dense > 0) {
       dim3 g((unsigned)d->n_dense, (unsigned)d->K);
       k_apply_dense<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense, d->d_row_perm,
                                              d->d_col_perm, X, Y, d->K, d->n_rows, d->n_cols, 0);
       GCQ_CUDA(ctx, cudaGetLastError());
+      count_launches(1);
     }
     return BEM_OK;
   }
@@ -275,16 +277,19 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
                                                               (S* const*)d->d_fib, d->n_blocks, d->d_zoff,
                                                               d->d_col_perm, X, (cx<A>*)d->d_z, d->K, d->n_cols);
     GCQ_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
     dim3 g((unsigned)d->n_aca, 8);
     k_contract_apply<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_aca_list, (S* const*)d->d_face, d->n_blocks, d->d_zoff,
                                               d->d_row_perm, (const cx<A>*)d->d_z, Y);
     GCQ_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
   }
   if (d->n_dense > 0) {
     dim3 g((unsigned)d->n_dense, (unsigned)d->K);
     k_apply_dense<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense, d->d_row_perm,
                                            d->d_col_perm, X, Y, d->K, d->n_rows, d->n_cols, 1);
     GCQ_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
   }
   return BEM_OK;
 }
@@ -347,6 +352,7 @@ static bem_status op_dense_t(bem_op* op, void* out, cudaStream_t st) {
                                                            (S* const*)d->d_dense, d->n_blocks, d->d_row_perm,
                                                            d->d_col_perm, (S*)out, d->K, d->n_cols);
     e = cudaGetLastError();
+    count_launches(1);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(dt);
@@ -388,6 +394,10 @@ bem_status op_stats(const bem_op* op, bem_op_stats* s) {
   s->t_entries_ms = d->t_entries_ms;
   s->t_compress_ms = d->t_compress_ms;
   s->apply_bytes = d->apply_bytes;
+  s->t_face_ms = d->t_face_ms;
+  s->face_launches = d->face_launches;
+  s->face_alg_bytes = d->face_alg_bytes;
+  s->launches = d->launches;
   return BEM_OK;
 }
 
@@ -437,6 +447,7 @@ bem_status cq_transform(int N, int64_t nvec, const void* in, void* out, bool inv
   const double lnlam = std::log(1e-10) / (2.0 * N);
   dim3 g((unsigned)((nvec + 127) / 128), (unsigned)L);
   k_cq<<<g, 128, 0, st>>>(L, lnlam, nvec, (const double2*)in, (double2*)out, inverse ? 1 : 0);
+  count_launches(1);
   return cudaGetLastError() == cudaSuccess ? BEM_OK : BEM_ERR_CUDA;
 }
 

@@ -290,18 +290,19 @@ __device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<flo
 template <int KERN, int ROWS>
 __device__ __forceinline__ bool entry_heavy(const EntryView& v, int i, int j) {
   const double* x = row_point<ROWS>(v, i);
-  if (KERN == BEM_SL) {
+  if constexpr (KERN == BEM_SL) {
     const int32_t* t = v.tri + 3 * (int64_t)j;
     if (ROWS == BEM_ROWS_NODES ? (t[0] == i || t[1] == i || t[2] == i) : j == i) return true;
     return rule_index2(v.geo[j], x) >= 2;
+  } else {
+    for (int p = v.ne_ptr[j]; p < v.ne_ptr[j + 1]; ++p) {
+      const int e = v.ne_elem[p];
+      const int32_t* t = v.tri + 3 * (int64_t)e;
+      if (ROWS == BEM_ROWS_NODES ? (t[0] == i || t[1] == i || t[2] == i) : e == i) return true;
+      if (rule_index2(v.geo[e], x) >= 2) return true;
+    }
+    return false;
   }
-  for (int p = v.ne_ptr[j]; p < v.ne_ptr[j + 1]; ++p) {
-    const int e = v.ne_elem[p];
-    const int32_t* t = v.tri + 3 * (int64_t)e;
-    if (ROWS == BEM_ROWS_NODES ? (t[0] == i || t[1] == i || t[2] == i) : e == i) return true;
-    if (rule_index2(v.geo[e], x) >= 2) return true;
-  }
-  return false;
 }
 
 template <int KERN, int ROWS>

@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -17,6 +18,9 @@
 #include "internal.h"
 
 namespace gcq {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches += n; }
 
 // ---------------------------------------------------------------------------
 // quadrature tables (host-built, uploaded once per device)
@@ -212,6 +216,7 @@ bem_status ensure_rigid_body(bem_mesh* m, cudaStream_t st) {
   EntryView v = make_view(m);
   k_rigid_body<<<(unsigned)m->n_nodes, 256, 0, st>>>(v, m->d_rb);
   GCQ_CUDA(ctx, cudaGetLastError());
+  count_launches(1);
   return BEM_OK;
 }
 
@@ -232,6 +237,7 @@ bem_status launch_entries(bem_mesh* m, int rows, int kernel, const int32_t* req,
     GCQ_DISPATCH(kernel, rows,
                  (k_entries_req<float, float2, KK, RR><<<grid, tb, 0, st>>>(v, req, n, (float2*)out, d_flag)));
   GCQ_CUDA(ctx, cudaGetLastError());
+  count_launches(1);
   return BEM_OK;
 }
 
@@ -239,3 +245,5 @@ bem_status launch_entries(bem_mesh* m, int rows, int kernel, const int32_t* req,
 
 #include "aca3d.cuh"
 #include "apply.cuh"
+
+extern "C" int64_t bem_kernel_launches(void) { return gcq::g_launches.load(); }

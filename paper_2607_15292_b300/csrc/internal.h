@@ -120,6 +120,7 @@ namespace gcq {
 
 // error helpers -------------------------------------------------------------
 bem_status set_err(bem_ctx* ctx, bem_status st, const std::string& msg);
+void count_launches(int64_t n);
 bem_status cuda_err(bem_ctx* ctx, cudaError_t e, const char* what);
 
 #define GCQ_CUDA(ctx, call)                                         \
