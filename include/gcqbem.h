@@ -135,6 +135,31 @@ void bem_mesh_destroy(bem_mesh* mesh);
 bem_status bem_entries(bem_mesh* mesh, int32_t rows, int32_t kernel,
                        const int32_t* req, int64_t n, void* out, void* stream);
 
+/* bem_entries without any device allocation.  The paper has no
+ * counterpart; this is a service to callers that cannot call cudaMalloc
+ * during the call: code running while a CUDA graph is captured, inside
+ * another framework's memory pool or real-time loop, or under a fixed,
+ * pre-reserved memory budget.  Same requests, output and precision as
+ * bem_entries; the range-check scratch that bem_entries allocates per call
+ * is a static device array of 256 words (1 KiB) instead, which every device
+ * that loads the library holds until the process exits.
+ *  - At most 16,777,216 requests per call (256 words x 65,536 requests);
+ *    larger n returns BEM_ERR_ARG before any device work.
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.  Later calls only memset, launch and copy
+ *    1 KiB back.
+ *  - All calls share the array: calls whose device work overlaps (other
+ *    streams, other host threads) race on it and must be serialised by the
+ *    caller.  The words used are reset at the start of every call.
+ *  - BEM_DL with BEM_ROWS_NODES needs the mesh's rigid-body diagonal, which
+ *    is computed (and allocated) by the first bem_entries or bem_op_compress
+ *    of that kind on the mesh; without it this call returns BEM_ERR_STATE.
+ *  - Synchronises the stream; an out-of-range request yields a NaN block and
+ *    BEM_ERR_ARG naming the first offending request. */
+bem_status bem_entries_noalloc(bem_mesh* mesh, int32_t rows, int32_t kernel,
+                               const int32_t* req, int64_t n, void* out, void* stream);
+
 /* Row/column cluster trees by PCA bisection and the block cluster tree with
  * the admissibility of Eq. (3.11) (host C++), for the given rows and
  * kernel.  Deterministic. */

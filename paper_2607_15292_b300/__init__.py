@@ -67,6 +67,7 @@ _SIGS = {
     "bem_mesh_create": (_i32, [_vp, _P(_dbl), _i64, _P(_i32), _i64, _P(_vp)]),
     "bem_mesh_destroy": (None, [_vp]),
     "bem_entries": (_i32, [_vp, _i32, _i32, _vp, _i64, _vp, _vp]),
+    "bem_entries_noalloc": (_i32, [_vp, _i32, _i32, _vp, _i64, _vp, _vp]),
     "bem_tree_build": (_i32, [_vp, _i32, _i32, _P(_vp)]),
     "bem_tree_destroy": (None, [_vp]),
     "bem_tree_sizes": (_i32, [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64)]),
@@ -207,6 +208,13 @@ class Mesh:
         tensor (n, 3, 3) (complex128 in FP64, complex64 in MIXED)."""
         n = req.shape[0]
         _check(_lib.bem_entries(self._p, rows, kernel, _dptr(req), n, _dptr(out), _stream_ptr(stream)),
+               self.ctx.ptr)
+
+    def entries_noalloc(self, rows: int, kernel: int, req, out, stream=None):
+        """As entries(), through bem_entries_noalloc: no device allocation in
+        the call (static 1 KiB scratch, at most 16,777,216 requests)."""
+        n = req.shape[0]
+        _check(_lib.bem_entries_noalloc(self._p, rows, kernel, _dptr(req), n, _dptr(out), _stream_ptr(stream)),
                self.ctx.ptr)
 
     def tree(self, rows: int, kernel: int) -> "Tree":

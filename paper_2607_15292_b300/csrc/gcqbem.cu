@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <atomic>
 #include <mutex>
@@ -241,7 +242,119 @@ bem_status launch_entries(bem_mesh* m, int rows, int kernel, const int32_t* req,
   return BEM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// no-allocation variant of the raw-request entry kernel
+//
+// For callers that must not allocate device memory during a call: code that
+// runs while a CUDA graph is being captured, inside another framework's
+// memory pool or real-time loop, or under a pre-reserved memory budget.  The
+// range-check scratch that bem_entries allocates per call lives here in a
+// file-scope device array instead: kNoAllocSlots words, word w holding the
+// smallest offending request index of requests [w * kNoAllocChunk, (w + 1) *
+// kNoAllocChunk), so one call handles at most kNoAllocSlots * kNoAllocChunk
+// requests.  Every device that loads the library holds the array (1 KiB)
+// until the process exits; all calls share it, so calls that overlap on the
+// GPU race on it.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocSlots = 256;
+constexpr int64_t kNoAllocChunk = 65536;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned int g_noalloc_scratch[kNoAllocSlots];
+static std::mutex g_noalloc_mu;
+static unsigned int* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+template <typename R, typename S, int KERN, int ROWS>
+__global__ void k_entries_req_noalloc(EntryView v, const int32_t* __restrict__ req, int64_t n, S* __restrict__ out,
+                                      unsigned int* __restrict__ slots) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = req[3 * t], j = req[3 * t + 1], k = req[3 * t + 2];
+  const int64_t nr = ROWS == BEM_ROWS_NODES ? v.n_nodes : v.n_tris;
+  const int64_t nc = KERN == BEM_SL ? v.n_tris : v.n_nodes;
+  S* o = out + 9 * t;
+  if (i < 0 || i >= nr || j < 0 || j >= nc || k < -1 || k >= v.K) {
+    for (int c = 0; c < 9; ++c) St<S>::st(o + c, {NAN, NAN});
+    atomicMin(slots + t / kNoAllocChunk, (unsigned int)(t % kNoAllocChunk));
+    return;
+  }
+  cx<double> is2;
+  const cx<double> s = freq(v, k, is2);
+  cx<double> e[9];
+  entry<R, KERN, ROWS>(v, i, j, s, is2, e);
+  for (int c = 0; c < 9; ++c) St<S>::st(o + c, e[c]);
+}
+
+// device address of the scratch for the context's (current) device, resolved
+// once per device with cudaGetSymbolAddress
+static bem_status noalloc_scratch(bem_ctx* ctx, unsigned int** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+    return set_err_c(ctx, BEM_ERR_ARG, "bem_entries_noalloc: device ordinal beyond 63");
+  if (!g_noalloc_addr[ctx->device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "bem_entries_noalloc: cudaGetSymbolAddress");
+    g_noalloc_addr[ctx->device] = static_cast<unsigned int*>(p);
+  }
+  *out = g_noalloc_addr[ctx->device];
+  return BEM_OK;
+}
+
 }  // namespace gcq
+
+extern "C" bem_status bem_entries_noalloc(bem_mesh* mesh, int32_t rows, int32_t kernel, const int32_t* req, int64_t n,
+                                          void* out, void* stream) {
+  using namespace gcq;
+  if (!mesh) return BEM_ERR_ARG;
+  bem_ctx* ctx = mesh->ctx;
+  if ((rows != BEM_ROWS_CENTROIDS && rows != BEM_ROWS_NODES) || (kernel != BEM_SL && kernel != BEM_DL) || n < 0 ||
+      (n > 0 && (!req || !out)))
+    return set_err_c(ctx, BEM_ERR_ARG, "bem_entries_noalloc: bad arguments");
+  if (n > (int64_t)kNoAllocSlots * kNoAllocChunk)
+    return set_err_c(ctx, BEM_ERR_ARG,
+                     "bem_entries_noalloc: more than 16777216 requests in one call (split the call)");
+  if (ctx->device < 0) return set_err_c(ctx, BEM_ERR_STATE, "bem_entries_noalloc: host-only context (device -1)");
+  if (!ctx->has_material) return set_err_c(ctx, BEM_ERR_STATE, "bem_entries_noalloc: material not set");
+  if (ctx->K < 1) return set_err_c(ctx, BEM_ERR_STATE, "bem_entries_noalloc: frequencies not set");
+  if (kernel == BEM_DL && rows == BEM_ROWS_NODES && !mesh->d_rb)
+    return set_err_c(ctx, BEM_ERR_STATE,
+                     "bem_entries_noalloc: rigid-body diagonal not prepared; call bem_entries or bem_op_compress "
+                     "once for this mesh with BEM_DL and BEM_ROWS_NODES first");
+  if (n == 0) return BEM_OK;
+  GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
+  unsigned int* slots = nullptr;
+  bem_status s = noalloc_scratch(ctx, &slots);
+  if (s != BEM_OK) return s;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int nslots = (int)((n + kNoAllocChunk - 1) / kNoAllocChunk);
+  GCQ_CUDA(ctx, cudaMemsetAsync(slots, 0xff, sizeof(unsigned int) * nslots, st));   // "no offending index"
+  const EntryView v = make_view(mesh);
+  const int tb = 128;
+  const unsigned grid = (unsigned)((n + tb - 1) / tb);
+  if (ctx->opt.precision == BEM_FP64)
+    GCQ_DISPATCH(kernel, rows,
+                 (k_entries_req_noalloc<double, double2, KK, RR><<<grid, tb, 0, st>>>(v, req, n, (double2*)out,
+                                                                                      slots)));
+  else
+    GCQ_DISPATCH(kernel, rows,
+                 (k_entries_req_noalloc<float, float2, KK, RR><<<grid, tb, 0, st>>>(v, req, n, (float2*)out,
+                                                                                    slots)));
+  GCQ_CUDA(ctx, cudaGetLastError());
+  count_launches(1);
+  unsigned int host[kNoAllocSlots];
+  GCQ_CUDA(ctx, cudaMemcpyAsync(host, slots, sizeof(unsigned int) * nslots, cudaMemcpyDeviceToHost, st));
+  GCQ_CUDA(ctx, cudaStreamSynchronize(st));
+  for (int w = 0; w < nslots; ++w)
+    if (host[w] != 0xffffffffu) {
+      char msg[160];
+      snprintf(msg, sizeof(msg), "bem_entries_noalloc: request %lld out of range",
+               (long long)(w * kNoAllocChunk + host[w]));
+      return set_err_c(ctx, BEM_ERR_ARG, msg);
+    }
+  return BEM_OK;
+}
+
+namespace gcq {}  // aca3d.cuh and apply.cuh reopen the namespace
 
 #include "aca3d.cuh"
 #include "apply.cuh"

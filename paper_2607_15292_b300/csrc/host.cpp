@@ -23,6 +23,14 @@ bem_status set_err(bem_ctx* ctx, bem_status st, const std::string& msg) {
   return st;
 }
 
+bem_status set_err_c(bem_ctx* ctx, bem_status st, const char* msg) {
+  if (ctx) {
+    ctx->err.assign(msg);
+    return st;
+  }
+  return set_err(nullptr, st, msg);
+}
+
 bem_status cuda_err(bem_ctx* ctx, cudaError_t e, const char* what) {
   std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
   return set_err(ctx, e == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA, m);
@@ -361,6 +369,7 @@ bem_status bem_ctx_create(const bem_options* opt, bem_ctx** out) {
   if (!ctx) return set_err(nullptr, BEM_ERR_OOM, "bem_ctx_create: host allocation");
   ctx->opt = o;
   ctx->device = o.device;
+  ctx->err.reserve(512);
   e = cudaSetDevice(o.device);
   if (e != cudaSuccess) {
     delete ctx;

@@ -120,6 +120,9 @@ namespace gcq {
 
 // error helpers -------------------------------------------------------------
 bem_status set_err(bem_ctx* ctx, bem_status st, const std::string& msg);
+// as set_err, copying into the context's preallocated message buffer (no
+// host allocation for messages shorter than its reserved capacity)
+bem_status set_err_c(bem_ctx* ctx, bem_status st, const char* msg);
 void count_launches(int64_t n);
 bem_status cuda_err(bem_ctx* ctx, cudaError_t e, const char* what);
 
