@@ -74,6 +74,8 @@ struct OpData {
   void* d_z = nullptr;               // contracted-apply scratch
   int64_t* d_zoff = nullptr;         // per aca block offset into d_z (faces x n x 3)
   int32_t* d_zitems = nullptr;       // contracted-apply z work items (int4)
+  void* d_xp = nullptr;              // batched apply: X in cluster order, K x 3 per column
+  void* d_yp = nullptr;              // batched apply: Y in cluster order, K x 3 per row
   int64_t n_zitems = 0;
   int64_t z_elems = 0;
 };

@@ -10,9 +10,6 @@
 
 namespace gcq {
 
-constexpr int kAT = 16;   // rows per apply tile
-constexpr int kAK = 16;   // frequencies per apply tile
-constexpr int kAJ = 8;    // columns per smem chunk
 
 template <typename A>
 __device__ __forceinline__ void atomic_add_c(A* p, cx<A> v) {
@@ -36,69 +33,6 @@ struct Ld<float2, float> {
     return {v.x, v.y};
   }
 };
-
-// items: (block, row tile, k tile, 0)
-template <typename S, typename A>
-__global__ void __launch_bounds__(kAT* kAK) k_apply_aca(const BlkDev* __restrict__ blk, const int4* __restrict__ items,
-                                                        S* const* __restrict__ face_tab, S* const* __restrict__ fib_tab,
-                                                        int64_t nb, const int32_t* __restrict__ row_perm,
-                                                        const int32_t* __restrict__ col_perm, const S* __restrict__ X,
-                                                        S* __restrict__ Y, int K, int64_t n_rows, int64_t n_cols) {
-  __shared__ cx<A> sH[kAT][kAJ][9];
-  __shared__ cx<A> sZ[kAJ][kAK][3];
-  __shared__ cx<A> sF[kAK][9];
-  const int4 it = items[blockIdx.x];
-  const BlkDev& B = blk[it.x];
-  const int ti = threadIdx.x / kAK, tk = threadIdx.x % kAK;
-  const int64_t li = (int64_t)it.y * kAT + ti;
-  const int k = it.z * kAK + tk;
-  cx<A> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-  for (int p = 0; p < B.rank; ++p) {
-    const S* H = face_tab[(int64_t)p * nb + it.x];
-    const S* f = fib_tab[(int64_t)p * nb + it.x];
-    __syncthreads();
-    for (int c = threadIdx.x; c < kAK * 9; c += blockDim.x) {
-      const int kk = it.z * kAK + c / 9;
-      sF[c / 9][c % 9] = kk < K ? Ld<S, A>::ld(f + (int64_t)kk * 9 + c % 9) : cx<A>{0, 0};
-    }
-    for (int64_t j0 = 0; j0 < B.n; j0 += kAJ) {
-      __syncthreads();
-      for (int c = threadIdx.x; c < kAT * kAJ * 9; c += blockDim.x) {
-        const int r = c / (kAJ * 9), rem = c % (kAJ * 9), jj = rem / 9, q = rem % 9;
-        const int64_t gi = (int64_t)it.y * kAT + r, gj = j0 + jj;
-        sH[r][jj][q] = (gi < B.m && gj < B.n) ? Ld<S, A>::ld(H + (gi * B.n + gj) * 9 + q) : cx<A>{0, 0};
-      }
-      for (int c = threadIdx.x; c < kAJ * kAK; c += blockDim.x) {
-        const int kk = c / kAJ, jj = c % kAJ;
-        const int64_t gj = j0 + jj;
-        const int kg = it.z * kAK + kk;
-        cx<A> x[3] = {{0, 0}, {0, 0}, {0, 0}};
-        if (gj < B.n && kg < K) {
-          const S* xp = X + ((int64_t)kg * n_cols + col_perm[B.c0 + gj]) * 3;
-          for (int b = 0; b < 3; ++b) x[b] = Ld<S, A>::ld(xp + b);
-        }
-        for (int a = 0; a < 3; ++a) {
-          cx<A> z = {0, 0};
-          for (int b = 0; b < 3; ++b) z = cfma(sF[kk][3 * a + b], x[b], z);
-          sZ[jj][kk][a] = z;
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int jj = 0; jj < kAJ; ++jj)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const cx<A> z = sZ[jj][tk][b];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) acc[a] = cfma(sH[ti][jj][3 * a + b], z, acc[a]);
-        }
-    }
-  }
-  if (li < B.m && k < K) {
-    A* y = (A*)(Y + ((int64_t)k * n_rows + row_perm[B.r0 + li]) * 3);
-    for (int a = 0; a < 3; ++a) atomic_add_c(y + 2 * a, acc[a]);
-  }
-}
 
 // dense fallback blocks: Y_k[rows] += D_k X_k[cols]; CTA per (block, k), warp per row
 template <typename S, typename A>
@@ -191,13 +125,127 @@ __global__ void k_contract_apply(const BlkDev* __restrict__ blk, const int32_t* 
   }
 }
 
+// ---- batched apply of 3D-ACA blocks, frequency-contiguous layout ------------
+// Xp: n_cols x K x 3 and Yp: n_rows x K x 3 complex in cluster order.  A CTA
+// owns kBM rows x kBK frequencies of one block and streams every face of the
+// block once through shared memory in chunks of kBN columns:
+//   Z[j][a][k] = sum_b f_p[k][a][b] x_k[j][b]      (fibre transform, per chunk)
+//   Y[i][k][a] += sum_j sum_b H_p[i][j][a][b] Z[j][b][k]
+// Each thread accumulates 8 frequencies x 3 components of one row in registers;
+// the block's result is added to Yp once (atomics) after all faces.
+constexpr int kBM = 32, kBK = 64, kBN = 16, kTPR = 8;
+constexpr int kSHR = kBN * 9 + 1;   // padded row stride of the face tile (no bank conflicts)
+constexpr int kApplyThreads = kBM * kTPR;   // 256
+
+template <typename S, typename A>
+__global__ void __launch_bounds__(kApplyThreads) k_apply_faces(const BlkDev* __restrict__ blk,
+                                                               const int4* __restrict__ items,
+                                                               S* const* __restrict__ face_tab,
+                                                               S* const* __restrict__ fib_tab, int64_t nb,
+                                                               const S* __restrict__ Xp, A* __restrict__ Yp, int K) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<A>* sH = reinterpret_cast<cx<A>*>(smem_raw);       // [kBM][kBN * 9 + 1] (padded rows)
+  cx<A>* sZ = sH + kBM * kSHR;                           // [kBN][3][kBK]
+  cx<A>* sF = sZ + kBN * 3 * kBK;                        // [kBK][9]
+  const int4 it = items[blockIdx.x];
+  const BlkDev& B = blk[it.x];
+  const int r = threadIdx.x / kTPR, kq = threadIdx.x % kTPR;
+  const int64_t i0 = (int64_t)it.y * kBM;
+  const int k0 = it.z * kBK;
+  const int nk = min(kBK, K - k0);
+  cx<A> acc[kBK / kTPR][3];
+#pragma unroll
+  for (int t = 0; t < kBK / kTPR; ++t)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc[t][a] = {A(0), A(0)};
+  for (int p = 0; p < B.rank; ++p) {
+    const S* H = face_tab[(int64_t)p * nb + it.x];
+    const S* f = fib_tab[(int64_t)p * nb + it.x];
+    __syncthreads();
+    for (int c = threadIdx.x; c < kBK * 9; c += blockDim.x) {
+      const int kk = c / 9;
+      sF[c] = kk < nk ? Ld<S, A>::ld(f + (int64_t)(k0 + kk) * 9 + c % 9) : cx<A>{A(0), A(0)};
+    }
+    for (int64_t j0 = 0; j0 < B.n; j0 += kBN) {
+      __syncthreads();
+      for (int c = threadIdx.x; c < kBM * kBN * 9; c += blockDim.x) {
+        const int rr = c / (kBN * 9), rem = c % (kBN * 9), jj = rem / 9;
+        const int64_t gi = i0 + rr, gj = j0 + jj;
+        sH[rr * kSHR + rem] = (gi < B.m && gj < B.n) ? Ld<S, A>::ld(H + (gi * B.n + gj) * 9 + rem % 9) : cx<A>{A(0), A(0)};
+      }
+      for (int c = threadIdx.x; c < kBN * kBK; c += blockDim.x) {
+        const int jj = c / kBK, kk = c % kBK;
+        const int64_t gj = j0 + jj;
+        cx<A> x[3] = {{A(0), A(0)}, {A(0), A(0)}, {A(0), A(0)}};
+        if (gj < B.n && kk < nk) {
+          const S* xp = Xp + ((B.c0 + gj) * K + k0 + kk) * 3;
+          for (int b = 0; b < 3; ++b) x[b] = Ld<S, A>::ld(xp + b);
+        }
+        for (int a = 0; a < 3; ++a) {
+          cx<A> z = {A(0), A(0)};
+          for (int b = 0; b < 3; ++b) z = cfma(sF[kk * 9 + 3 * a + b], x[b], z);
+          sZ[(jj * 3 + a) * kBK + kk] = z;
+        }
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int jj = 0; jj < kBN; ++jj) {
+        cx<A> h[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) h[c] = sH[r * kSHR + jj * 9 + c];
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int t = 0; t < kBK / kTPR; ++t) {
+            const cx<A> z = sZ[(jj * 3 + b) * kBK + kq + kTPR * t];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[t][a] = cfma(h[3 * a + b], z, acc[t][a]);
+          }
+      }
+    }
+  }
+  const int64_t gi = i0 + r;
+  if (gi < B.m)
+#pragma unroll
+    for (int t = 0; t < kBK / kTPR; ++t) {
+      const int kk = kq + kTPR * t;
+      if (kk < nk) {
+        A* y = Yp + (((B.r0 + gi) * K + k0 + kk) * 3) * 2;
+        for (int a = 0; a < 3; ++a) atomic_add_c(y + 2 * a, acc[t][a]);
+      }
+    }
+}
+
+// X[k][col][c] -> Xp[pos][k][c] (cluster order), Yp[pos][k][c] -> Y[k][row][c]
+template <typename S>
+__global__ void k_perm_x(const S* __restrict__ X, S* __restrict__ Xp, const int32_t* __restrict__ perm, int64_t n,
+                         int K) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * K) return;
+  const int64_t pos = t / K;
+  const int k = (int)(t - pos * K);
+  const S* src = X + ((int64_t)k * n + perm[pos]) * 3;
+  S* dst = Xp + t * 3;
+  for (int c = 0; c < 3; ++c) dst[c] = src[c];
+}
+template <typename S>
+__global__ void k_unperm_y(const S* __restrict__ Yp, S* __restrict__ Y, const int32_t* __restrict__ perm, int64_t n,
+                           int K) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * K) return;
+  const int64_t pos = t / K;
+  const int k = (int)(t - pos * K);
+  const S* src = Yp + t * 3;
+  S* dst = Y + ((int64_t)k * n + perm[pos]) * 3;
+  for (int c = 0; c < 3; ++c) dst[c] = src[c];
+}
+
 bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
   std::vector<int4> items;
   std::vector<int32_t> dense, aca;
   std::vector<int64_t> zoff;
   std::vector<int4> zitems;   // (block, face, 128-column chunk, aca index)
   int64_t z = 0;
-  const int nkt = (d->K + kAK - 1) / kAK;
   for (int64_t b = 0; b < d->n_blocks; ++b) {
     const BlkDev& B = d->h_blk[b];
     if (B.status == ST_DENSE) dense.push_back((int32_t)b);
@@ -207,8 +255,8 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
       aca.push_back((int32_t)b);
       zoff.push_back(z);
       z += (int64_t)B.rank * B.n * 3;
-      for (int64_t rt = 0; rt * kAT < B.m; ++rt)
-        for (int kt = 0; kt < nkt; ++kt) items.push_back(make_int4((int)b, (int)rt, kt, 0));
+      for (int64_t rt = 0; rt * kBM < B.m; ++rt)
+        for (int kt = 0; kt * kBK < d->K; ++kt) items.push_back(make_int4((int)b, (int)rt, kt, 0));
     }
   }
   std::vector<void*>* own = &d->allocs;
@@ -224,7 +272,10 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
   GCQ_CUDA(ctx, dmalloc(&d->d_zitems, sizeof(int4) * std::max<size_t>(1, zitems.size()), own));
   if (!zitems.empty())
     GCQ_CUDA(ctx, cudaMemcpy(d->d_zitems, zitems.data(), sizeof(int4) * zitems.size(), cudaMemcpyHostToDevice));
-  const size_t zb = (d->prec == BEM_FP64 ? sizeof(double2) : sizeof(float2)) * std::max<int64_t>(1, z);
+  const size_t es = d->prec == BEM_FP64 ? sizeof(double2) : sizeof(float2);
+  GCQ_CUDA(ctx, dmalloc(&d->d_xp, es * 3 * (size_t)d->K * d->n_cols, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_yp, es * 3 * (size_t)d->K * d->n_rows, own));
+  const size_t zb = es * std::max<int64_t>(1, z);
   GCQ_CUDA(ctx, dmalloc(&d->d_z, zb, own));
   if (!items.empty())
     GCQ_CUDA(ctx, cudaMemcpy(d->d_apply_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
@@ -235,14 +286,14 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
     GCQ_CUDA(ctx, cudaMemcpy(d->d_zoff, zoff.data(), sizeof(int64_t) * zoff.size(), cudaMemcpyHostToDevice));
   }
   // algorithmic bytes of one batched apply: stored operator + X + Y
-  const int64_t es = d->prec == BEM_FP64 ? 16 : 8;
+  const int64_t esb = (int64_t)es;
   int64_t stored = 0;
   for (int64_t b = 0; b < d->n_blocks; ++b) {
     const BlkDev& B = d->h_blk[b];
-    if (B.status == ST_DENSE) stored += (int64_t)d->K * B.m * B.n * 9 * es;
-    if (B.status == ST_DONE) stored += (int64_t)B.rank * (B.m * B.n + d->K) * 9 * es;
+    if (B.status == ST_DENSE) stored += (int64_t)d->K * B.m * B.n * 9 * esb;
+    if (B.status == ST_DONE) stored += (int64_t)B.rank * (B.m * B.n + d->K) * 9 * esb;
   }
-  d->apply_bytes = stored + (int64_t)d->K * (d->n_rows + d->n_cols) * 3 * es;
+  d->apply_bytes = stored + (int64_t)d->K * (d->n_rows + d->n_cols) * 3 * esb;
   return BEM_OK;
 }
 
@@ -252,16 +303,26 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
   bem_ctx* ctx = op->tree->mesh->ctx;
   const S* X = (const S*)Xv;
   S* Y = (S*)Yv;
-  const int64_t ny = mode == BEM_APPLY_BATCHED ? (int64_t)d->K * d->n_rows * 3 : d->n_rows * 3;
-  GCQ_CUDA(ctx, cudaMemsetAsync(Y, 0, sizeof(S) * ny, st));
+  if (mode != BEM_APPLY_BATCHED) GCQ_CUDA(ctx, cudaMemsetAsync(Y, 0, sizeof(S) * d->n_rows * 3, st));
   if (mode == BEM_APPLY_BATCHED) {
+    const int64_t nx = (int64_t)d->n_cols * d->K, nyp = (int64_t)d->n_rows * d->K;
+    k_perm_x<S><<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(X, (S*)d->d_xp, d->d_col_perm, d->n_cols, d->K);
+    GCQ_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
+    GCQ_CUDA(ctx, cudaMemsetAsync(d->d_yp, 0, sizeof(S) * 3 * nyp, st));
     if (d->n_apply_items > 0) {
-      k_apply_aca<S, A><<<(unsigned)d->n_apply_items, kAT * kAK, 0, st>>>(
+      const size_t smem = sizeof(cx<A>) * (kBM * kSHR + kBN * 3 * kBK + kBK * 9);
+      cudaFuncSetAttribute(k_apply_faces<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_apply_faces<S, A><<<(unsigned)d->n_apply_items, kApplyThreads, smem, st>>>(
           d->d_blk, (const int4*)d->d_apply_items, (S* const*)d->d_face, (S* const*)d->d_fib, d->n_blocks,
-          d->d_row_perm, d->d_col_perm, X, Y, d->K, d->n_rows, d->n_cols);
+          (const S*)d->d_xp, (A*)d->d_yp, d->K);
       GCQ_CUDA(ctx, cudaGetLastError());
       count_launches(1);
     }
+    k_unperm_y<S><<<(unsigned)((nyp + 255) / 256), 256, 0, st>>>((const S*)d->d_yp, Y, d->d_row_perm, d->n_rows,
+                                                                 d->K);
+    GCQ_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
     if (d->n_dense > 0) {
       dim3 g((unsigned)d->n_dense, (unsigned)d->K);
       k_apply_dense<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense, d->d_row_perm,

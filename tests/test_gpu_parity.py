@@ -192,3 +192,26 @@ def test_aca3d_against_oracle_compression_config1():
     assert np.linalg.norm(C - D) / nD < 10 * eps
     assert np.linalg.norm(Co - D) / nD < 10 * eps
     assert np.linalg.norm(C - Co) / nD < 20 * eps
+
+
+# --------------------------------------------------------------------------
+# CQ transforms (scaled DFT over the frequency circle)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N,nvec", [(16, 7), (64, 1000), (128, 33)])
+def test_cq_transforms_match_oracle(N, nvec):
+    from oracle import cq
+    L = N + 1
+    g_host = syn.complex_normal(5, (L, nvec))
+    gin = torch.tensor(g_host, dtype=torch.complex128, device="cuda")
+    gh = torch.empty_like(gin)
+    g.cq_forward(N, nvec, gin, gh)
+    want = cq.forward(g_host, N)
+    got = gh.cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    back = torch.empty_like(gin)
+    g.cq_inverse(N, nvec, gh, back)
+    # the inverse scales level n by lam^-n (up to 1e5): rounding grows with it
+    scale = (cq.lam_c(N) ** -np.arange(L))[:, None] * np.abs(want).max() / L
+    err = np.abs(back.cpu().numpy() - cq.inverse(want, N))
+    assert (err <= 1e-12 * scale).all()
+    assert (np.abs(back.cpu().numpy() - g_host) <= 1e-12 * scale + 1e-13 * np.abs(g_host).max()).all()
