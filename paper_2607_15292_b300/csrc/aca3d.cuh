@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restr
       fl[c] = 0.f;
     }
     const bool heavy = ok && entry_heavy<KERN, ROWS>(v, i, j);
-    if (ok && !heavy) entry_f<KERN, ROWS>(v, i, j, sf32, is32, 0, 1, fh);
+    if (ok && !heavy) entry_f<KERN, ROWS>(v, i, j, sf32, is32, kd, 0, 1, fh);
     unsigned hm = __ballot_sync(0xffffffffu, heavy);
     const int lane = threadIdx.x & 31;
     while (hm) {
@@ -311,13 +311,13 @@ __global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restr
       hm &= hm - 1;
       const int iL = __shfl_sync(0xffffffffu, i, L), jL = __shfl_sync(0xffffffffu, j, L);
       float part[18];
-      entry_f_warp<KERN, ROWS>(v, iL, jL, sf32, is32, part);
+      entry_f_warp<KERN, ROWS>(v, iL, jL, sf32, is32, kd, part);
       if (lane == L)
         for (int c = 0; c < 18; ++c) fh[c] = part[c];
     }
   } else {
     for (int c = 0; c < 9; ++c) Hd64[c] = {0, 0};
-    if (ok) entry<R, KERN, ROWS>(v, i, j, s, is2, Hd64);
+    if (ok) entry<R, KERN, ROWS>(v, i, j, kd, s, is2, Hd64);
   }
   // residual: H = E - sum_p H_p[i,j] f_p[k_d]
   for (int p0 = 0; p0 < slot; p0 += 64) {
@@ -547,7 +547,7 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
     cx<double> E[9];
     cx<double> is2;
     cx<double> s = freq(v, k, is2);
-    entry<R, KERN, ROWS>(v, i, j, s, is2, E);
+    entry<R, KERN, ROWS>(v, i, j, k, s, is2, E);
     for (int p = 0; p < slot; ++p) {
       const S* Hp = face_tab[(int64_t)p * nb + b] + B.piv * 9;
       const S* fp = fib_tab[(int64_t)p * nb + b] + (int64_t)k * 9;
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(kTile) k_dense_fill(EntryView v, const Tile* _
   cx<double> is2;
   cx<double> s = freq(v, t.k, is2);
   cx<double> H[9];
-  entry<R, KERN, ROWS>(v, i, j, s, is2, H);
+  entry<R, KERN, ROWS>(v, i, j, t.k, s, is2, H);
   S* out = dense[t.blk] + ((int64_t)t.k * B.m * B.n + e) * 9;
   for (int c = 0; c < 9; ++c) St<S>::st(out + c, H[c]);
 }

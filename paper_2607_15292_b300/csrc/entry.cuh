@@ -125,47 +125,51 @@ struct SeriesLen<float> {
   static constexpr double z = 2.0;
 };
 
-// A, B (and A', B' if D) at distance r and frequency s; DYN subtracts the
-// static (s = 0) values (bounded remainder next to a singular point).
+// Series branch: A, B (and A', B' if D) from the Taylor series in
+// w = -s r / c2; DYN drops the m = 0 (static) term.
 template <typename R, bool D, bool DYN>
-__device__ __forceinline__ void kernel_coeffs(const KC<R>& k, R r, cx<R> s, cx<R> is2, cx<R>& A, cx<R>& B,
-                                              cx<R>& dA, cx<R>& dB) {
+__device__ __forceinline__ void series_coeffs(const KC<R>& k, R r, cx<R> w, cx<R>& A, cx<R>& B, cx<R>& dA,
+                                              cx<R>& dB, cx<R>& S3) {
   const R ir = R(1) / r;
-  cx<R> w = mk<R>(-s.x * r * k.ic2, -s.y * r * k.ic2);
-  if (w.x * w.x + w.y * w.y < R(SeriesLen<R>::z * SeriesLen<R>::z)) {
-    constexpr int M = SeriesLen<R>::n;
-    const int m0 = DYN ? 1 : 0;
-    cx<R> pa = mk<R>(k.ta[M - 1], R(0)), pb = mk<R>(k.tb[M - 1], R(0));
-    cx<R> qa = mk<R>(R(M - 2) * k.ta[M - 1], R(0)), qb = mk<R>(R(M - 2) * k.tb[M - 1], R(0));
+  constexpr int M = SeriesLen<R>::n;
+  const int m0 = DYN ? 1 : 0;
+  cx<R> pa = mk<R>(k.ta[M - 1], R(0)), pb = mk<R>(k.tb[M - 1], R(0));
+  cx<R> qa = mk<R>(R(M - 2) * k.ta[M - 1], R(0)), qb = mk<R>(R(M - 2) * k.tb[M - 1], R(0));
 #pragma unroll
-    for (int m = M - 2; m >= m0; --m) {
-      pa = cfma(pa, w, mk<R>(k.ta[m], R(0)));
-      pb = cfma(pb, w, mk<R>(k.tb[m], R(0)));
-      if (D) {
-        qa = cfma(qa, w, mk<R>(R(m - 1) * k.ta[m], R(0)));
-        qb = cfma(qb, w, mk<R>(R(m - 1) * k.tb[m], R(0)));
-      }
-    }
-    if (DYN) {  // the polynomials above started at m = 1: multiply by w
-      pa = pa * w;
-      pb = pb * w;
-      qa = qa * w;
-      qb = qb * w;
-    }
-    const R f = k.ic2s * ir;
-    A = f * pa;
-    B = f * pb;
+  for (int m = M - 2; m >= m0; --m) {
+    pa = cfma(pa, w, mk<R>(k.ta[m], R(0)));
+    pb = cfma(pb, w, mk<R>(k.tb[m], R(0)));
     if (D) {
-      dA = (f * ir) * qa;
-      dB = (f * ir) * qb;
+      qa = cfma(qa, w, mk<R>(R(m - 1) * k.ta[m], R(0)));
+      qb = cfma(qb, w, mk<R>(R(m - 1) * k.tb[m], R(0)));
     }
-    return;
   }
+  if (DYN) {  // the polynomials above started at m = 1: multiply by w
+    pa = pa * w;
+    pb = pb * w;
+    qa = qa * w;
+    qb = qb * w;
+  }
+  const R f = k.ic2s * ir;
+  A = f * pa;
+  B = f * pb;
+  if (D) {
+    dA = (f * ir) * qa;
+    dB = (f * ir) * qb;
+    S3 = dA + dB + (R(2) * ir) * B;
+  }
+}
+
+// Closed form with given k_a r (kr1, kr2) and exponentials e_a = exp(-k_a r).
+// S3 = A' + B' + 2 B / r, the combination of the traction kernel's n_i rh_j
+// term: in closed form the c2-wave parts cancel exactly and
+//   S3 = -(k1 r + 1) exp(-k1 r) / (c1^2 r^2),
+// which is evaluated directly (no cancellation).
+template <typename R, bool D, bool DYN>
+__device__ __forceinline__ void closed_coeffs(const KC<R>& k, R r, cx<R> kr1, cx<R> kr2, cx<R> e1, cx<R> e2,
+                                              cx<R> is2, cx<R>& A, cx<R>& B, cx<R>& dA, cx<R>& dB, cx<R>& S3) {
+  const R ir = R(1) / r;
   const R ir2 = ir * ir, ir3 = ir2 * ir;
-  // wave 1 (c1) and wave 2 (c2)
-  cx<R> kr1 = mk<R>(s.x * r * k.ic1, s.y * r * k.ic1);
-  cx<R> kr2 = mk<R>(s.x * r * k.ic2, s.y * r * k.ic2);
-  cx<R> e1 = cexp_neg(kr1), e2 = cexp_neg(kr2);
   cx<R> kk1 = kr1 * kr1, kk2 = kr2 * kr2;
   cx<R> P1 = (ir3 * e1) * (kr1 + mk<R>(R(1), R(0)));
   cx<R> P2 = (ir3 * e2) * (kr2 + mk<R>(R(1), R(0)));
@@ -178,6 +182,7 @@ __device__ __forceinline__ void kernel_coeffs(const KC<R>& k, R r, cx<R> s, cx<R
     cx<R> R2 = (-ir3 * ir * e2) * (kk2 * kr2 + R(4) * kk2 + R(9) * kr2 + mk<R>(R(9), R(0)));
     dA = (-r * k.ic2s) * P2 + ir * B;
     dB = (R1 - R2) * is2;
+    S3 = (-ir2 * k.ic1 * k.ic1) * (e1 * (kr1 + mk<R>(R(1), R(0))));
   }
   if (DYN) {
     A.x -= k.alpha * ir;
@@ -185,8 +190,60 @@ __device__ __forceinline__ void kernel_coeffs(const KC<R>& k, R r, cx<R> s, cx<R
     if (D) {
       dA.x += k.alpha * ir2;
       dB.x += k.beta * ir2;
+      // static S3 = (beta - alpha) / r^2 = -1 / (c1^2 r^2)
+      S3.x += k.ic1 * k.ic1 * ir2;
     }
   }
+}
+
+// A, B (and A', B' if D) at distance r and frequency s; DYN subtracts the
+// static (s = 0) values (bounded remainder next to a singular point).
+template <typename R, bool D, bool DYN>
+__device__ __forceinline__ void kernel_coeffs(const KC<R>& k, R r, cx<R> s, cx<R> is2, cx<R>& A, cx<R>& B,
+                                              cx<R>& dA, cx<R>& dB, cx<R>& S3) {
+  cx<R> w = mk<R>(-s.x * r * k.ic2, -s.y * r * k.ic2);
+  if (w.x * w.x + w.y * w.y < R(SeriesLen<R>::z * SeriesLen<R>::z)) {
+    series_coeffs<R, D, DYN>(k, r, w, A, B, dA, dB, S3);
+    return;
+  }
+  cx<R> kr1 = mk<R>(s.x * r * k.ic1, s.y * r * k.ic1);
+  cx<R> kr2 = mk<R>(s.x * r * k.ic2, s.y * r * k.ic2);
+  closed_coeffs<R, D, DYN>(k, r, kr1, kr2, cexp_neg(kr1), cexp_neg(kr2), is2, A, B, dA, dB, S3);
+}
+
+// accumulate w U into (SA, SB[6]) from the coefficients, unit vector h
+template <typename R>
+__device__ __forceinline__ void acc_U_from(R wq, const R* h, cx<R> A, cx<R> B, cx<R>& SA, cx<R>* SB) {
+  SA = SA + wq * A;
+  cx<R> wb = wq * B;
+  SB[0] = SB[0] + (h[0] * h[0]) * wb;
+  SB[1] = SB[1] + (h[0] * h[1]) * wb;
+  SB[2] = SB[2] + (h[0] * h[2]) * wb;
+  SB[3] = SB[3] + (h[1] * h[1]) * wb;
+  SB[4] = SB[4] + (h[1] * h[2]) * wb;
+  SB[5] = SB[5] + (h[2] * h[2]) * wb;
+}
+
+// accumulate w T^T (double-layer integrand) from the coefficients
+template <typename R>
+__device__ __forceinline__ void acc_TT_from(const KC<R>& k, R wq, R r, const R* h, const R* n, cx<R> A, cx<R> B,
+                                            cx<R> dA, cx<R> dB, cx<R> S3, cx<R>* acc) {
+  (void)A;
+  const R ir = R(1) / r;
+  cx<R> Bir = ir * B;
+  cx<R> f1 = (wq * k.c2s * k.inv4pi) * (dA + Bir);
+  cx<R> f2 = (wq * R(2) * k.c2s * k.inv4pi) * (dB - R(2) * Bir);
+  cx<R> f3 = (wq * k.inv4pi) * ((k.c1s - R(2) * k.c2s) * S3 + (R(2) * k.c2s) * Bir);
+  R rn = h[0] * n[0] + h[1] * n[1] + h[2] * n[2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      R c1v = (a == b ? rn : R(0)) + h[b] * n[a];
+      R c2v = rn * h[a] * h[b];
+      R c3v = n[b] * h[a];
+      acc[3 * a + b] = acc[3 * a + b] + c1v * f1 + c2v * f2 + c3v * f3;
+    }
 }
 
 // accumulate w U(d) into (SA, SB[6]): U = (SA I + SB) / (4 pi rho)
@@ -196,8 +253,8 @@ __device__ __forceinline__ void acc_U(const KC<R>& k, R wq, R dx, R dy, R dz, cx
   R r = sqrt(dx * dx + dy * dy + dz * dz);
   R ir = R(1) / r;
   R h[3] = {dx * ir, dy * ir, dz * ir};
-  cx<R> A, B, dA, dB;
-  kernel_coeffs<R, false, false>(k, r, s, is2, A, B, dA, dB);
+  cx<R> A, B, dA, dB, S3;
+  kernel_coeffs<R, false, false>(k, r, s, is2, A, B, dA, dB, S3);
   SA = SA + wq * A;
   cx<R> wb = wq * B;
   SB[0] = SB[0] + (h[0] * h[0]) * wb;
@@ -209,29 +266,16 @@ __device__ __forceinline__ void acc_U(const KC<R>& k, R wq, R dx, R dy, R dz, cx
 }
 
 // accumulate w T^T(d, n) (double-layer integrand, 9 entries [a*3+b] = T_ba)
+
 template <typename R, bool DYN>
 __device__ __forceinline__ void acc_TT(const KC<R>& k, R wq, R dx, R dy, R dz, const R* n, cx<R> s, cx<R> is2,
                                        cx<R>* acc) {
   R r = sqrt(dx * dx + dy * dy + dz * dz);
   R ir = R(1) / r;
   R h[3] = {dx * ir, dy * ir, dz * ir};
-  cx<R> A, B, dA, dB;
-  kernel_coeffs<R, true, DYN>(k, r, s, is2, A, B, dA, dB);
-  cx<R> Bir = ir * B;
-  cx<R> f1 = (wq * k.c2s * k.inv4pi) * (dA + Bir);
-  cx<R> f2 = (wq * R(2) * k.c2s * k.inv4pi) * (dB - R(2) * Bir);
-  cx<R> f3 = (wq * k.inv4pi) * ((k.c1s - R(2) * k.c2s) * (dA + dB + R(2) * Bir) + (R(2) * k.c2s) * Bir);
-  R rn = h[0] * n[0] + h[1] * n[1] + h[2] * n[2];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      // T_ba = f1 (rn d_ba + rh_b n_a) + f2 rn rh_b rh_a + f3 n_b rh_a
-      R c1v = (a == b ? rn : R(0)) + h[b] * n[a];
-      R c2v = rn * h[a] * h[b];
-      R c3v = n[b] * h[a];
-      acc[3 * a + b] = acc[3 * a + b] + c1v * f1 + c2v * f2 + c3v * f3;
-    }
+  cx<R> A, B, dA, dB, S3;
+  kernel_coeffs<R, true, DYN>(k, r, s, is2, A, B, dA, dB, S3);
+  acc_TT_from<R>(k, wq, r, h, n, A, B, dA, dB, S3, acc);
 }
 
 // static Kelvin T0^T (real), [a*3+b] = T0_ba
@@ -273,6 +317,8 @@ struct EntryView {
   const double* rb;          // n_nodes x 9 (node rows, double layer) or null
   const double2* s;          // K
   const double2* inv_s2;     // K
+  const float4* sw;          // [K][2] s_k / c_a float-float (MIXED path)
+  const float4* ef;          // [n_tris][4] FP32 element frames (MIXED path)
   int64_t n_nodes, n_tris;
   int32_t K;
   double nu;

@@ -127,9 +127,101 @@ __device__ __forceinline__ void vert_f(const FrameF& f, int a, float* P) {
   for (int k = 0; k < 3; ++k) P[k] = a == 0 ? 0.f : (a == 1 ? f.e1[k] : f.e2[k]);
 }
 
+// exp(-s r0 / c_a), a = 1, 2, at a reference distance r0 (an FP32 number):
+// the phase (Im s / c_a) r0 is formed as a float-float product and reduced
+// modulo 2 pi with a two-part 2 pi; the magnitude exp(-(Re s / c_a) r0) gets
+// the low part of its exponent as a first-order factor.  Removes the FP32
+// error proportional to |s| r / c of exp(-s r / c) evaluated at full r.
+__device__ __forceinline__ void ref_exp(const EntryView& v, int k, float r0, cx<float>* E0, cx<float>* w) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const float4 q = v.sw[2 * k + a];   // (re_hi, re_lo, im_hi, im_lo) of s_k / c_a
+    w[a] = {q.x, q.z};
+    const float ph = q.z * r0;
+    float pe = fmaf(q.z, r0, -ph);
+    pe = fmaf(q.w, r0, pe);
+    const float nt = rintf(ph * 0.159154943091895336f);
+    float t = fmaf(-nt, 6.28318548202514648f, ph);   // 2 pi = 6.2831854820 - 1.7484556e-7
+    t = fmaf(nt, 1.74845553e-07f, t) + pe;
+    const float mg = q.x * r0;
+    float me = fmaf(q.x, r0, -mg);
+    me = fmaf(q.y, r0, me);
+    const float mag = expf(-mg) * (1.f - me);
+    float sn, cs;
+    sincosf(t, &sn, &cs);
+    E0[a] = {mag * cs, -mag * sn};
+  }
+}
+
+// reference data of a regular element integral for row point x: D = c - x
+// (FP64 difference rounded once), r0 = |D| rounded to FP32, c0 = |D|^2 - r0^2,
+// and the quadrature rule chosen from |D|^2 (same decision as the FP64 path)
+struct RefF {
+  float D[3], r0, c0;
+  int ri;
+  bool use;
+};
+__device__ __forceinline__ RefF ref_f(const ElemGeo& g, const double* x, float s_abs) {
+  RefF R;
+  const double dx = g.c[0] - x[0], dy = g.c[1] - x[1], dz = g.c[2] - x[2];
+  const double d2 = dx * dx + dy * dy + dz * dz;
+  const double hb = g.h * (1.0 - 1e-12);
+  const double h2 = hb * hb;
+  R.ri = d2 >= rule_dist(0) * rule_dist(0) * h2 ? 0
+       : d2 >= rule_dist(1) * rule_dist(1) * h2 ? 1
+       : d2 >= rule_dist(2) * rule_dist(2) * h2 ? 2 : 3;
+  R.D[0] = (float)dx;
+  R.D[1] = (float)dy;
+  R.D[2] = (float)dz;
+  R.r0 = sqrtf((float)d2);
+  R.c0 = (float)(d2 - (double)R.r0 * (double)R.r0);
+  R.use = false;
+  (void)s_abs;
+  return R;
+}
+
+// geometry of regular point (xi, eta): d = y - x, r = |d|, dr = r - r0
+// computed from the small offset dd = y - c without cancellation
+__device__ __forceinline__ void ref_point(const RefF& R, const float4& a0, const float4& e1, const float4& e2,
+                                          float xi, float et, float* d, float& r, float& dr) {
+  const float dd0 = a0.x + xi * e1.x + et * e2.x;
+  const float dd1 = a0.y + xi * e1.y + et * e2.y;
+  const float dd2 = a0.z + xi * e1.z + et * e2.z;
+  d[0] = R.D[0] + dd0;
+  d[1] = R.D[1] + dd1;
+  d[2] = R.D[2] + dd2;
+  r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  const float num = R.c0 + 2.f * (R.D[0] * dd0 + R.D[1] * dd1 + R.D[2] * dd2) + (dd0 * dd0 + dd1 * dd1 + dd2 * dd2);
+  dr = num / (r + R.r0);
+}
+
+// kernel coefficients at a regular point: series for |s| r / c2 < 2, else the
+// closed form with exp(-s r / c_a) = E0_a exp(-s dr / c_a) when the reference
+// is in use (large |s| r0 / c2), or evaluated directly
+template <bool D>
+__device__ __forceinline__ void coeffs_ref(const KC<float>& k, float r, float dr, cx<float> s, cx<float> is2,
+                                           bool use, const cx<float>* E0, const cx<float>* w, cx<float>& A,
+                                           cx<float>& B, cx<float>& dA, cx<float>& dB, cx<float>& S3) {
+  const cx<float> ws = {-s.x * r * k.ic2, -s.y * r * k.ic2};
+  if (ws.x * ws.x + ws.y * ws.y < 4.f) {
+    series_coeffs<float, D, false>(k, r, ws, A, B, dA, dB, S3);
+    return;
+  }
+  const cx<float> kr1 = {w[0].x * r, w[0].y * r}, kr2 = {w[1].x * r, w[1].y * r};
+  cx<float> e1, e2;
+  if (use) {
+    e1 = E0[0] * cexp_neg(cx<float>{w[0].x * dr, w[0].y * dr});
+    e2 = E0[1] * cexp_neg(cx<float>{w[1].x * dr, w[1].y * dr});
+  } else {
+    e1 = cexp_neg(kr1);
+    e2 = cexp_neg(kr2);
+  }
+  closed_coeffs<float, D, false>(k, r, kr1, kr2, e1, e2, is2, A, B, dA, dB, S3);
+}
+
 // ---- single layer: V[i, e] partial sum over points lane, lane + nl, ... -------
 template <int ROWS>
-__device__ void entry_sl_f(const EntryView& v, int i, int e, cx<float> s, cx<float> is2, int lane, int nl,
+__device__ void entry_sl_f(const EntryView& v, int i, int e, cx<float> s, cx<float> is2, int kf, int lane, int nl,
                            float* out18) {
   const ElemGeo& g = v.geo[e];
   const double* x = row_point<ROWS>(v, i);
@@ -169,13 +261,23 @@ __device__ void entry_sl_f(const EntryView& v, int i, int e, cx<float> s, cx<flo
       acc.tick();
     }
   } else {
-    const int ri = rule_index2(g, x);
-    const int q0 = rule_offset(ri), q1 = rule_offset(ri + 1);
+    const RefF R = ref_f(g, x, 0.f);
+    const int q0 = rule_offset(R.ri), q1 = rule_offset(R.ri + 1);
+    const float4 a0 = v.ef[4 * (int64_t)e], fe1 = v.ef[4 * (int64_t)e + 1], fe2 = v.ef[4 * (int64_t)e + 2];
+    cx<float> E0[2], w[2];
+    const bool use = kf >= 0 && (s.x * s.x + s.y * s.y) * R.r0 * R.r0 * v.kf.ic2s > 16.f;   // |s| r0 / c2 > 4
+    if (use) ref_exp(v, kf, R.r0, E0, w);
+    else w[0] = s * v.kf.ic1, w[1] = s * v.kf.ic2;
     for (int q = q0 + lane; q < q1; q += nl) {
       const float xi = c_rule_f[3 * q], et = c_rule_f[3 * q + 1];
-      const float wq = c_rule_f[3 * q + 2] * f.area2;
-      acc_U<float>(v.kf, wq, f.d0[0] + xi * f.e1[0] + et * f.e2[0], f.d0[1] + xi * f.e1[1] + et * f.e2[1],
-                   f.d0[2] + xi * f.e1[2] + et * f.e2[2], s, is2, *SA, SB);
+      const float wq = c_rule_f[3 * q + 2] * a0.w;
+      float d[3], r, dr;
+      ref_point(R, a0, fe1, fe2, xi, et, d, r, dr);
+      const float ir = 1.f / r;
+      const float hh[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
+      cx<float> A, Bc, dA, dB, S3;
+      coeffs_ref<false>(v.kf, r, dr, s, is2, use, E0, w, A, Bc, dA, dB, S3);
+      acc_U_from<float>(wq, hh, A, Bc, *SA, SB);
       acc.tick();
     }
   }
@@ -194,7 +296,7 @@ __device__ void entry_sl_f(const EntryView& v, int i, int e, cx<float> s, cx<flo
 
 // ---- double layer (C + K)[i, j] partial sum ---------------------------------
 template <int ROWS>
-__device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<float> is2, int lane, int nl,
+__device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<float> is2, int kf, int lane, int nl,
                            float* out18) {
   const double* x = row_point<ROWS>(v, i);
   FAcc<18> acc;
@@ -213,20 +315,32 @@ __device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<flo
       apex = (t[0] == i) ? 0 : (t[1] == i) ? 1 : (t[2] == i) ? 2 : -1;
     else if (e == i)
       apex = 3;
-    const FrameF f = frame_f(g, x);
     if (apex < 0) {
-      const int ri = rule_index2(g, x);
-      const int q0 = rule_offset(ri), q1 = rule_offset(ri + 1);
+      const RefF R = ref_f(g, x, 0.f);
+      const int q0 = rule_offset(R.ri), q1 = rule_offset(R.ri + 1);
+      const float4 a0 = v.ef[4 * (int64_t)e], fe1 = v.ef[4 * (int64_t)e + 1], fe2 = v.ef[4 * (int64_t)e + 2];
+      const float4 fn = v.ef[4 * (int64_t)e + 3];
+      const float nf[3] = {fn.x, fn.y, fn.z};
+      cx<float> E0[2], w[2];
+      const bool use = kf >= 0 && (s.x * s.x + s.y * s.y) * R.r0 * R.r0 * v.kf.ic2s > 16.f;
+      if (use) ref_exp(v, kf, R.r0, E0, w);
+      else w[0] = s * v.kf.ic1, w[1] = s * v.kf.ic2;
       for (int q = q0 + lane; q < q1; q += nl) {
         const float xi = c_rule_f[3 * q], et = c_rule_f[3 * q + 1];
         const float phi = a == 0 ? 1.f - xi - et : (a == 1 ? xi : et);
-        const float wq = c_rule_f[3 * q + 2] * f.area2 * phi;
-        acc_TT<float, false>(v.kf, wq, f.d0[0] + xi * f.e1[0] + et * f.e2[0], f.d0[1] + xi * f.e1[1] + et * f.e2[1],
-                             f.d0[2] + xi * f.e1[2] + et * f.e2[2], f.n, s, is2, A9);
+        const float wq = c_rule_f[3 * q + 2] * a0.w * phi;
+        float d[3], r, dr;
+        ref_point(R, a0, fe1, fe2, xi, et, d, r, dr);
+        const float ir = 1.f / r;
+        const float hh[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
+        cx<float> A, Bc, dA, dB, S3;
+        coeffs_ref<true>(v.kf, r, dr, s, is2, use, E0, w, A, Bc, dA, dB, S3);
+        acc_TT_from<float>(v.kf, wq, r, hh, nf, A, Bc, dA, dB, S3, A9);
         acc.tick();
       }
       continue;
     }
+    const FrameF f = frame_f(g, x);
     const float xr[3] = {-f.d0[0], -f.d0[1], -f.d0[2]};
     const int nsub = apex == 3 ? 3 : 1;
     for (int q = lane; q < nsub * 256; q += nl) {
@@ -306,21 +420,21 @@ __device__ __forceinline__ bool entry_heavy(const EntryView& v, int i, int j) {
 }
 
 template <int KERN, int ROWS>
-__device__ __forceinline__ void entry_f(const EntryView& v, int i, int j, cx<float> s, cx<float> is2, int lane,
-                                        int nl, float* out18) {
+__device__ __forceinline__ void entry_f(const EntryView& v, int i, int j, cx<float> s, cx<float> is2, int kf,
+                                        int lane, int nl, float* out18) {
   if (KERN == BEM_SL)
-    entry_sl_f<ROWS>(v, i, j, s, is2, lane, nl, out18);
+    entry_sl_f<ROWS>(v, i, j, s, is2, kf, lane, nl, out18);
   else
-    entry_dl_f<ROWS>(v, i, j, s, is2, lane, nl, out18);
+    entry_dl_f<ROWS>(v, i, j, s, is2, kf, lane, nl, out18);
 }
 
 // warp-cooperative evaluation: every lane of the warp calls this with the
 // same (i, j, s); the sum over all points is returned in all lanes
 template <int KERN, int ROWS>
-__device__ __forceinline__ void entry_f_warp(const EntryView& v, int i, int j, cx<float> s, cx<float> is2,
+__device__ __forceinline__ void entry_f_warp(const EntryView& v, int i, int j, cx<float> s, cx<float> is2, int kf,
                                              float* out18) {
   const int lane = threadIdx.x & 31;
-  entry_f<KERN, ROWS>(v, i, j, s, is2, lane, 32, out18);
+  entry_f<KERN, ROWS>(v, i, j, s, is2, kf, lane, 32, out18);
 #pragma unroll
   for (int c = 0; c < 18; ++c)
     for (int o = 16; o > 0; o >>= 1) out18[c] += __shfl_xor_sync(0xffffffffu, out18[c], o);
@@ -329,11 +443,12 @@ __device__ __forceinline__ void entry_f_warp(const EntryView& v, int i, int j, c
 // entry in the precision of the context: FP64 (entry.cuh) or FP32 (above,
 // one thread for all points); result in double
 template <typename R, int KERN, int ROWS>
-__device__ __forceinline__ void entry(const EntryView& v, int i, int j, cx<double> s, cx<double> is2,
+__device__ __forceinline__ void entry(const EntryView& v, int i, int j, int kf, cx<double> s, cx<double> is2,
                                       cx<double>* out) {
   if constexpr (sizeof(R) == sizeof(float)) {
     float o[18];
-    entry_f<KERN, ROWS>(v, i, j, cx<float>{(float)s.x, (float)s.y}, cx<float>{(float)is2.x, (float)is2.y}, 0, 1, o);
+    entry_f<KERN, ROWS>(v, i, j, cx<float>{(float)s.x, (float)s.y}, cx<float>{(float)is2.x, (float)is2.y}, kf, 0, 1,
+                        o);
     for (int c = 0; c < 9; ++c) out[c] = {(double)o[2 * c], (double)o[2 * c + 1]};
   } else {
     if (KERN == BEM_SL)

@@ -72,6 +72,8 @@ static EntryView make_view(const bem_mesh* m) {
   v.rb = m->d_rb;
   v.s = m->ctx->d_s;
   v.inv_s2 = m->ctx->d_inv_s2;
+  v.sw = m->ctx->d_sw;
+  v.ef = m->d_ef;
   v.n_nodes = m->n_nodes;
   v.n_tris = m->n_tris;
   v.K = m->ctx->K;
@@ -146,7 +148,7 @@ __global__ void k_entries_req(EntryView v, const int32_t* __restrict__ req, int6
   cx<double> is2;
   cx<double> s = freq(v, k, is2);
   cx<double> e[9];
-  entry<R, KERN, ROWS>(v, i, j, s, is2, e);
+  entry<R, KERN, ROWS>(v, i, j, k, s, is2, e);
   for (int c = 0; c < 9; ++c) St<S>::st(o + c, e[c]);
 }
 
@@ -280,7 +282,7 @@ __global__ void k_entries_req_noalloc(EntryView v, const int32_t* __restrict__ r
   cx<double> is2;
   const cx<double> s = freq(v, k, is2);
   cx<double> e[9];
-  entry<R, KERN, ROWS>(v, i, j, s, is2, e);
+  entry<R, KERN, ROWS>(v, i, j, k, s, is2, e);
   for (int c = 0; c < 9; ++c) St<S>::st(o + c, e[c]);
 }
 

@@ -91,6 +91,29 @@ void series_tables(double c1, double c2, double* ta, double* tb) {
   }
 }
 
+// s_k / c_a for both waves as float-float pairs (hi + lo), used by the FP32
+// entries to form exp(-s r0 / c_a) at an exact reference distance r0 with the
+// phase reduced modulo 2 pi in float-float arithmetic
+bem_status update_wave_table(bem_ctx* ctx) {
+  if (ctx->device < 0 || !ctx->has_material || ctx->K < 1) return BEM_OK;
+  std::vector<float> t(8 * (size_t)ctx->K);
+  const double ic[2] = {1.0 / ctx->mat.c1, 1.0 / ctx->mat.c2};
+  for (int k = 0; k < ctx->K; ++k)
+    for (int a = 0; a < 2; ++a) {
+      const double re = ctx->s[2 * k] * ic[a], im = ctx->s[2 * k + 1] * ic[a];
+      float* q = &t[8 * (size_t)k + 4 * a];
+      q[0] = (float)re;
+      q[1] = (float)(re - (double)q[0]);
+      q[2] = (float)im;
+      q[3] = (float)(im - (double)q[2]);
+    }
+  cudaFree(ctx->d_sw);
+  ctx->d_sw = nullptr;
+  GCQ_CUDA(ctx, cudaMalloc(&ctx->d_sw, sizeof(float) * t.size()));
+  GCQ_CUDA(ctx, cudaMemcpy(ctx->d_sw, t.data(), sizeof(float) * t.size(), cudaMemcpyHostToDevice));
+  return BEM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // cluster trees (Sec. 3.1, Eq. (3.10)) and block cluster tree (Eq. (3.11))
 // ---------------------------------------------------------------------------
@@ -391,6 +414,7 @@ void bem_ctx_destroy(bem_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaFree(ctx->d_s);
     cudaFree(ctx->d_inv_s2);
+    cudaFree(ctx->d_sw);
   }
   delete ctx;
 }
@@ -424,7 +448,7 @@ bem_status bem_material_set(bem_ctx* ctx, double rho, double lambda, double mu, 
   ctx->has_material = true;
   if (c1) *c1 = m.c1;
   if (c2) *c2 = m.c2;
-  return BEM_OK;
+  return update_wave_table(ctx);
 }
 
 bem_status bem_freqs_bdf2(int32_t N, double dt, int32_t K, double* s) {
@@ -473,7 +497,7 @@ bem_status bem_freqs_set(bem_ctx* ctx, const double* s, int32_t K) {
   GCQ_CUDA(ctx, cudaMemcpy(ctx->d_inv_s2, inv.data(), sizeof(double2) * K, cudaMemcpyHostToDevice));
   ctx->s.assign(s, s + 2 * K);
   ctx->K = K;
-  return BEM_OK;
+  return update_wave_table(ctx);
 }
 
 static void mesh_free(bem_mesh* m) {
@@ -490,6 +514,7 @@ static void mesh_free(bem_mesh* m) {
   cudaFree(m->d_ne_elem);
   cudaFree(m->d_ne_loc);
   cudaFree(m->d_rb);
+  cudaFree(m->d_ef);
   delete m;
 }
 
@@ -564,6 +589,18 @@ bem_status bem_mesh_create(bem_ctx* ctx, const double* xyz, int64_t nn, const in
   std::vector<double> cent(3 * ne);
   for (int64_t e = 0; e < ne; ++e)
     for (int k = 0; k < 3; ++k) cent[3 * e + k] = m->geo[e].c[k];
+  std::vector<float> ef(16 * ne, 0.f);   // FP32 element frames relative to the centroid
+  for (int64_t e = 0; e < ne; ++e) {
+    const ElemGeo& g = m->geo[e];
+    float* q = &ef[16 * e];
+    for (int k = 0; k < 3; ++k) {
+      q[k] = (float)(g.p0[k] - g.c[k]);
+      q[4 + k] = (float)g.e1[k];
+      q[8 + k] = (float)g.e2[k];
+      q[12 + k] = (float)g.n[k];
+    }
+    q[3] = (float)g.area2;
+  }
   cudaError_t ce = cudaSetDevice(ctx->device);
 #define MCPY(dst, src, bytes)                                                   \
   if (ce == cudaSuccess) ce = cudaMalloc(&dst, bytes);                         \
@@ -575,6 +612,7 @@ bem_status bem_mesh_create(bem_ctx* ctx, const double* xyz, int64_t nn, const in
   MCPY(m->d_ne_ptr, m->ne_ptr.data(), sizeof(int32_t) * (nn + 1));
   MCPY(m->d_ne_elem, m->ne_elem.data(), sizeof(int32_t) * 3 * ne);
   MCPY(m->d_ne_loc, m->ne_loc.data(), sizeof(int32_t) * 3 * ne);
+  MCPY(m->d_ef, ef.data(), sizeof(float) * ef.size());
 #undef MCPY
   if (ce != cudaSuccess) {
     mesh_free(m);

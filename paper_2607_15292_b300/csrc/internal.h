@@ -70,6 +70,7 @@ struct bem_ctx {
   std::vector<double> s;          // 2K
   double2* d_s = nullptr;         // s_k
   double2* d_inv_s2 = nullptr;    // 1 / s_k^2
+  float4* d_sw = nullptr;         // [K][2] s_k / c_a as float-float (re_hi, re_lo, im_hi, im_lo)
 };
 
 struct bem_mesh {
@@ -90,6 +91,7 @@ struct bem_mesh {
   int32_t* d_ne_elem = nullptr;
   int32_t* d_ne_loc = nullptr;
   double* d_rb = nullptr;         // rigid-body static diagonal (node rows), n_nodes x 9, lazily
+  float4* d_ef = nullptr;         // FP32 element frames: [p0 - c, 2 area], [e1, 0], [e2, 0], [n, 0]
 };
 
 struct BlockDesc {
@@ -134,6 +136,7 @@ bem_status cuda_err(bem_ctx* ctx, cudaError_t e, const char* what);
 
 // host-side building blocks (host.cpp) ----------------------------------------
 void series_tables(double c1, double c2, double* ta, double* tb);
+bem_status update_wave_table(bem_ctx* ctx);
 bem_status build_trees(bem_tree* t);
 
 // device-side entry points (entry.cu, aca3d.cu, apply.cu, cq.cu) ---------------
