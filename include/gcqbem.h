@@ -178,8 +178,11 @@ bem_status bem_tree_export(const bem_tree* tree, int32_t* row_perm, int32_t* col
  * Algorithm 1 with faces evaluated densely on the device at the pivot
  * frequencies, fibres over all K, dense fallback when no regular pivot
  * exists; far-block faces then compressed by matrix-valued ACA + QR/SVD to
- * eps_aca when options.compress_faces.  Synchronises the stream on return.
- * BEM_ERR_STATE if no frequencies or material are set. */
+ * eps_aca when options.compress_faces (bem_face_compress on each face, in
+ * slot order; a face is kept low rank only where that is smaller than the
+ * dense face, and once a block's face stays dense its later faces, whose
+ * pivot frequencies are larger, are not attempted).  Synchronises the
+ * stream on return.  BEM_ERR_STATE if no frequencies or material are set. */
 bem_status bem_op_compress(bem_tree* tree, void* stream, bem_op** out);
 void bem_op_destroy(bem_op* op);
 
@@ -213,13 +216,40 @@ typedef struct {
                                    an active block, the previous faces read
                                    once and the new face written once       */
   int64_t launches;             /* kernels launched by the compression     */
+  int64_t n_faces;              /* faces of 3D-ACA blocks (sum of ranks)   */
+  int64_t n_faces_lowrank;      /* of which stored as U' W'^T (Eq. (3.12))  */
+  double face_rank_mean;        /* mean rank k of the low-rank faces       */
+  double t_face_aca_ms;         /* device time of the face ACA kernel      */
 } bem_op_stats;
 bem_status bem_op_stats_get(const bem_op* op, bem_op_stats* st);
 
 /* Per-block results (host, n_blocks x 4 int64): kind (0 aca, 1 dense,
- * 2 rank0), rank, first pivot frequency k_1 (-1 if none), face storage
- * (0 dense faces, 1 low rank).  Blocks in bem_tree_export order. */
+ * 2 rank0), rank, first pivot frequency k_1 (-1 if none), number of the
+ * block's faces stored low rank.  Blocks in bem_tree_export order. */
 bem_status bem_op_blocks(const bem_op* op, int64_t* info);
+
+/* Storage of every face (host, K x n_blocks int32, [slot][block]): the rank
+ * k >= 0 of a face stored as U' W'^T by the face ACA + QR/SVD recompression
+ * of Sec. 3.1 (Eq. (3.12); far blocks only, tolerance eps_aca, in MIXED
+ * precision at least 2^-22, the c64 storage resolution), -1 for a face
+ * stored densely (near block, options.compress_faces = 0, no regular ACA
+ * pivot, or factors not smaller than the dense face), -2 where the block
+ * has no face in that slot. */
+bem_status bem_op_face_ranks(const bem_op* op, int32_t* ranks);
+
+/* The face compression of Sec. 3.1 (Eq. (3.12)) on one face, the step
+ * bem_op_compress applies to the faces of far blocks: matrix-valued
+ * partial-pivot ACA of the 3m x 3n matrix H[(i,a),(j,b)] to tolerance
+ * eps_face (relative Frobenius; in MIXED precision at least 2^-22), QR of
+ * both factors, SVD of R_U R_W^T, truncation.  H: device, m x n 3x3 blocks
+ * of c128, [i][j][a][b].  On return *rank (host) is the rank k >= 0 and out
+ * (device, at least 9 m n complex of the context's precision, c128 in FP64,
+ * c64 in MIXED) holds U' (3m x k) then W' (3n x k), column-major, with
+ * H ~= U' W'^T; *rank = -1 when no low-rank form smaller than the dense face
+ * was found (no regular pivot, more ACA steps than the operator allows, or
+ * k (m + n) >= 3 m n), out untouched.  Synchronises the stream. */
+bem_status bem_face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, double eps_face,
+                             int32_t* rank, void* out, void* stream);
 
 /* Number of CUDA kernels this library has launched in the process so far
  * (all contexts); used to count the device work of a timed region. */

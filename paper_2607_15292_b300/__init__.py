@@ -50,7 +50,8 @@ class bem_op_stats(ctypes.Structure):
                 ("t_entries_ms", ctypes.c_double), ("t_compress_ms", ctypes.c_double),
                 ("apply_bytes", ctypes.c_int64), ("t_face_ms", ctypes.c_double),
                 ("face_launches", ctypes.c_int64), ("face_alg_bytes", ctypes.c_double),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("n_faces", ctypes.c_int64), ("n_faces_lowrank", ctypes.c_int64),
+                ("face_rank_mean", ctypes.c_double), ("t_face_aca_ms", ctypes.c_double)]
 
 
 _vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -78,6 +79,8 @@ _SIGS = {
     "bem_op_dense": (_i32, [_vp, _vp, _vp]),
     "bem_op_stats_get": (_i32, [_vp, _P(bem_op_stats)]),
     "bem_op_blocks": (_i32, [_vp, _P(_i64)]),
+    "bem_op_face_ranks": (_i32, [_vp, _P(_i32)]),
+    "bem_face_compress": (_i32, [_vp, _vp, _i64, _i64, _dbl, _P(_i32), _vp, _vp]),
     "bem_kernel_launches": (_i64, []),
     "bem_cq_forward": (_i32, [_i32, _i64, _vp, _vp, _vp]),
     "bem_cq_inverse": (_i32, [_i32, _i64, _vp, _vp, _vp]),
@@ -185,6 +188,17 @@ class Context:
     def mesh(self, xyz, tri) -> "Mesh":
         return Mesh(self, xyz, tri)
 
+    def face_compress(self, H, eps_face: float, out, stream=None) -> int:
+        """Face ACA + QR/SVD recompression of one face H (device complex128,
+        m x n x 3 x 3); out (device, >= 9 m n complex of the context's
+        precision) receives U' (3m x k) then W' (3n x k) column-major.
+        Returns k, or -1 when the face stays dense."""
+        m, n = int(H.shape[0]), int(H.shape[1])
+        rk = ctypes.c_int32(-2)
+        _check(_lib.bem_face_compress(self.ptr, _dptr(H), m, n, float(eps_face), ctypes.byref(rk), _dptr(out),
+                                      _stream_ptr(stream)), self.ptr)
+        return rk.value
+
 
 class Mesh:
     def __init__(self, ctx: Context, xyz, tri):
@@ -270,6 +284,10 @@ class Stats:
     face_launches: int
     face_alg_bytes: float
     launches: int
+    n_faces: int
+    n_faces_lowrank: int
+    face_rank_mean: float
+    t_face_aca_ms: float
 
 
 class Operator:
@@ -303,4 +321,10 @@ class Operator:
     def blocks(self) -> np.ndarray:
         out = np.zeros((self.tree.n_blocks, 4), dtype=np.int64)
         _check(_lib.bem_op_blocks(self._p, out.ctypes.data_as(_P(_i64))))
+        return out
+
+    def face_ranks(self) -> np.ndarray:
+        """(K, n_blocks) int32: rank of each low-rank face, -1 dense face, -2 no face."""
+        out = np.zeros((self.K, self.tree.n_blocks), dtype=np.int32)
+        _check(_lib.bem_op_face_ranks(self._p, out.ctypes.data_as(_P(_i32))))
         return out

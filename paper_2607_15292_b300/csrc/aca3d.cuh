@@ -78,6 +78,21 @@ struct OpData {
   void* d_yp = nullptr;              // batched apply: Y in cluster order, K x 3 per row
   int64_t n_zitems = 0;
   int64_t z_elems = 0;
+  // face storage (face ACA of far blocks, Eq. (3.12)): per [slot][block]
+  // -2 no face, -1 dense face, k >= 0 low rank U' (3m x k) then W' (3n x k),
+  // both column-major, at the face pointer
+  std::vector<int32_t> h_frank;
+  int32_t* d_frank = nullptr;
+  int64_t n_faces = 0, n_faces_lr = 0, face_rank_sum = 0;
+  double t_face_aca_ms = 0;
+  double stored_bytes = 0;
+  // apply scratch of the low-rank faces: T_p (k x K) per face
+  int64_t* d_toff = nullptr;         // [slot][block] offset into d_t, -1 if none
+  void* d_t = nullptr;
+  int32_t* d_lr_items = nullptr;     // (block, slot, pseudo-row tile, k tile) int4
+  int64_t n_lr_items = 0;
+  int32_t* d_lr_faces = nullptr;     // (block, slot) int2 of low-rank faces with k > 0
+  int64_t n_lr_faces = 0;
 };
 
 // ---- 3x3 complex helpers (FP64) ----------------------------------------------
@@ -666,19 +681,268 @@ void free_op(OpData* d) {
 
 bem_status build_apply_lists(bem_ctx* ctx, OpData* d);
 
-// storage conversion of the accepted faces and fibres (compression-time
-// float-float -> final c64 in MIXED mode)
+// copy of the accepted faces, factors and fibres into their final storage:
+// kind 0 float-float (float4) -> c64, kind 1 16-byte copy (c128), kind 2
+// 8-byte copy (c64)
 struct Seg {
-  const float4* src;
-  float2* dst;
+  const void* src;
+  void* dst;
   int64_t n;
+  int64_t kind;
 };
 __global__ void k_convert(const Seg* __restrict__ segs) {
   const Seg g = segs[blockIdx.x];
-  for (int64_t i = threadIdx.x; i < g.n; i += blockDim.x) {
-    const float4 v = g.src[i];
-    g.dst[i] = make_float2(v.x + v.z, v.y + v.w);
+  if (g.kind == 0) {
+    const float4* s = (const float4*)g.src;
+    float2* o = (float2*)g.dst;
+    for (int64_t i = threadIdx.x; i < g.n; i += blockDim.x) {
+      const float4 v = s[i];
+      o[i] = make_float2(v.x + v.z, v.y + v.w);
+    }
+  } else if (g.kind == 1) {
+    const double2* s = (const double2*)g.src;
+    double2* o = (double2*)g.dst;
+    for (int64_t i = threadIdx.x; i < g.n; i += blockDim.x) o[i] = s[i];
+  } else {
+    const float2* s = (const float2*)g.src;
+    float2* o = (float2*)g.dst;
+    for (int64_t i = threadIdx.x; i < g.n; i += blockDim.x) o[i] = s[i];
   }
+}
+template <typename SC>
+constexpr int64_t seg_kind() {
+  return sizeof(SC) == sizeof(float4) && std::is_same<SC, float4>::value ? 0 : (sizeof(SC) == 16 ? 1 : 2);
+}
+
+static bem_status run_segs(bem_ctx* ctx, const std::vector<Seg>& segs, cudaStream_t st, OpData* d) {
+  if (segs.empty()) return BEM_OK;
+  Seg* d_segs = nullptr;
+  GCQ_CUDA(ctx, cudaMalloc(&d_segs, sizeof(Seg) * segs.size()));
+  cudaError_t e = cudaMemcpyAsync(d_segs, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice, st);
+  for (size_t s0 = 0; e == cudaSuccess && s0 < segs.size(); s0 += 65535u * 512u) {
+    const size_t ns = std::min(segs.size() - s0, (size_t)65535u * 512u);
+    k_convert<<<(unsigned)ns, 256, 0, st>>>(d_segs + s0);
+    e = cudaGetLastError();
+    d->launches++;
+    count_launches(1);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_segs);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "bem_op_compress: storage copy");
+  return BEM_OK;
+}
+
+}  // namespace gcq
+#include "faceaca.cuh"
+namespace gcq {
+
+// Face ACA + recompression of every face of the far 3D-ACA blocks (W: working
+// precision), then the final storage of all accepted faces and fibres.
+template <typename W, typename SC, typename SF>
+static bem_status finalize_storage(bem_ctx* ctx, OpData* d, cudaStream_t st) {
+  const int K = d->K;
+  const int64_t nb = d->n_blocks;
+  std::vector<void*>* own = &d->allocs;
+  d->h_frank.assign((size_t)nb * K, -2);
+  for (int64_t b = 0; b < nb; ++b) {
+    const BlkDev& B = d->h_blk[b];
+    if (B.status != ST_DONE) continue;
+    for (int p = 0; p < B.rank; ++p) d->h_frank[(size_t)p * nb + b] = -1;
+    d->n_faces += B.rank;
+  }
+  std::vector<void*> fin_face((size_t)nb * K, nullptr);
+  if (ctx->opt.compress_faces) {
+    // (block, slot) items of the far blocks in slot order on a persistent
+    // queue; once a block's face of slot p stays dense its later faces are
+    // skipped (the pivot frequencies of Algorithm 1 move to larger |s| with
+    // d and the face ranks grow with them)
+    const double eps_face =
+        d->prec == BEM_FP64 ? ctx->opt.eps_aca : std::max(ctx->opt.eps_aca, (double)kMixedFaceTolFloor);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    std::vector<int2> items;
+    std::vector<int32_t> hm(nb), hn(nb), hstop(nb, K);
+    int64_t mmax = 1, nmax = 1;
+    int tcmax = 1;
+    for (int64_t b = 0; b < nb; ++b) {
+      const BlkDev& B = d->h_blk[b];
+      hm[b] = (int32_t)B.m;
+      hn[b] = (int32_t)B.n;
+      if (B.status != ST_DONE || !B.far || B.rank < 1) continue;
+      mmax = std::max(mmax, B.m);
+      nmax = std::max(nmax, B.n);
+      tcmax = std::max(tcmax, face_tcap(B.m, B.n, face_tcap_max<W>()));
+    }
+    for (int p = 0; p < K; ++p) {
+      const size_t first = items.size();
+      for (int64_t b = 0; b < nb; ++b) {
+        const BlkDev& B = d->h_blk[b];
+        if (B.status == ST_DONE && B.far && p < B.rank) items.push_back(make_int2((int)b, p));
+      }
+      std::stable_sort(items.begin() + first, items.end(), [&](const int2& a, const int2& b) {
+        return (int64_t)hm[a.x] * hn[a.x] > (int64_t)hm[b.x] * hn[b.x];
+      });
+    }
+    const size_t jsm = 64u << 10;   // Jacobi matrices in shared memory up to this size
+    const int jsmem_n = (int)std::floor(std::sqrt((double)jsm / (2.0 * sizeof(cx<W>))));
+    cudaError_t e = cudaSuccess;
+    if (!items.empty()) {
+      e = cudaFuncSetAttribute(k_face_aca<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
+      int per_sm = 1, n_sm = 1;
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_face_aca<W>, kFaceThreads, jsm);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+      const size_t c = sizeof(cx<W>), N = 3 * (size_t)tcmax;
+      const size_t per_cta = al(c * 3 * mmax * N) + al(c * 3 * nmax * N) + al(c * 2 * N * N) + al(sizeof(int32_t) * tcmax);
+      const size_t n_cta = std::max<size_t>(1, std::min<size_t>(items.size(), (size_t)std::max(1, per_sm) * n_sm));
+      const size_t hdr = al(sizeof(int2) * items.size()) + al(sizeof(int32_t) * (3 * nb + 1 + nb * K)) +
+                         al(sizeof(FaceJob) * n_cta);
+      char* mem = nullptr;
+      if (e == cudaSuccess && cudaMalloc(&mem, hdr + per_cta * n_cta) != cudaSuccess) e = cudaErrorMemoryAllocation;
+      if (e == cudaSuccess) {
+        char* o = mem;
+        int2* d_items = (int2*)o;
+        o += al(sizeof(int2) * items.size());
+        int32_t* d_i32 = (int32_t*)o;   // counter, stop[nb], m[nb], n[nb], frank[nb K]
+        o += al(sizeof(int32_t) * (3 * nb + 1 + nb * K));
+        FaceJob* d_jobs = (FaceJob*)o;
+        o += al(sizeof(FaceJob) * n_cta);
+        std::vector<FaceJob> jobs(n_cta);
+        int32_t* d_fr = d_i32 + 1 + 3 * nb;
+        for (size_t q = 0; q < n_cta; ++q) {
+          FaceJob& j = jobs[q];
+          j = FaceJob{};
+          j.nb = nb;
+          j.face_tab = d->d_face;
+          j.frank = d_fr;
+          j.U = o;
+          o += al(c * 3 * mmax * N);
+          j.W = o;
+          o += al(c * 3 * nmax * N);
+          j.J = o;
+          o += al(c * 2 * N * N);
+          j.used = (int32_t*)o;
+          o += al(sizeof(int32_t) * tcmax);
+        }
+        std::vector<int32_t> h_i32(1 + 3 * nb);
+        h_i32[0] = 0;
+        std::copy(hstop.begin(), hstop.end(), h_i32.begin() + 1);
+        std::copy(hm.begin(), hm.end(), h_i32.begin() + 1 + nb);
+        std::copy(hn.begin(), hn.end(), h_i32.begin() + 1 + 2 * nb);
+        e = cudaMemcpyAsync(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(d_i32, h_i32.data(), sizeof(int32_t) * h_i32.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(d_fr, d->h_frank.data(), sizeof(int32_t) * nb * K, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(FaceJob) * n_cta, cudaMemcpyHostToDevice, st);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        if (e == cudaSuccess) {
+          FaceQueue fq{d_items, (int64_t)items.size(), d_i32, d_i32 + 1, d_i32 + 1 + nb, d_i32 + 1 + 2 * nb};
+          cudaEventRecord(e0, st);
+          k_face_aca<W><<<(unsigned)n_cta, kFaceThreads, jsm, st>>>(fq, d_jobs, eps_face, jsmem_n);
+          e = cudaGetLastError();
+          cudaEventRecord(e1, st);
+          d->launches++;
+          count_launches(1);
+        }
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(d->h_frank.data(), d_fr, sizeof(int32_t) * nb * K, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          d->t_face_aca_ms += ms;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+      }
+      cudaFree(mem);
+    }
+    if (e == cudaErrorMemoryAllocation)
+      return set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for the face ACA");
+    if (e != cudaSuccess) return cuda_err(ctx, e, "bem_op_compress: face ACA");
+    // compact storage of the factors (written over their faces, working precision)
+    size_t fb = 0;
+    for (int64_t b = 0; b < nb; ++b)
+      for (int p = 0; p < K; ++p) {
+        const int32_t fr = d->h_frank[(size_t)p * nb + b];
+        if (fr < 0) continue;
+        d->n_faces_lr++;
+        d->face_rank_sum += fr;
+        fb += sizeof(SF) * 3 * (size_t)fr * (d->h_blk[b].m + d->h_blk[b].n);
+      }
+    char* fac = nullptr;
+    if (fb > 0 && dmalloc(&fac, fb, own) != cudaSuccess)
+      return set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for face factors");
+    std::vector<Seg> segs;
+    size_t fo = 0;
+    for (int64_t b = 0; b < nb; ++b)
+      for (int p = 0; p < K; ++p) {
+        const size_t idx = (size_t)p * nb + b;
+        const int32_t fr = d->h_frank[idx];
+        if (fr <= 0) continue;
+        const int64_t ne = 3 * (int64_t)fr * (d->h_blk[b].m + d->h_blk[b].n);
+        segs.push_back(Seg{d->h_face[idx], fac + fo, ne, sizeof(cx<W>) == 16 ? 1 : 2});
+        fin_face[idx] = fac + fo;
+        fo += sizeof(SF) * ne;
+      }
+    bem_status r = run_segs(ctx, segs, st, d);
+    if (r != BEM_OK) return r;
+  }
+  // dense faces and all fibres
+  size_t bytes = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const BlkDev& B = d->h_blk[b];
+    if (B.status != ST_DONE) continue;
+    for (int p = 0; p < B.rank; ++p)
+      if (d->h_frank[(size_t)p * nb + b] == -1) bytes += sizeof(SF) * 9 * (size_t)(B.m * B.n);
+    bytes += sizeof(SF) * 9 * (size_t)K * B.rank;
+  }
+  char* fin = nullptr;
+  if (dmalloc(&fin, bytes, own) != cudaSuccess)
+    return set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for the compressed tensor");
+  std::vector<Seg> segs;
+  size_t off = 0;
+  double stored = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const BlkDev& B = d->h_blk[b];
+    if (B.status == ST_DENSE) stored += sizeof(SF) * 9.0 * K * (double)(B.m * B.n);
+    for (int p = 0; p < K; ++p) {
+      const size_t idx = (size_t)p * nb + b;
+      void*& hf = d->h_face[idx];
+      void*& hb = d->h_fib[idx];
+      if (B.status != ST_DONE || p >= B.rank) {
+        hf = nullptr;
+        hb = nullptr;
+        continue;
+      }
+      const int32_t fr = d->h_frank[idx];
+      if (fr == -1) {
+        segs.push_back(Seg{hf, fin + off, 9 * B.m * B.n, seg_kind<SC>()});
+        hf = fin + off;
+        off += sizeof(SF) * 9 * B.m * B.n;
+        stored += sizeof(SF) * 9.0 * (double)(B.m * B.n);
+      } else {
+        hf = fin_face[idx];
+        stored += sizeof(SF) * 3.0 * fr * (double)(B.m + B.n);
+      }
+      segs.push_back(Seg{hb, fin + off, 9 * (int64_t)K, seg_kind<SC>()});
+      hb = fin + off;
+      off += sizeof(SF) * 9 * K;
+      stored += sizeof(SF) * 9.0 * K;
+    }
+  }
+  d->stored_bytes = stored;
+  bem_status r = run_segs(ctx, segs, st, d);
+  if (r != BEM_OK) return r;
+  GCQ_CUDA(ctx, dmalloc(&d->d_frank, sizeof(int32_t) * nb * K, own));
+  GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_frank, d->h_frank.data(), sizeof(int32_t) * nb * K, cudaMemcpyHostToDevice, st));
+  GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_face, d->h_face.data(), sizeof(void*) * nb * K, cudaMemcpyHostToDevice, st));
+  GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_fib, d->h_fib.data(), sizeof(void*) * nb * K, cudaMemcpyHostToDevice, st));
+  GCQ_CUDA(ctx, cudaStreamSynchronize(st));
+  return BEM_OK;
 }
 
 // R: compute type of regular far-field entries; SC: storage of faces and
@@ -761,7 +1025,7 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   float t_ent = 0.f;
   std::vector<Tile> tiles;
   std::vector<int32_t> active;
-  std::vector<void*> slot_chunks;   // compression-time storage when SC != SF
+  std::vector<void*> slot_chunks;   // compression-time storage of faces and fibres
   bem_status result = BEM_OK;
   for (int slot = 0; slot < K && result == BEM_OK; ++slot) {
     active.clear();
@@ -780,7 +1044,7 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
     if (active.empty()) break;
     // slot storage: one chunk for all faces + fibres of this slot
     char* chunk = nullptr;
-    if (dmalloc(&chunk, face_bytes + fib_bytes, std::is_same<SC, SF>::value ? own : &slot_chunks) != cudaSuccess) {
+    if (dmalloc(&chunk, face_bytes + fib_bytes, &slot_chunks) != cudaSuccess) {
       result = set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for 3D-ACA faces");
       break;
     }
@@ -876,51 +1140,8 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
       t_ent += ms;
     }
   }
-  // final storage of the accepted pairs
-  if (result == BEM_OK && !std::is_same<SC, SF>::value) {
-    size_t bytes = 0;
-    for (int64_t b = 0; b < nb; ++b) {
-      const BlkDev& B = d->h_blk[b];
-      if (B.status == ST_DONE) bytes += sizeof(SF) * 9 * (size_t)B.rank * (B.m * B.n + K);
-    }
-    char* fin = nullptr;
-    if (dmalloc(&fin, bytes, own) != cudaSuccess) {
-      result = set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for the compressed tensor");
-    } else {
-      std::vector<Seg> segs;
-      size_t off = 0;
-      for (int64_t b = 0; b < nb; ++b) {
-        const BlkDev& B = d->h_blk[b];
-        for (int p = 0; p < K; ++p) {
-          void*& hf = d->h_face[(int64_t)p * nb + b];
-          void*& hb = d->h_fib[(int64_t)p * nb + b];
-          if (B.status != ST_DONE || p >= B.rank) {
-            hf = nullptr;
-            hb = nullptr;
-            continue;
-          }
-          segs.push_back(Seg{(const float4*)hf, (float2*)(fin + off), 9 * B.m * B.n});
-          hf = fin + off;
-          off += sizeof(SF) * 9 * B.m * B.n;
-          segs.push_back(Seg{(const float4*)hb, (float2*)(fin + off), 9 * (int64_t)K});
-          hb = fin + off;
-          off += sizeof(SF) * 9 * K;
-        }
-      }
-      if (!segs.empty()) {
-        Seg* d_segs = nullptr;
-        GCQ_CUDA(ctx, dmalloc(&d_segs, sizeof(Seg) * segs.size(), &scratch));
-        GCQ_CUDA(ctx, cudaMemcpyAsync(d_segs, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice, st));
-        k_convert<<<(unsigned)segs.size(), 256, 0, st>>>(d_segs);
-        GCQ_CUDA(ctx, cudaGetLastError());
-        d->launches++;
-        count_launches(1);
-      }
-      GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_face, d->h_face.data(), sizeof(void*) * nb * K, cudaMemcpyHostToDevice, st));
-      GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_fib, d->h_fib.data(), sizeof(void*) * nb * K, cudaMemcpyHostToDevice, st));
-      GCQ_CUDA(ctx, cudaStreamSynchronize(st));
-    }
-  }
+  // face ACA of far blocks and final storage of the accepted pairs
+  if (result == BEM_OK) result = finalize_storage<R, SC, SF>(ctx, d, st);
   for (void* p : slot_chunks) cudaFree(p);
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
@@ -935,6 +1156,84 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   d->t_compress_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   return BEM_OK;
+}
+
+// one face through k_face_aca (the step finalize_storage applies to every
+// face of a far block): H device c128 [i][j][3][3]
+template <typename SC>
+__global__ void k_face_store(const double2* __restrict__ H, SC* __restrict__ out, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    St<SC>::st(out + e, cx<double>{H[e].x, H[e].y});
+}
+
+template <typename W, typename SC, typename SF>
+static bem_status face_compress_t(bem_ctx* ctx, const void* H, int64_t m, int64_t n, double eps, int32_t* rank,
+                                  void* out, cudaStream_t st) {
+  FaceJob j{};
+  j.m = (int32_t)m;
+  j.n = (int32_t)n;
+  j.tcap = face_tcap(m, n, face_tcap_max<W>());
+  j.rank = 1;
+  j.nb = 1;
+  j.blk = 0;
+  const size_t c = sizeof(cx<W>), N = 3 * (size_t)j.tcap;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t bH = al(sizeof(SC) * 9 * m * n), bU = al(c * 3 * m * N), bW = al(c * 3 * n * N),
+               bJ = al(c * 2 * N * N), bu = al(sizeof(int32_t) * j.tcap);
+  char* scr = nullptr;
+  GCQ_CUDA(ctx, cudaMalloc(&scr, bH + bU + bW + bJ + bu + sizeof(FaceJob) + 512));
+  void* Hst = scr;
+  j.U = scr + bH;
+  j.W = scr + bH + bU;
+  j.J = scr + bH + bU + bW;
+  j.used = (int32_t*)(scr + bH + bU + bW + bJ);
+  char* tail = scr + bH + bU + bW + bJ + bu;
+  FaceJob* d_job = (FaceJob*)tail;
+  void** d_tab = (void**)(tail + sizeof(FaceJob));
+  int32_t* d_i32 = (int32_t*)(tail + sizeof(FaceJob) + sizeof(void*));   // frank, counter, stop, m, n
+  int2* d_item = (int2*)(d_i32 + 6);
+  j.frank = d_i32;
+  j.face_tab = d_tab;
+  const double eps_face = std::is_same<W, double>::value ? eps : std::max(eps, (double)kMixedFaceTolFloor);
+  const size_t jsm = 64u << 10;
+  const int jsmem_n = (int)std::floor(std::sqrt((double)jsm / (2.0 * sizeof(cx<W>))));
+  int32_t rk = -1;
+  const int32_t h_i32[6] = {-1, 0, 1, (int32_t)m, (int32_t)n, 0};
+  const int2 item = make_int2(0, 0);
+  cudaError_t e = cudaMemcpyAsync(d_job, &j, sizeof(FaceJob), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, &Hst, sizeof(void*), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_i32, h_i32, sizeof(h_i32), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_item, &item, sizeof(int2), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_aca<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
+  if (e == cudaSuccess) {
+    k_face_store<SC><<<256, 256, 0, st>>>((const double2*)H, (SC*)Hst, 9 * m * n);
+    FaceQueue fq{d_item, 1, d_i32 + 1, d_i32 + 2, d_i32 + 3, d_i32 + 4};
+    k_face_aca<W><<<1, kFaceThreads, jsm, st>>>(fq, d_job, eps_face, jsmem_n);
+    count_launches(2);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&rk, j.frank, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && rk > 0) {
+    std::vector<Seg> segs{Seg{Hst, out, 3 * (int64_t)rk * (m + n), sizeof(cx<W>) == 16 ? 1 : 2}};
+    OpData tmp;
+    bem_status r = run_segs(ctx, segs, st, &tmp);
+    if (r != BEM_OK) {
+      cudaFree(scr);
+      return r;
+    }
+  }
+  cudaFree(scr);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "bem_face_compress");
+  *rank = rk;
+  return BEM_OK;
+}
+
+bem_status face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, double eps, int32_t* rank, void* out,
+                         cudaStream_t st) {
+  return ctx->opt.precision == BEM_FP64
+             ? face_compress_t<double, double2, double2>(ctx, H, m, n, eps, rank, out, st)
+             : face_compress_t<float, float4, float2>(ctx, H, m, n, eps, rank, out, st);
 }
 
 bem_status compress(bem_tree* tree, cudaStream_t st, OpData** out) {

@@ -92,12 +92,38 @@ __global__ void k_contract_z(const BlkDev* __restrict__ blk, const int4* __restr
   for (int a = 0; a < 3; ++a) zp[a] = z[a];
 }
 
-// contracted: y[row(li)] += sum_p sum_lj H_p[li][lj] z_p[lj]   (warp per row)
+// contracted, low-rank faces: t_p[q] = sum_(j,b) W'[(j,b), q] z_p[(j,b)]  (warp per q)
+template <typename S, typename A>
+__global__ void k_contract_lr_t(const BlkDev* __restrict__ blk, const int4* __restrict__ faces,
+                                S* const* __restrict__ face_tab, const int32_t* __restrict__ frank,
+                                const int64_t* __restrict__ toff, int64_t nb, const int64_t* __restrict__ zoff,
+                                const cx<A>* __restrict__ Z, cx<A>* __restrict__ T) {
+  const int4 fc = faces[blockIdx.x];   // (block, slot, aca index, 0)
+  const BlkDev& B = blk[fc.x];
+  const int64_t idx = (int64_t)fc.y * nb + fc.x;
+  const int fr = frank[idx];
+  const S* Wt = face_tab[idx] + 3 * B.m * (int64_t)fr;
+  const cx<A>* z = Z + zoff[fc.z] + (int64_t)fc.y * B.n * 3;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = w; q < fr; q += nw) {
+    cx<A> acc = {A(0), A(0)};
+    for (int64_t e = lane; e < 3 * B.n; e += 32) acc = cfma(Ld<S, A>::ld(Wt + (int64_t)q * 3 * B.n + e), z[e], acc);
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) T[toff[idx] + q] = acc;
+  }
+}
+
+// contracted: y[row(li)] += sum_p sum_lj H_p[li][lj] z_p[lj]   (warp per row);
+// low-rank faces: y[row(li)][a] += sum_q U'[(li,a), q] t_p[q]
 template <typename S, typename A>
 __global__ void k_contract_apply(const BlkDev* __restrict__ blk, const int32_t* __restrict__ list,
-                                 S* const* __restrict__ face_tab, int64_t nb, const int64_t* __restrict__ zoff,
-                                 const int32_t* __restrict__ row_perm, const cx<A>* __restrict__ Z,
-                                 S* __restrict__ Y) {
+                                 S* const* __restrict__ face_tab, const int32_t* __restrict__ frank,
+                                 const int64_t* __restrict__ toff, const cx<A>* __restrict__ T, int64_t nb,
+                                 const int64_t* __restrict__ zoff, const int32_t* __restrict__ row_perm,
+                                 const cx<A>* __restrict__ Z, S* __restrict__ Y) {
   const int ai = blockIdx.x;
   const int b = list[ai];
   const BlkDev& B = blk[b];
@@ -105,7 +131,15 @@ __global__ void k_contract_apply(const BlkDev* __restrict__ blk, const int32_t* 
   for (int64_t li = (int64_t)blockIdx.y * nw + w; li < B.m; li += (int64_t)gridDim.y * nw) {
     cx<A> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
     for (int p = 0; p < B.rank; ++p) {
-      const S* H = face_tab[(int64_t)p * nb + b];
+      const int64_t idx = (int64_t)p * nb + b;
+      const S* H = face_tab[idx];
+      const int fr = frank[idx];
+      if (fr >= 0) {
+        const cx<A>* t = T + (fr > 0 ? toff[idx] : 0);
+        for (int q = lane; q < fr; q += 32)
+          for (int a = 0; a < 3; ++a) acc[a] = cfma(Ld<S, A>::ld(H + (int64_t)q * 3 * B.m + 3 * li + a), t[q], acc[a]);
+        continue;
+      }
       const cx<A>* z = Z + zoff[ai] + (int64_t)p * B.n * 3;
       for (int64_t lj = lane; lj < B.n; lj += 32) {
         const S* h = H + (li * B.n + lj) * 9;
@@ -131,17 +165,69 @@ __global__ void k_contract_apply(const BlkDev* __restrict__ blk, const int32_t* 
 // block once through shared memory in chunks of kBN columns:
 //   Z[j][a][k] = sum_b f_p[k][a][b] x_k[j][b]      (fibre transform, per chunk)
 //   Y[i][k][a] += sum_j sum_b H_p[i][j][a][b] Z[j][b][k]
-// Each thread accumulates 8 frequencies x 3 components of one row in registers;
-// the block's result is added to Yp once (atomics) after all faces.
+// A low-rank face H_p = U' W'^T (Eq. (3.12)) contributes U' T_p instead, with
+// T_p = W'^T Z (k x K) computed beforehand by k_apply_lr_t; its chunks of
+// 3 kBN rank columns take the place of kBN nodes x 3 components, so one inner
+// loop serves both.  Each thread accumulates 8 frequencies x 3 components of
+// one row in registers; the block's result is added to Yp once (atomics).
 constexpr int kBM = 32, kBK = 64, kBN = 16, kTPR = 8;
 constexpr int kSHR = kBN * 9 + 1;   // padded row stride of the face tile (no bank conflicts)
 constexpr int kApplyThreads = kBM * kTPR;   // 256
+
+// Z chunk: sZ[(jj * 3 + a) * kBK + kk] = sum_b f[kk][a][b] x[j0 + jj][b] (zero outside)
+template <typename S, typename A>
+__device__ __forceinline__ void load_z_chunk(cx<A>* sZ, const cx<A>* sF, const S* __restrict__ Xp, int64_t c0,
+                                             int64_t j0, int64_t n, int K, int k0, int nk) {
+  for (int c = threadIdx.x; c < kBN * kBK; c += blockDim.x) {
+    const int jj = c / kBK, kk = c % kBK;
+    const int64_t gj = j0 + jj;
+    cx<A> x[3] = {{A(0), A(0)}, {A(0), A(0)}, {A(0), A(0)}};
+    if (gj < n && kk < nk) {
+      const S* xp = Xp + ((c0 + gj) * K + k0 + kk) * 3;
+      for (int b = 0; b < 3; ++b) x[b] = Ld<S, A>::ld(xp + b);
+    }
+    for (int a = 0; a < 3; ++a) {
+      cx<A> z = {A(0), A(0)};
+      for (int b = 0; b < 3; ++b) z = cfma(sF[kk * 9 + 3 * a + b], x[b], z);
+      sZ[(jj * 3 + a) * kBK + kk] = z;
+    }
+  }
+}
+template <typename S, typename A>
+__device__ __forceinline__ void load_f(cx<A>* sF, const S* __restrict__ f, int k0, int nk) {
+  for (int c = threadIdx.x; c < kBK * 9; c += blockDim.x) {
+    const int kk = c / 9;
+    sF[c] = kk < nk ? Ld<S, A>::ld(f + (int64_t)(k0 + kk) * 9 + c % 9) : cx<A>{A(0), A(0)};
+  }
+}
+// acc[t][a] += sum_jj sum_b sH[r][jj][a][b] sZ[jj][b][kq + kTPR t]
+template <typename A>
+__device__ __forceinline__ void mac_chunk(cx<A> (&acc)[kBK / kTPR][3], const cx<A>* sH, const cx<A>* sZ, int r,
+                                          int kq) {
+#pragma unroll 4
+  for (int jj = 0; jj < kBN; ++jj) {
+    cx<A> h[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) h[c] = sH[r * kSHR + jj * 9 + c];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int t = 0; t < kBK / kTPR; ++t) {
+        const cx<A> z = sZ[(jj * 3 + b) * kBK + kq + kTPR * t];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[t][a] = cfma(h[3 * a + b], z, acc[t][a]);
+      }
+  }
+}
 
 template <typename S, typename A>
 __global__ void __launch_bounds__(kApplyThreads) k_apply_faces(const BlkDev* __restrict__ blk,
                                                                const int4* __restrict__ items,
                                                                S* const* __restrict__ face_tab,
-                                                               S* const* __restrict__ fib_tab, int64_t nb,
+                                                               S* const* __restrict__ fib_tab,
+                                                               const int32_t* __restrict__ frank,
+                                                               const int64_t* __restrict__ toff,
+                                                               const cx<A>* __restrict__ T, int64_t nb,
                                                                const S* __restrict__ Xp, A* __restrict__ Yp, int K) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<A>* sH = reinterpret_cast<cx<A>*>(smem_raw);       // [kBM][kBN * 9 + 1] (padded rows)
@@ -153,19 +239,44 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_faces(const BlkDev* __r
   const int64_t i0 = (int64_t)it.y * kBM;
   const int k0 = it.z * kBK;
   const int nk = min(kBK, K - k0);
+  const int64_t M3 = 3 * B.m;
   cx<A> acc[kBK / kTPR][3];
 #pragma unroll
   for (int t = 0; t < kBK / kTPR; ++t)
 #pragma unroll
     for (int a = 0; a < 3; ++a) acc[t][a] = {A(0), A(0)};
   for (int p = 0; p < B.rank; ++p) {
-    const S* H = face_tab[(int64_t)p * nb + it.x];
-    const S* f = fib_tab[(int64_t)p * nb + it.x];
-    __syncthreads();
-    for (int c = threadIdx.x; c < kBK * 9; c += blockDim.x) {
-      const int kk = c / 9;
-      sF[c] = kk < nk ? Ld<S, A>::ld(f + (int64_t)(k0 + kk) * 9 + c % 9) : cx<A>{A(0), A(0)};
+    const int64_t idx = (int64_t)p * nb + it.x;
+    const S* H = face_tab[idx];
+    const int fr = frank[idx];
+    if (fr == 0) continue;
+    if (fr > 0) {
+      // low rank: rank columns q = 3 jj + b of U' against T_p[q][k]
+      const cx<A>* Tp = T + toff[idx];
+      for (int q0 = 0; q0 < fr; q0 += 3 * kBN) {
+        __syncthreads();
+        for (int c = threadIdx.x; c < kBM * 3 * 3 * kBN; c += blockDim.x) {
+          // consecutive threads along the rows (i, a) of one rank column (coalesced)
+          const int q = c / (kBM * 3), rem = c % (kBM * 3), rr = rem / 3, a = rem % 3;
+          const int jj = q / 3, b = q % 3;
+          const int64_t gi = i0 + rr;
+          const int gq = q0 + q;
+          sH[rr * kSHR + jj * 9 + 3 * a + b] =
+              (gi < B.m && gq < fr) ? Ld<S, A>::ld(H + (int64_t)gq * M3 + 3 * gi + a) : cx<A>{A(0), A(0)};
+        }
+        for (int c = threadIdx.x; c < 3 * kBN * kBK; c += blockDim.x) {
+          const int q = c / kBK, kk = c % kBK;
+          const int gq = q0 + q;
+          sZ[q * kBK + kk] = (gq < fr && kk < nk) ? Tp[(int64_t)gq * K + k0 + kk] : cx<A>{A(0), A(0)};
+        }
+        __syncthreads();
+        mac_chunk<A>(acc, sH, sZ, r, kq);
+      }
+      continue;
     }
+    const S* f = fib_tab[idx];
+    __syncthreads();
+    load_f<S, A>(sF, f, k0, nk);
     for (int64_t j0 = 0; j0 < B.n; j0 += kBN) {
       __syncthreads();
       for (int c = threadIdx.x; c < kBM * kBN * 9; c += blockDim.x) {
@@ -173,35 +284,9 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_faces(const BlkDev* __r
         const int64_t gi = i0 + rr, gj = j0 + jj;
         sH[rr * kSHR + rem] = (gi < B.m && gj < B.n) ? Ld<S, A>::ld(H + (gi * B.n + gj) * 9 + rem % 9) : cx<A>{A(0), A(0)};
       }
-      for (int c = threadIdx.x; c < kBN * kBK; c += blockDim.x) {
-        const int jj = c / kBK, kk = c % kBK;
-        const int64_t gj = j0 + jj;
-        cx<A> x[3] = {{A(0), A(0)}, {A(0), A(0)}, {A(0), A(0)}};
-        if (gj < B.n && kk < nk) {
-          const S* xp = Xp + ((B.c0 + gj) * K + k0 + kk) * 3;
-          for (int b = 0; b < 3; ++b) x[b] = Ld<S, A>::ld(xp + b);
-        }
-        for (int a = 0; a < 3; ++a) {
-          cx<A> z = {A(0), A(0)};
-          for (int b = 0; b < 3; ++b) z = cfma(sF[kk * 9 + 3 * a + b], x[b], z);
-          sZ[(jj * 3 + a) * kBK + kk] = z;
-        }
-      }
+      load_z_chunk<S, A>(sZ, sF, Xp, B.c0, j0, B.n, K, k0, nk);
       __syncthreads();
-#pragma unroll 4
-      for (int jj = 0; jj < kBN; ++jj) {
-        cx<A> h[9];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) h[c] = sH[r * kSHR + jj * 9 + c];
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-          for (int t = 0; t < kBK / kTPR; ++t) {
-            const cx<A> z = sZ[(jj * 3 + b) * kBK + kq + kTPR * t];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) acc[t][a] = cfma(h[3 * a + b], z, acc[t][a]);
-          }
-      }
+      mac_chunk<A>(acc, sH, sZ, r, kq);
     }
   }
   const int64_t gi = i0 + r;
@@ -214,6 +299,65 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_faces(const BlkDev* __r
         for (int a = 0; a < 3; ++a) atomic_add_c(y + 2 * a, acc[t][a]);
       }
     }
+}
+
+// T_p = W'^T Z_p for every low-rank face: item (block, slot, tile of kBM
+// rank triples, frequency tile).  Rank column q = 3 r + a of the tile plays
+// the role of row r, component a of k_apply_faces; the result is stored.
+template <typename S, typename A>
+__global__ void __launch_bounds__(kApplyThreads) k_apply_lr_t(const BlkDev* __restrict__ blk,
+                                                              const int4* __restrict__ items,
+                                                              S* const* __restrict__ face_tab,
+                                                              S* const* __restrict__ fib_tab,
+                                                              const int32_t* __restrict__ frank,
+                                                              const int64_t* __restrict__ toff,
+                                                              cx<A>* __restrict__ T, int64_t nb,
+                                                              const S* __restrict__ Xp, int K) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<A>* sH = reinterpret_cast<cx<A>*>(smem_raw);
+  cx<A>* sZ = sH + kBM * kSHR;
+  cx<A>* sF = sZ + kBN * 3 * kBK;
+  const int4 it = items[blockIdx.x];
+  const BlkDev& B = blk[it.x];
+  const int64_t idx = (int64_t)it.y * nb + it.x;
+  const int fr = frank[idx];
+  const S* Wt = face_tab[idx] + 3 * B.m * (int64_t)fr;   // W' (3n x k), column q contiguous
+  const int64_t N3 = 3 * B.n;
+  const int r = threadIdx.x / kTPR, kq = threadIdx.x % kTPR;
+  const int q0 = it.z * 3 * kBM;
+  const int k0 = it.w * kBK;
+  const int nk = min(kBK, K - k0);
+  cx<A> acc[kBK / kTPR][3];
+#pragma unroll
+  for (int t = 0; t < kBK / kTPR; ++t)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc[t][a] = {A(0), A(0)};
+  load_f<S, A>(sF, fib_tab[idx], k0, nk);
+  for (int64_t j0 = 0; j0 < B.n; j0 += kBN) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < kBM * kBN * 9; c += blockDim.x) {
+      // consecutive threads along the rows (j, b) of one rank column
+      const int qq = c / (kBN * 3), rem = c % (kBN * 3), jj = rem / 3, b = rem % 3;
+      const int rr = qq / 3, a = qq % 3;
+      const int gq = q0 + qq;
+      const int64_t gj = j0 + jj;
+      sH[rr * kSHR + jj * 9 + 3 * a + b] =
+          (gq < fr && gj < B.n) ? Ld<S, A>::ld(Wt + (int64_t)gq * N3 + 3 * gj + b) : cx<A>{A(0), A(0)};
+    }
+    load_z_chunk<S, A>(sZ, sF, Xp, B.c0, j0, B.n, K, k0, nk);
+    __syncthreads();
+    mac_chunk<A>(acc, sH, sZ, r, kq);
+  }
+  cx<A>* Tp = T + toff[idx];
+#pragma unroll
+  for (int t = 0; t < kBK / kTPR; ++t) {
+    const int kk = kq + kTPR * t;
+    if (kk < nk)
+      for (int a = 0; a < 3; ++a) {
+        const int gq = q0 + 3 * r + a;
+        if (gq < fr) Tp[(int64_t)gq * K + k0 + kk] = acc[t][a];
+      }
+  }
 }
 
 // X[k][col][c] -> Xp[pos][k][c] (cluster order), Yp[pos][k][c] -> Y[k][row][c]
@@ -241,17 +385,28 @@ __global__ void k_unperm_y(const S* __restrict__ Yp, S* __restrict__ Y, const in
 }
 
 bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
-  std::vector<int4> items;
+  std::vector<int4> items, lr_items, lr_faces;
   std::vector<int32_t> dense, aca;
   std::vector<int64_t> zoff;
   std::vector<int4> zitems;   // (block, face, 128-column chunk, aca index)
-  int64_t z = 0;
-  for (int64_t b = 0; b < d->n_blocks; ++b) {
+  std::vector<int64_t> toff((size_t)d->n_blocks * d->K, -1);
+  int64_t z = 0, tt = 0;
+  const int64_t nb = d->n_blocks;
+  for (int64_t b = 0; b < nb; ++b) {
     const BlkDev& B = d->h_blk[b];
     if (B.status == ST_DENSE) dense.push_back((int32_t)b);
     if (B.status == ST_DONE && B.rank > 0) {
-      for (int p = 0; p < B.rank; ++p)
+      for (int p = 0; p < B.rank; ++p) {
         for (int64_t c = 0; c * 128 < B.n; ++c) zitems.push_back(make_int4((int)b, p, (int)c, (int)aca.size()));
+        const int fr = d->h_frank[(size_t)p * nb + b];
+        if (fr > 0) {
+          toff[(size_t)p * nb + b] = tt;
+          tt += (int64_t)fr * d->K;
+          lr_faces.push_back(make_int4((int)b, p, (int)aca.size(), 0));
+          for (int q = 0; q * 3 * kBM < fr; ++q)
+            for (int kt = 0; kt * kBK < d->K; ++kt) lr_items.push_back(make_int4((int)b, p, q, kt));
+        }
+      }
       aca.push_back((int32_t)b);
       zoff.push_back(z);
       z += (int64_t)B.rank * B.n * 3;
@@ -264,36 +419,30 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
   d->n_dense = (int64_t)dense.size();
   d->n_aca = (int64_t)aca.size();
   d->z_elems = z;
-  GCQ_CUDA(ctx, dmalloc(&d->d_apply_items, sizeof(int4) * std::max<size_t>(1, items.size()), own));
-  GCQ_CUDA(ctx, dmalloc(&d->d_dense_list, sizeof(int32_t) * std::max<size_t>(1, dense.size()), own));
-  GCQ_CUDA(ctx, dmalloc(&d->d_aca_list, sizeof(int32_t) * std::max<size_t>(1, aca.size()), own));
-  GCQ_CUDA(ctx, dmalloc(&d->d_zoff, sizeof(int64_t) * std::max<size_t>(1, zoff.size()), own));
+  d->n_lr_items = (int64_t)lr_items.size();
+  d->n_lr_faces = (int64_t)lr_faces.size();
+  auto up = [&](auto** dst, const auto& v) -> cudaError_t {
+    using T = typename std::decay<decltype(v)>::type::value_type;
+    cudaError_t e = dmalloc(dst, sizeof(T) * std::max<size_t>(1, v.size()), own);
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+  };
+  GCQ_CUDA(ctx, up((int4**)&d->d_apply_items, items));
+  GCQ_CUDA(ctx, up(&d->d_dense_list, dense));
+  GCQ_CUDA(ctx, up(&d->d_aca_list, aca));
+  GCQ_CUDA(ctx, up(&d->d_zoff, zoff));
+  GCQ_CUDA(ctx, up((int4**)&d->d_zitems, zitems));
+  GCQ_CUDA(ctx, up((int4**)&d->d_lr_items, lr_items));
+  GCQ_CUDA(ctx, up((int4**)&d->d_lr_faces, lr_faces));
+  GCQ_CUDA(ctx, up(&d->d_toff, toff));
   d->n_zitems = (int64_t)zitems.size();
-  GCQ_CUDA(ctx, dmalloc(&d->d_zitems, sizeof(int4) * std::max<size_t>(1, zitems.size()), own));
-  if (!zitems.empty())
-    GCQ_CUDA(ctx, cudaMemcpy(d->d_zitems, zitems.data(), sizeof(int4) * zitems.size(), cudaMemcpyHostToDevice));
   const size_t es = d->prec == BEM_FP64 ? sizeof(double2) : sizeof(float2);
   GCQ_CUDA(ctx, dmalloc(&d->d_xp, es * 3 * (size_t)d->K * d->n_cols, own));
   GCQ_CUDA(ctx, dmalloc(&d->d_yp, es * 3 * (size_t)d->K * d->n_rows, own));
-  const size_t zb = es * std::max<int64_t>(1, z);
-  GCQ_CUDA(ctx, dmalloc(&d->d_z, zb, own));
-  if (!items.empty())
-    GCQ_CUDA(ctx, cudaMemcpy(d->d_apply_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
-  if (!dense.empty())
-    GCQ_CUDA(ctx, cudaMemcpy(d->d_dense_list, dense.data(), sizeof(int32_t) * dense.size(), cudaMemcpyHostToDevice));
-  if (!aca.empty()) {
-    GCQ_CUDA(ctx, cudaMemcpy(d->d_aca_list, aca.data(), sizeof(int32_t) * aca.size(), cudaMemcpyHostToDevice));
-    GCQ_CUDA(ctx, cudaMemcpy(d->d_zoff, zoff.data(), sizeof(int64_t) * zoff.size(), cudaMemcpyHostToDevice));
-  }
+  GCQ_CUDA(ctx, dmalloc(&d->d_z, es * std::max<int64_t>(1, z), own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_t, es * std::max<int64_t>(1, tt), own));
   // algorithmic bytes of one batched apply: stored operator + X + Y
-  const int64_t esb = (int64_t)es;
-  int64_t stored = 0;
-  for (int64_t b = 0; b < d->n_blocks; ++b) {
-    const BlkDev& B = d->h_blk[b];
-    if (B.status == ST_DENSE) stored += (int64_t)d->K * B.m * B.n * 9 * esb;
-    if (B.status == ST_DONE) stored += (int64_t)B.rank * (B.m * B.n + d->K) * 9 * esb;
-  }
-  d->apply_bytes = stored + (int64_t)d->K * (d->n_rows + d->n_cols) * 3 * esb;
+  d->apply_bytes = (int64_t)d->stored_bytes + (int64_t)d->K * (d->n_rows + d->n_cols) * 3 * (int64_t)es;
   return BEM_OK;
 }
 
@@ -310,12 +459,20 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
     GCQ_CUDA(ctx, cudaMemsetAsync(d->d_yp, 0, sizeof(S) * 3 * nyp, st));
+    const size_t smem = sizeof(cx<A>) * (kBM * kSHR + kBN * 3 * kBK + kBK * 9);
+    if (d->n_lr_items > 0) {
+      cudaFuncSetAttribute(k_apply_lr_t<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_apply_lr_t<S, A><<<(unsigned)d->n_lr_items, kApplyThreads, smem, st>>>(
+          d->d_blk, (const int4*)d->d_lr_items, (S* const*)d->d_face, (S* const*)d->d_fib, d->d_frank, d->d_toff,
+          (cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_xp, d->K);
+      GCQ_CUDA(ctx, cudaGetLastError());
+      count_launches(1);
+    }
     if (d->n_apply_items > 0) {
-      const size_t smem = sizeof(cx<A>) * (kBM * kSHR + kBN * 3 * kBK + kBK * 9);
       cudaFuncSetAttribute(k_apply_faces<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_apply_faces<S, A><<<(unsigned)d->n_apply_items, kApplyThreads, smem, st>>>(
-          d->d_blk, (const int4*)d->d_apply_items, (S* const*)d->d_face, (S* const*)d->d_fib, d->n_blocks,
-          (const S*)d->d_xp, (A*)d->d_yp, d->K);
+          d->d_blk, (const int4*)d->d_apply_items, (S* const*)d->d_face, (S* const*)d->d_fib, d->d_frank,
+          d->d_toff, (const cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_xp, (A*)d->d_yp, d->K);
       GCQ_CUDA(ctx, cudaGetLastError());
       count_launches(1);
     }
@@ -339,8 +496,16 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
                                                               d->d_col_perm, X, (cx<A>*)d->d_z, d->K, d->n_cols);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
+    if (d->n_lr_faces > 0) {
+      k_contract_lr_t<S, A><<<(unsigned)d->n_lr_faces, 128, 0, st>>>(
+          d->d_blk, (const int4*)d->d_lr_faces, (S* const*)d->d_face, d->d_frank, d->d_toff, d->n_blocks,
+          d->d_zoff, (const cx<A>*)d->d_z, (cx<A>*)d->d_t);
+      GCQ_CUDA(ctx, cudaGetLastError());
+      count_launches(1);
+    }
     dim3 g((unsigned)d->n_aca, 8);
-    k_contract_apply<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_aca_list, (S* const*)d->d_face, d->n_blocks, d->d_zoff,
+    k_contract_apply<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_aca_list, (S* const*)d->d_face, d->d_frank,
+                                              d->d_toff, (const cx<A>*)d->d_t, d->n_blocks, d->d_zoff,
                                               d->d_row_perm, (const cx<A>*)d->d_z, Y);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
@@ -364,7 +529,8 @@ bem_status apply(bem_op* op, int mode, const void* X, void* Y, cudaStream_t st) 
 template <typename S>
 __global__ void k_op_dense(const BlkDev* __restrict__ blk, const Tile* __restrict__ tiles,
                            S* const* __restrict__ face_tab, S* const* __restrict__ fib_tab,
-                           S* const* __restrict__ dense, int64_t nb, const int32_t* __restrict__ row_perm,
+                           const int32_t* __restrict__ frank, S* const* __restrict__ dense, int64_t nb,
+                           const int32_t* __restrict__ row_perm,
                            const int32_t* __restrict__ col_perm, S* __restrict__ out, int K, int64_t n_cols) {
   const Tile t = tiles[blockIdx.x];
   const BlkDev& B = blk[t.blk];
@@ -382,12 +548,23 @@ __global__ void k_op_dense(const BlkDev* __restrict__ blk, const Tile* __restric
     } else if (B.status == ST_DONE) {
       for (int p = 0; p < B.rank; ++p) {
         cx<double> h[9], f[9], hf[9];
-        const S* hp = face_tab[(int64_t)p * nb + t.blk] + e * 9;
-        const S* fp = fib_tab[(int64_t)p * nb + t.blk] + (int64_t)k * 9;
-        for (int c = 0; c < 9; ++c) {
-          h[c] = St<S>::ld(hp + c);
-          f[c] = St<S>::ld(fp + c);
+        const int64_t idx = (int64_t)p * nb + t.blk;
+        const int fr = frank[idx];
+        const S* fp = fib_tab[idx] + (int64_t)k * 9;
+        if (fr >= 0) {   // low rank: H[(li,a),(lj,b)] = sum_q U'[(li,a),q] W'[(lj,b),q]
+          const S* Up = face_tab[idx];
+          const S* Wp = Up + 3 * B.m * (int64_t)fr;
+          for (int c = 0; c < 9; ++c) h[c] = {0, 0};
+          for (int q = 0; q < fr; ++q)
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b)
+                h[3 * a + b] = h[3 * a + b] + St<S>::ld(Up + (int64_t)q * 3 * B.m + 3 * li + a) *
+                                                  St<S>::ld(Wp + (int64_t)q * 3 * B.n + 3 * lj + b);
+        } else {
+          const S* hp = face_tab[idx] + e * 9;
+          for (int c = 0; c < 9; ++c) h[c] = St<S>::ld(hp + c);
         }
+        for (int c = 0; c < 9; ++c) f[c] = St<S>::ld(fp + c);
         mm3(h, f, hf);
         for (int c = 0; c < 9; ++c) v[c] = v[c] + hf[c];
       }
@@ -410,7 +587,7 @@ static bem_status op_dense_t(bem_op* op, void* out, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(dt, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
     k_op_dense<S><<<(unsigned)tiles.size(), kTile, 0, st>>>(d->d_blk, dt, (S* const*)d->d_face, (S* const*)d->d_fib,
-                                                           (S* const*)d->d_dense, d->n_blocks, d->d_row_perm,
+                                                           d->d_frank, (S* const*)d->d_dense, d->n_blocks, d->d_row_perm,
                                                            d->d_col_perm, (S*)out, d->K, d->n_cols);
     e = cudaGetLastError();
     count_launches(1);
@@ -436,7 +613,6 @@ bem_status op_stats(const bem_op* op, bem_op_stats* s) {
     s->n_far += B.far;
     if (B.status == ST_DENSE) {
       s->n_dense++;
-      s->stored_bytes += es * 9.0 * d->K * B.m * B.n;
     } else if (B.status == ST_RANK0) {
       s->n_rank0++;
     } else {
@@ -444,11 +620,11 @@ bem_status op_stats(const bem_op* op, bem_op_stats* s) {
       s->rank_min = std::min<int64_t>(s->rank_min, B.rank);
       s->rank_max = std::max<int64_t>(s->rank_max, B.rank);
       rank_sum += B.rank;
-      s->stored_bytes += es * 9.0 * B.rank * ((double)B.m * B.n + d->K);
     }
   }
   if (s->n_aca == 0) s->rank_min = 0;
   s->rank_mean = s->n_aca ? rank_sum / s->n_aca : 0.0;
+  s->stored_bytes = d->stored_bytes;
   s->dense_bytes = es * 9.0 * d->K * (double)d->n_rows * (double)d->n_cols;
   s->compression_rate = s->stored_bytes / s->dense_bytes;
   s->entries_evaluated = d->entries;
@@ -459,6 +635,10 @@ bem_status op_stats(const bem_op* op, bem_op_stats* s) {
   s->face_launches = d->face_launches;
   s->face_alg_bytes = d->face_alg_bytes;
   s->launches = d->launches;
+  s->n_faces = d->n_faces;
+  s->n_faces_lowrank = d->n_faces_lr;
+  s->face_rank_mean = d->n_faces_lr ? (double)d->face_rank_sum / d->n_faces_lr : 0.0;
+  s->t_face_aca_ms = d->t_face_aca_ms;
   return BEM_OK;
 }
 
@@ -472,8 +652,16 @@ bem_status op_blocks(const bem_op* op, int64_t* info) {
     info[4 * b + 0] = B.status == ST_DENSE ? 1 : (B.status == ST_RANK0 ? 2 : 0);
     info[4 * b + 1] = B.status == ST_DENSE ? d->K : B.rank;
     info[4 * b + 2] = B.status == ST_DONE && B.rank > 0 ? ks[(size_t)b * d->K] : -1;
-    info[4 * b + 3] = 0;
+    int64_t lr = 0;
+    for (int p = 0; B.status == ST_DONE && p < B.rank; ++p) lr += d->h_frank[(size_t)p * d->n_blocks + b] >= 0;
+    info[4 * b + 3] = lr;
   }
+  return BEM_OK;
+}
+
+bem_status op_face_ranks(const bem_op* op, int32_t* out) {
+  const OpData* d = op->d;
+  std::memcpy(out, d->h_frank.data(), sizeof(int32_t) * d->h_frank.size());
   return BEM_OK;
 }
 

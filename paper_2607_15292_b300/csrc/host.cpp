@@ -766,6 +766,21 @@ bem_status bem_op_blocks(const bem_op* op, int64_t* info) {
   return op_blocks(op, info);
 }
 
+bem_status bem_face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, double eps_face, int32_t* rank,
+                             void* out, void* stream) {
+  if (!ctx) return BEM_ERR_ARG;
+  if (!H || !out || !rank || m < 1 || n < 1 || m > (1 << 20) || n > (1 << 20) || !(eps_face > 0 && eps_face < 1))
+    return set_err(ctx, BEM_ERR_ARG, "bem_face_compress: invalid argument");
+  if (ctx->device < 0) return set_err(ctx, BEM_ERR_STATE, "bem_face_compress: host-only context (device -1)");
+  GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
+  return face_compress(ctx, H, m, n, eps_face, rank, out, (cudaStream_t)stream);
+}
+
+bem_status bem_op_face_ranks(const bem_op* op, int32_t* ranks) {
+  if (!op || !ranks) return BEM_ERR_ARG;
+  return op_face_ranks(op, ranks);
+}
+
 bem_status bem_cq_forward(int32_t N, int64_t nvec, const void* in, void* out, void* stream) {
   if (N < 1 || nvec < 1 || !in || !out) return BEM_ERR_ARG;
   return cq_transform(N, nvec, in, out, false, (cudaStream_t)stream);
