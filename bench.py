@@ -246,7 +246,42 @@ def main():
 
     extra = {"apply_gbs": apply_gbs, "apply_ms": apply_ms, "compression_rate_V": sv.compression_rate,
              "compression_rate_K": sk.compression_rate, "rank_mean_V": sv.rank_mean, "rank_mean_K": sk.rank_mean,
-             "blocks_V": [sv.n_aca, sv.n_dense, sv.n_rank0], "blocks_K": [sk.n_aca, sk.n_dense, sk.n_rank0]}
+             "blocks_V": [sv.n_aca, sv.n_dense, sv.n_rank0], "blocks_K": [sk.n_aca, sk.n_dense, sk.n_rank0],
+             "faces_lowrank_V": [sv.n_faces_lowrank, sv.n_faces], "faces_lowrank_K": [sk.n_faces_lowrank, sk.n_faces],
+             "face_rank_mean_V": sv.face_rank_mean, "face_rank_mean_K": sk.face_rank_mean,
+             "face_aca_ms_V": sv.t_face_aca_ms, "face_aca_ms_K": sk.t_face_aca_ms,
+             "compress_ms_V": sv.t_compress_ms, "compress_ms_K": sk.t_compress_ms}
+
+    # error against the exact operator on sampled rows: the rows of C(s_k)
+    # from the library's FP64 entries (parity-checked against the oracle to
+    # 1e-10), applied to the same vectors
+    rows_sample = np.sort(np.random.default_rng(5).choice(len(xyz), 24, replace=False))
+    ctxE = g.Context(eps=WORKLOAD["eps"], precision=g.BEM_FP64, device=local)
+    ctxE.material(*syn.STEEL)
+    ctxE.freqs(s)
+    meshE = ctxE.mesh(xyz, tri)
+
+    def exact_rows(kern, X):
+        ncol = len(tri) if kern == g.BEM_SL else len(xyz)
+        r_, c_, k_ = np.meshgrid(rows_sample, np.arange(ncol), np.arange(K), indexing="ij")
+        req = torch.tensor(np.stack([r_.ravel(), c_.ravel(), k_.ravel()], 1).astype(np.int32), device=dev)
+        out = torch.empty((req.shape[0], 3, 3), dtype=torch.complex128, device=dev)
+        meshE.entries(g.BEM_ROWS_NODES, kern, req, out, stream)
+        C = out.view(len(rows_sample), ncol, K, 3, 3)
+        return torch.einsum("ijkab,kjb->kia", C, X.to(torch.complex128))
+
+    def rel(a, b):
+        return (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+
+    YV_ex = exact_rows(g.BEM_SL, XV)
+    YK_ex = exact_rows(g.BEM_DL, XK)
+    oV.apply(XV, YV, g.BEM_APPLY_BATCHED, stream)
+    oK.apply(XK, YK, g.BEM_APPLY_BATCHED, stream)
+    torch.cuda.synchronize()
+    rs = torch.tensor(rows_sample, device=dev)
+    extra.update({"mixed_vs_exact_rel_err_V": rel(YV[:, rs].to(torch.complex128), YV_ex),
+                  "mixed_vs_exact_rel_err_K": rel(YK[:, rs].to(torch.complex128), YK_ex),
+                  "error_sample": "24 seeded node rows x all columns x all 64 frequencies, FP64 entries"})
 
     # FP64 GPU form: same path in FP64, speedup and error of the mixed apply
     if not args.no_fp64:
@@ -272,7 +307,9 @@ def main():
         errK = (torch.linalg.norm(YK.to(torch.complex128) - YK64) / torch.linalg.norm(YK64)).item()
         extra.update({"fp64_entries_per_s": e64 / (ms64 / 1e3), "fp64_ms_per_step": ms64,
                       "mixed_vs_fp64_speedup": (ms64 / 1e3) / (ms / args.steps / 1e3),
-                      "mixed_vs_fp64_rel_err_V": errV, "mixed_vs_fp64_rel_err_K": errK})
+                      "mixed_vs_fp64_rel_err_V": errV, "mixed_vs_fp64_rel_err_K": errK,
+                      "fp64_vs_exact_rel_err_V": rel(YV64[:, rs], YV_ex),
+                      "fp64_vs_exact_rel_err_K": rel(YK64[:, rs], YK_ex)})
         del oV64, oK64
 
     # end to end through the public API with host buffers
@@ -313,7 +350,10 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.4 TB/s"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64 (FP32) far field + FP64 near/singular, pivots, norms",
+            "vs_baseline": None, "dtype": "c64",
+            "dtype_detail": ("MIXED: FP32 entries (near/singular included), float-float 3D-ACA faces/fibres "
+                             "during compression, c64 storage and apply; FP64 rigid-body diagonal, fibre step, "
+                             "pivots and norms"),
             "data": "synthetic", "config": dict(WORKLOAD, l2="inputs larger than L2 (faces ~GB)"),
             "clocks": clk.summary(),
             "e2e": {"value": e_entries / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

@@ -558,11 +558,30 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
   cx<double> f[9];
   for (int c = 0; c < 9; ++c) f[c] = {0, 0};
   S* fd = fib_tab[(int64_t)slot * nb + b];
+  cx<double> E[9];
+  bool heavy = false;
+  if constexpr (sizeof(R) == sizeof(float)) heavy = entry_heavy<KERN, ROWS>(v, i, j);
+  if (heavy) {
+    // a near/singular pivot entry is evaluated as k_face evaluates it
+    // (warp-cooperative, same point split and reduction): bitwise the same
+    // value at k = k_d, so that f_d[k_d] = I holds exactly
+    const int lane = threadIdx.x & 31, w0 = threadIdx.x & ~31;
+    for (int kk = 0; kk < 32 && w0 + kk < K; ++kk) {
+      cx<double> is2b;
+      const cx<double> s2 = freq(v, w0 + kk, is2b);
+      float part[18];
+      entry_f_warp<KERN, ROWS>(v, i, j, cx<float>{(float)s2.x, (float)s2.y}, cx<float>{(float)is2b.x, (float)is2b.y},
+                               w0 + kk, part);
+      if (lane == kk)
+        for (int c = 0; c < 9; ++c) E[c] = {(double)part[2 * c], (double)part[2 * c + 1]};
+    }
+  }
   if (ok) {
-    cx<double> E[9];
-    cx<double> is2;
-    cx<double> s = freq(v, k, is2);
-    entry<R, KERN, ROWS>(v, i, j, k, s, is2, E);
+    if (!heavy) {
+      cx<double> is2;
+      cx<double> s = freq(v, k, is2);
+      entry<R, KERN, ROWS>(v, i, j, k, s, is2, E);
+    }
     for (int p = 0; p < slot; ++p) {
       const S* Hp = face_tab[(int64_t)p * nb + b] + B.piv * 9;
       const S* fp = fib_tab[(int64_t)p * nb + b] + (int64_t)k * 9;
@@ -752,144 +771,125 @@ static bem_status finalize_storage(bem_ctx* ctx, OpData* d, cudaStream_t st) {
   }
   std::vector<void*> fin_face((size_t)nb * K, nullptr);
   if (ctx->opt.compress_faces) {
-    // (block, slot) items of the far blocks in slot order on a persistent
-    // queue; once a block's face of slot p stays dense its later faces are
-    // skipped (the pivot frequencies of Algorithm 1 move to larger |s| with
-    // d and the face ranks grow with them)
+    // slot by slot, one CTA per face; once a block's face of slot p stays
+    // dense its later faces are not attempted (the pivot frequencies of
+    // Algorithm 1 move to larger |s| with d and the face ranks grow with them)
     const double eps_face =
         d->prec == BEM_FP64 ? ctx->opt.eps_aca : std::max(ctx->opt.eps_aca, (double)kMixedFaceTolFloor);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    std::vector<int2> items;
-    std::vector<int32_t> hm(nb), hn(nb), hstop(nb, K);
-    int64_t mmax = 1, nmax = 1;
-    int tcmax = 1;
-    for (int64_t b = 0; b < nb; ++b) {
-      const BlkDev& B = d->h_blk[b];
-      hm[b] = (int32_t)B.m;
-      hn[b] = (int32_t)B.n;
-      if (B.status != ST_DONE || !B.far || B.rank < 1) continue;
-      mmax = std::max(mmax, B.m);
-      nmax = std::max(nmax, B.n);
-      tcmax = std::max(tcmax, face_tcap(B.m, B.n, face_tcap_max<W>()));
-    }
-    for (int p = 0; p < K; ++p) {
-      const size_t first = items.size();
+    auto job_bytes = [&](const FaceJob& j) {
+      const size_t c = sizeof(cx<W>), N = 3 * (size_t)j.tcap;
+      return al(c * 3 * j.m * N) + al(c * 3 * j.n * N) + al(c * 2 * N * N) + al(c * N * 3 * (j.m + j.n)) +
+             al(sizeof(int32_t) * j.tcap);
+    };
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t budget = std::max<size_t>(256u << 20, std::min<size_t>(size_t(4) << 30, free_b / 4));
+    // each batch's factors are copied from its scratch into a compact
+    // allocation owned by the operator
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    bem_status res = BEM_OK;
+    for (int slot = 0; slot < K && res == BEM_OK; ++slot) {
+      std::vector<FaceJob> jobs;
+      std::vector<int64_t> jidx;   // [slot][block] index of each job
       for (int64_t b = 0; b < nb; ++b) {
         const BlkDev& B = d->h_blk[b];
-        if (B.status == ST_DONE && B.far && p < B.rank) items.push_back(make_int2((int)b, p));
+        if (B.status != ST_DONE || !B.far || slot >= B.rank) continue;
+        if (slot > 0 && d->h_frank[(size_t)(slot - 1) * nb + b] < 0) continue;
+        FaceJob j{};
+        j.m = (int32_t)B.m;
+        j.n = (int32_t)B.n;
+        j.tcap = face_tcap(B.m, B.n, face_tcap_max<W>());
+        j.H = d->h_face[(size_t)slot * nb + b];
+        jobs.push_back(j);
+        jidx.push_back((int64_t)slot * nb + b);
       }
-      std::stable_sort(items.begin() + first, items.end(), [&](const int2& a, const int2& b) {
-        return (int64_t)hm[a.x] * hn[a.x] > (int64_t)hm[b.x] * hn[b.x];
-      });
-    }
-    const size_t jsm = 64u << 10;   // Jacobi matrices in shared memory up to this size
-    const int jsmem_n = (int)std::floor(std::sqrt((double)jsm / (2.0 * sizeof(cx<W>))));
-    cudaError_t e = cudaSuccess;
-    if (!items.empty()) {
-      e = cudaFuncSetAttribute(k_face_aca<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
-      int per_sm = 1, n_sm = 1;
-      if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_face_aca<W>, kFaceThreads, jsm);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
-      const size_t c = sizeof(cx<W>), N = 3 * (size_t)tcmax;
-      const size_t per_cta = al(c * 3 * mmax * N) + al(c * 3 * nmax * N) + al(c * 2 * N * N) + al(sizeof(int32_t) * tcmax);
-      const size_t n_cta = std::max<size_t>(1, std::min<size_t>(items.size(), (size_t)std::max(1, per_sm) * n_sm));
-      const size_t hdr = al(sizeof(int2) * items.size()) + al(sizeof(int32_t) * (3 * nb + 1 + nb * K)) +
-                         al(sizeof(FaceJob) * n_cta);
-      char* mem = nullptr;
-      if (e == cudaSuccess && cudaMalloc(&mem, hdr + per_cta * n_cta) != cudaSuccess) e = cudaErrorMemoryAllocation;
-      if (e == cudaSuccess) {
-        char* o = mem;
-        int2* d_items = (int2*)o;
-        o += al(sizeof(int2) * items.size());
-        int32_t* d_i32 = (int32_t*)o;   // counter, stop[nb], m[nb], n[nb], frank[nb K]
-        o += al(sizeof(int32_t) * (3 * nb + 1 + nb * K));
-        FaceJob* d_jobs = (FaceJob*)o;
-        o += al(sizeof(FaceJob) * n_cta);
-        std::vector<FaceJob> jobs(n_cta);
-        int32_t* d_fr = d_i32 + 1 + 3 * nb;
-        for (size_t q = 0; q < n_cta; ++q) {
-          FaceJob& j = jobs[q];
-          j = FaceJob{};
-          j.nb = nb;
-          j.face_tab = d->d_face;
-          j.frank = d_fr;
-          j.U = o;
-          o += al(c * 3 * mmax * N);
-          j.W = o;
-          o += al(c * 3 * nmax * N);
-          j.J = o;
-          o += al(c * 2 * N * N);
-          j.used = (int32_t*)o;
-          o += al(sizeof(int32_t) * tcmax);
+      if (jobs.empty()) break;
+      size_t j0 = 0;
+      while (j0 < jobs.size() && res == BEM_OK) {
+        size_t j1 = j0, bytes = 0;
+        while (j1 < jobs.size() && (j1 == j0 || bytes + job_bytes(jobs[j1]) <= budget)) bytes += job_bytes(jobs[j1++]);
+        const size_t nj = j1 - j0;
+        char* scr = nullptr;
+        FaceJob* d_jobs = nullptr;
+        int32_t* d_rank = nullptr;
+        if (cudaMalloc(&scr, bytes) != cudaSuccess || cudaMalloc(&d_jobs, sizeof(FaceJob) * nj) != cudaSuccess ||
+            cudaMalloc(&d_rank, sizeof(int32_t) * nj) != cudaSuccess) {
+          cudaFree(scr);
+          cudaFree(d_jobs);
+          res = set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for the face ACA");
+          break;
         }
-        std::vector<int32_t> h_i32(1 + 3 * nb);
-        h_i32[0] = 0;
-        std::copy(hstop.begin(), hstop.end(), h_i32.begin() + 1);
-        std::copy(hm.begin(), hm.end(), h_i32.begin() + 1 + nb);
-        std::copy(hn.begin(), hn.end(), h_i32.begin() + 1 + 2 * nb);
-        e = cudaMemcpyAsync(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(d_i32, h_i32.data(), sizeof(int32_t) * h_i32.size(), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(d_fr, d->h_frank.data(), sizeof(int32_t) * nb * K, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(FaceJob) * n_cta, cudaMemcpyHostToDevice, st);
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
+        size_t off = 0;
+        for (size_t q = j0; q < j1; ++q) {
+          FaceJob& j = jobs[q];
+          const size_t c = sizeof(cx<W>), N = 3 * (size_t)j.tcap;
+          j.U = scr + off;
+          off += al(c * 3 * j.m * N);
+          j.W = scr + off;
+          off += al(c * 3 * j.n * N);
+          j.J = scr + off;
+          off += al(c * 2 * N * N);
+          j.O = scr + off;
+          off += al(c * N * 3 * (j.m + j.n));
+          j.used = (int32_t*)(scr + off);
+          off += al(sizeof(int32_t) * j.tcap);
+        }
+        std::vector<int32_t> rk(nj, -1);
+        cudaError_t e = cudaMemcpyAsync(d_jobs, jobs.data() + j0, sizeof(FaceJob) * nj, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) {
-          FaceQueue fq{d_items, (int64_t)items.size(), d_i32, d_i32 + 1, d_i32 + 1 + nb, d_i32 + 1 + 2 * nb};
           cudaEventRecord(e0, st);
-          k_face_aca<W><<<(unsigned)n_cta, kFaceThreads, jsm, st>>>(fq, d_jobs, eps_face, jsmem_n);
+          k_face_aca<W><<<(unsigned)nj, kFaceThreads, 0, st>>>(d_jobs, d_rank, eps_face);
           e = cudaGetLastError();
           cudaEventRecord(e1, st);
           d->launches++;
           count_launches(1);
         }
         if (e == cudaSuccess)
-          e = cudaMemcpyAsync(d->h_frank.data(), d_fr, sizeof(int32_t) * nb * K, cudaMemcpyDeviceToHost, st);
+          e = cudaMemcpyAsync(rk.data(), d_rank, sizeof(int32_t) * nj, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e == cudaSuccess) {
           float ms = 0.f;
           cudaEventElapsedTime(&ms, e0, e1);
           d->t_face_aca_ms += ms;
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        size_t fb = 0;
+        for (size_t q = 0; q < nj && e == cudaSuccess; ++q)
+          if (rk[q] > 0) fb += sizeof(SF) * 3 * (size_t)rk[q] * (jobs[j0 + q].m + jobs[j0 + q].n);
+        char* fac = nullptr;
+        if (e != cudaSuccess) {
+          res = cuda_err(ctx, e, "bem_op_compress: face ACA");
+        } else if (fb > 0 && dmalloc(&fac, fb, own) != cudaSuccess) {
+          res = set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for face factors");
+        } else {
+          std::vector<Seg> segs;
+          size_t fo = 0;
+          for (size_t q = 0; q < nj; ++q) {
+            const FaceJob& j = jobs[q + j0];
+            const size_t idx = (size_t)jidx[q + j0];
+            d->h_frank[idx] = rk[q];
+            if (rk[q] < 0) continue;
+            d->n_faces_lr++;
+            d->face_rank_sum += rk[q];
+            if (rk[q] == 0) continue;
+            const int64_t ne = 3 * (int64_t)rk[q] * (j.m + j.n);
+            segs.push_back(Seg{j.O, fac + fo, ne, sizeof(cx<W>) == 16 ? 1 : 2});
+            fin_face[idx] = fac + fo;
+            fo += sizeof(SF) * ne;
+          }
+          res = run_segs(ctx, segs, st, d);
+        }
+        cudaFree(scr);
+        cudaFree(d_jobs);
+        cudaFree(d_rank);
+        j0 = j1;
       }
-      cudaFree(mem);
     }
-    if (e == cudaErrorMemoryAllocation)
-      return set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for the face ACA");
-    if (e != cudaSuccess) return cuda_err(ctx, e, "bem_op_compress: face ACA");
-    // compact storage of the factors (written over their faces, working precision)
-    size_t fb = 0;
-    for (int64_t b = 0; b < nb; ++b)
-      for (int p = 0; p < K; ++p) {
-        const int32_t fr = d->h_frank[(size_t)p * nb + b];
-        if (fr < 0) continue;
-        d->n_faces_lr++;
-        d->face_rank_sum += fr;
-        fb += sizeof(SF) * 3 * (size_t)fr * (d->h_blk[b].m + d->h_blk[b].n);
-      }
-    char* fac = nullptr;
-    if (fb > 0 && dmalloc(&fac, fb, own) != cudaSuccess)
-      return set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for face factors");
-    std::vector<Seg> segs;
-    size_t fo = 0;
-    for (int64_t b = 0; b < nb; ++b)
-      for (int p = 0; p < K; ++p) {
-        const size_t idx = (size_t)p * nb + b;
-        const int32_t fr = d->h_frank[idx];
-        if (fr <= 0) continue;
-        const int64_t ne = 3 * (int64_t)fr * (d->h_blk[b].m + d->h_blk[b].n);
-        segs.push_back(Seg{d->h_face[idx], fac + fo, ne, sizeof(cx<W>) == 16 ? 1 : 2});
-        fin_face[idx] = fac + fo;
-        fo += sizeof(SF) * ne;
-      }
-    bem_status r = run_segs(ctx, segs, st, d);
-    if (r != BEM_OK) return r;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (res != BEM_OK) return res;
   }
   // dense faces and all fibres
   size_t bytes = 0;
@@ -1173,49 +1173,33 @@ static bem_status face_compress_t(bem_ctx* ctx, const void* H, int64_t m, int64_
   j.m = (int32_t)m;
   j.n = (int32_t)n;
   j.tcap = face_tcap(m, n, face_tcap_max<W>());
-  j.rank = 1;
-  j.nb = 1;
-  j.blk = 0;
   const size_t c = sizeof(cx<W>), N = 3 * (size_t)j.tcap;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t bH = al(sizeof(SC) * 9 * m * n), bU = al(c * 3 * m * N), bW = al(c * 3 * n * N),
-               bJ = al(c * 2 * N * N), bu = al(sizeof(int32_t) * j.tcap);
+               bJ = al(c * 2 * N * N), bO = al(c * N * 3 * (m + n)), bu = al(sizeof(int32_t) * j.tcap);
   char* scr = nullptr;
-  GCQ_CUDA(ctx, cudaMalloc(&scr, bH + bU + bW + bJ + bu + sizeof(FaceJob) + 512));
-  void* Hst = scr;
+  GCQ_CUDA(ctx, cudaMalloc(&scr, bH + bU + bW + bJ + bO + bu + 512));
+  j.H = scr;
   j.U = scr + bH;
   j.W = scr + bH + bU;
   j.J = scr + bH + bU + bW;
-  j.used = (int32_t*)(scr + bH + bU + bW + bJ);
-  char* tail = scr + bH + bU + bW + bJ + bu;
-  FaceJob* d_job = (FaceJob*)tail;
-  void** d_tab = (void**)(tail + sizeof(FaceJob));
-  int32_t* d_i32 = (int32_t*)(tail + sizeof(FaceJob) + sizeof(void*));   // frank, counter, stop, m, n
-  int2* d_item = (int2*)(d_i32 + 6);
-  j.frank = d_i32;
-  j.face_tab = d_tab;
+  j.O = scr + bH + bU + bW + bJ;
+  j.used = (int32_t*)(scr + bH + bU + bW + bJ + bO);
+  FaceJob* d_job = (FaceJob*)(scr + bH + bU + bW + bJ + bO + bu);
+  int32_t* d_rank = (int32_t*)(d_job + 1);
   const double eps_face = std::is_same<W, double>::value ? eps : std::max(eps, (double)kMixedFaceTolFloor);
-  const size_t jsm = 64u << 10;
-  const int jsmem_n = (int)std::floor(std::sqrt((double)jsm / (2.0 * sizeof(cx<W>))));
   int32_t rk = -1;
-  const int32_t h_i32[6] = {-1, 0, 1, (int32_t)m, (int32_t)n, 0};
-  const int2 item = make_int2(0, 0);
   cudaError_t e = cudaMemcpyAsync(d_job, &j, sizeof(FaceJob), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, &Hst, sizeof(void*), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_i32, h_i32, sizeof(h_i32), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_item, &item, sizeof(int2), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_face_aca<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
   if (e == cudaSuccess) {
-    k_face_store<SC><<<256, 256, 0, st>>>((const double2*)H, (SC*)Hst, 9 * m * n);
-    FaceQueue fq{d_item, 1, d_i32 + 1, d_i32 + 2, d_i32 + 3, d_i32 + 4};
-    k_face_aca<W><<<1, kFaceThreads, jsm, st>>>(fq, d_job, eps_face, jsmem_n);
+    k_face_store<SC><<<256, 256, 0, st>>>((const double2*)H, (SC*)scr, 9 * m * n);
+    k_face_aca<W><<<1, kFaceThreads, 0, st>>>(d_job, d_rank, eps_face);
     count_launches(2);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&rk, j.frank, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&rk, d_rank, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && rk > 0) {
-    std::vector<Seg> segs{Seg{Hst, out, 3 * (int64_t)rk * (m + n), sizeof(cx<W>) == 16 ? 1 : 2}};
+    std::vector<Seg> segs{Seg{j.O, out, 3 * (int64_t)rk * (m + n), sizeof(cx<W>) == 16 ? 1 : 2}};
     OpData tmp;
     bem_status r = run_segs(ctx, segs, st, &tmp);
     if (r != BEM_OK) {

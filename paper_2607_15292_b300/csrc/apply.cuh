@@ -34,12 +34,13 @@ struct Ld<float2, float> {
   }
 };
 
-// dense fallback blocks: Y_k[rows] += D_k X_k[cols]; CTA per (block, k), warp per row
+// dense fallback blocks, contracted: y[rows] += sum_k D_k X_k[cols] (FP64
+// atomics into y, original order); CTA per (block, k), warp per row
 template <typename S, typename A>
 __global__ void k_apply_dense(const BlkDev* __restrict__ blk, const int32_t* __restrict__ list,
                               S* const* __restrict__ dense, const int32_t* __restrict__ row_perm,
-                              const int32_t* __restrict__ col_perm, const S* __restrict__ X, S* __restrict__ Y, int K,
-                              int64_t n_rows, int64_t n_cols, int contracted) {
+                              const int32_t* __restrict__ col_perm, const S* __restrict__ X, double* __restrict__ Y,
+                              int K, int64_t n_cols) {
   const int b = list[blockIdx.x];
   const int k = blockIdx.y;
   const BlkDev& B = blk[b];
@@ -61,9 +62,8 @@ __global__ void k_apply_dense(const BlkDev* __restrict__ blk, const int32_t* __r
         acc[a].y += __shfl_down_sync(0xffffffffu, acc[a].y, o);
       }
     if (lane == 0) {
-      const int64_t row = row_perm[B.r0 + li];
-      A* y = (A*)(Y + (contracted ? row * 3 : ((int64_t)k * n_rows + row) * 3));
-      for (int a = 0; a < 3; ++a) atomic_add_c(y + 2 * a, acc[a]);
+      double* y = Y + (int64_t)row_perm[B.r0 + li] * 6;
+      for (int a = 0; a < 3; ++a) atomic_add_c<double>(y + 2 * a, cx<double>{(double)acc[a].x, (double)acc[a].y});
     }
   }
 }
@@ -123,7 +123,7 @@ __global__ void k_contract_apply(const BlkDev* __restrict__ blk, const int32_t* 
                                  S* const* __restrict__ face_tab, const int32_t* __restrict__ frank,
                                  const int64_t* __restrict__ toff, const cx<A>* __restrict__ T, int64_t nb,
                                  const int64_t* __restrict__ zoff, const int32_t* __restrict__ row_perm,
-                                 const cx<A>* __restrict__ Z, S* __restrict__ Y) {
+                                 const cx<A>* __restrict__ Z, double* __restrict__ Y) {
   const int ai = blockIdx.x;
   const int b = list[ai];
   const BlkDev& B = blk[b];
@@ -153,8 +153,8 @@ __global__ void k_contract_apply(const BlkDev* __restrict__ blk, const int32_t* 
         acc[a].y += __shfl_down_sync(0xffffffffu, acc[a].y, o);
       }
     if (lane == 0) {
-      A* y = (A*)(Y + (int64_t)row_perm[B.r0 + li] * 3);
-      for (int a = 0; a < 3; ++a) atomic_add_c(y + 2 * a, acc[a]);
+      double* y = Y + (int64_t)row_perm[B.r0 + li] * 6;
+      for (int a = 0; a < 3; ++a) atomic_add_c<double>(y + 2 * a, cx<double>{(double)acc[a].x, (double)acc[a].y});
     }
   }
 }
@@ -200,10 +200,18 @@ __device__ __forceinline__ void load_f(cx<A>* sF, const S* __restrict__ f, int k
     sF[c] = kk < nk ? Ld<S, A>::ld(f + (int64_t)(k0 + kk) * 9 + c % 9) : cx<A>{A(0), A(0)};
   }
 }
-// acc[t][a] += sum_jj sum_b sH[r][jj][a][b] sZ[jj][b][kq + kTPR t]
+// part[t][a] = sum_jj sum_b sH[r][jj][a][b] sZ[jj][b][kq + kTPR t]; acc += part.
+// Two-level summation: each chunk (3 kBN terms per output) is summed in a
+// fresh register before it joins the block's accumulator, so that FP32
+// rounding grows with sqrt(3 kBN + chunks) instead of sqrt(all terms).
 template <typename A>
 __device__ __forceinline__ void mac_chunk(cx<A> (&acc)[kBK / kTPR][3], const cx<A>* sH, const cx<A>* sZ, int r,
                                           int kq) {
+  cx<A> part[kBK / kTPR][3];
+#pragma unroll
+  for (int t = 0; t < kBK / kTPR; ++t)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) part[t][a] = {A(0), A(0)};
 #pragma unroll 4
   for (int jj = 0; jj < kBN; ++jj) {
     cx<A> h[9];
@@ -215,20 +223,25 @@ __device__ __forceinline__ void mac_chunk(cx<A> (&acc)[kBK / kTPR][3], const cx<
       for (int t = 0; t < kBK / kTPR; ++t) {
         const cx<A> z = sZ[(jj * 3 + b) * kBK + kq + kTPR * t];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) acc[t][a] = cfma(h[3 * a + b], z, acc[t][a]);
+        for (int a = 0; a < 3; ++a) part[t][a] = cfma(h[3 * a + b], z, part[t][a]);
       }
   }
+#pragma unroll
+  for (int t = 0; t < kBK / kTPR; ++t)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) acc[t][a] = acc[t][a] + part[t][a];
 }
 
 template <typename S, typename A>
-__global__ void __launch_bounds__(kApplyThreads) k_apply_faces(const BlkDev* __restrict__ blk,
+__global__ void __launch_bounds__(kApplyThreads, sizeof(A) == 4 ? 2 : 1) k_apply_faces(const BlkDev* __restrict__ blk,
                                                                const int4* __restrict__ items,
                                                                S* const* __restrict__ face_tab,
                                                                S* const* __restrict__ fib_tab,
                                                                const int32_t* __restrict__ frank,
                                                                const int64_t* __restrict__ toff,
                                                                const cx<A>* __restrict__ T, int64_t nb,
-                                                               const S* __restrict__ Xp, A* __restrict__ Yp, int K) {
+                                                               const S* __restrict__ Xp, double* __restrict__ Yp,
+                                                               int K) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<A>* sH = reinterpret_cast<cx<A>*>(smem_raw);       // [kBM][kBN * 9 + 1] (padded rows)
   cx<A>* sZ = sH + kBM * kSHR;                           // [kBN][3][kBK]
@@ -295,8 +308,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_faces(const BlkDev* __r
     for (int t = 0; t < kBK / kTPR; ++t) {
       const int kk = kq + kTPR * t;
       if (kk < nk) {
-        A* y = Yp + (((B.r0 + gi) * K + k0 + kk) * 3) * 2;
-        for (int a = 0; a < 3; ++a) atomic_add_c(y + 2 * a, acc[t][a]);
+        double* y = Yp + (((B.r0 + gi) * K + k0 + kk) * 3) * 2;
+        for (int a = 0; a < 3; ++a) atomic_add_c<double>(y + 2 * a, cx<double>{(double)acc[t][a].x, (double)acc[t][a].y});
       }
     }
 }
@@ -373,15 +386,54 @@ __global__ void k_perm_x(const S* __restrict__ X, S* __restrict__ Xp, const int3
   for (int c = 0; c < 3; ++c) dst[c] = src[c];
 }
 template <typename S>
-__global__ void k_unperm_y(const S* __restrict__ Yp, S* __restrict__ Y, const int32_t* __restrict__ perm, int64_t n,
-                           int K) {
+__global__ void k_unperm_y(const double2* __restrict__ Yp, S* __restrict__ Y, const int32_t* __restrict__ perm,
+                           int64_t n, int K) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * K) return;
   const int64_t pos = t / K;
   const int k = (int)(t - pos * K);
-  const S* src = Yp + t * 3;
+  const double2* src = Yp + t * 3;
   S* dst = Y + ((int64_t)k * n + perm[pos]) * 3;
-  for (int c = 0; c < 3; ++c) dst[c] = src[c];
+  for (int c = 0; c < 3; ++c) St<S>::st(dst + c, cx<double>{src[c].x, src[c].y});
+}
+
+template <typename S>
+__global__ void k_from_double(const double2* __restrict__ src, S* __restrict__ dst, int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) St<S>::st(dst + t, cx<double>{src[t].x, src[t].y});
+}
+
+// dense fallback blocks, batched: Yp[r0 + li][k] += D_k[li][lj] Xp[c0 + lj][k]
+// (cluster order, FP64 atomics); CTA per (block, k), warp per row
+template <typename S, typename A>
+__global__ void k_apply_dense_p(const BlkDev* __restrict__ blk, const int32_t* __restrict__ list,
+                                S* const* __restrict__ dense, const S* __restrict__ Xp, double* __restrict__ Yp,
+                                int K) {
+  const int b = list[blockIdx.x];
+  const int k = blockIdx.y;
+  const BlkDev& B = blk[b];
+  const S* D = dense[b] + (int64_t)k * B.m * B.n * 9;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t li = w; li < B.m; li += nw) {
+    cx<A> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int64_t lj = lane; lj < B.n; lj += 32) {
+      const S* xp = Xp + ((B.c0 + lj) * K + k) * 3;
+      cx<A> x[3];
+      for (int c = 0; c < 3; ++c) x[c] = Ld<S, A>::ld(xp + c);
+      const S* d = D + (li * B.n + lj) * 9;
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) acc[a] = cfma(Ld<S, A>::ld(d + 3 * a + c), x[c], acc[a]);
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[a].x += __shfl_down_sync(0xffffffffu, acc[a].x, o);
+        acc[a].y += __shfl_down_sync(0xffffffffu, acc[a].y, o);
+      }
+    if (lane == 0) {
+      double* y = Yp + (((B.r0 + li) * K + k) * 3) * 2;
+      for (int a = 0; a < 3; ++a) atomic_add_c<double>(y + 2 * a, cx<double>{(double)acc[a].x, (double)acc[a].y});
+    }
+  }
 }
 
 bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
@@ -438,7 +490,7 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
   d->n_zitems = (int64_t)zitems.size();
   const size_t es = d->prec == BEM_FP64 ? sizeof(double2) : sizeof(float2);
   GCQ_CUDA(ctx, dmalloc(&d->d_xp, es * 3 * (size_t)d->K * d->n_cols, own));
-  GCQ_CUDA(ctx, dmalloc(&d->d_yp, es * 3 * (size_t)d->K * d->n_rows, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_yp, sizeof(double2) * 3 * (size_t)d->K * d->n_rows, own));
   GCQ_CUDA(ctx, dmalloc(&d->d_z, es * std::max<int64_t>(1, z), own));
   GCQ_CUDA(ctx, dmalloc(&d->d_t, es * std::max<int64_t>(1, tt), own));
   // algorithmic bytes of one batched apply: stored operator + X + Y
@@ -452,13 +504,12 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
   bem_ctx* ctx = op->tree->mesh->ctx;
   const S* X = (const S*)Xv;
   S* Y = (S*)Yv;
-  if (mode != BEM_APPLY_BATCHED) GCQ_CUDA(ctx, cudaMemsetAsync(Y, 0, sizeof(S) * d->n_rows * 3, st));
   if (mode == BEM_APPLY_BATCHED) {
     const int64_t nx = (int64_t)d->n_cols * d->K, nyp = (int64_t)d->n_rows * d->K;
     k_perm_x<S><<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(X, (S*)d->d_xp, d->d_col_perm, d->n_cols, d->K);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
-    GCQ_CUDA(ctx, cudaMemsetAsync(d->d_yp, 0, sizeof(S) * 3 * nyp, st));
+    GCQ_CUDA(ctx, cudaMemsetAsync(d->d_yp, 0, sizeof(double2) * 3 * nyp, st));
     const size_t smem = sizeof(cx<A>) * (kBM * kSHR + kBN * 3 * kBK + kBK * 9);
     if (d->n_lr_items > 0) {
       cudaFuncSetAttribute(k_apply_lr_t<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -472,24 +523,26 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
       cudaFuncSetAttribute(k_apply_faces<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_apply_faces<S, A><<<(unsigned)d->n_apply_items, kApplyThreads, smem, st>>>(
           d->d_blk, (const int4*)d->d_apply_items, (S* const*)d->d_face, (S* const*)d->d_fib, d->d_frank,
-          d->d_toff, (const cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_xp, (A*)d->d_yp, d->K);
+          d->d_toff, (const cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_xp, (double*)d->d_yp, d->K);
       GCQ_CUDA(ctx, cudaGetLastError());
       count_launches(1);
     }
-    k_unperm_y<S><<<(unsigned)((nyp + 255) / 256), 256, 0, st>>>((const S*)d->d_yp, Y, d->d_row_perm, d->n_rows,
-                                                                 d->K);
-    GCQ_CUDA(ctx, cudaGetLastError());
-    count_launches(1);
     if (d->n_dense > 0) {
       dim3 g((unsigned)d->n_dense, (unsigned)d->K);
-      k_apply_dense<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense, d->d_row_perm,
-                                             d->d_col_perm, X, Y, d->K, d->n_rows, d->n_cols, 0);
+      k_apply_dense_p<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense,
+                                               (const S*)d->d_xp, (double*)d->d_yp, d->K);
       GCQ_CUDA(ctx, cudaGetLastError());
       count_launches(1);
     }
+    k_unperm_y<S><<<(unsigned)((nyp + 255) / 256), 256, 0, st>>>((const double2*)d->d_yp, Y, d->d_row_perm,
+                                                                 d->n_rows, d->K);
+    GCQ_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
     return BEM_OK;
   }
-  // contracted
+  // contracted: accumulated in FP64 (d_yp, original row order), then converted
+  double* yc = (double*)d->d_yp;
+  GCQ_CUDA(ctx, cudaMemsetAsync(yc, 0, sizeof(double2) * 3 * d->n_rows, st));
   if (d->n_zitems > 0) {
     k_contract_z<S, A><<<(unsigned)d->n_zitems, 128, 0, st>>>(d->d_blk, (const int4*)d->d_zitems,
                                                               (S* const*)d->d_fib, d->n_blocks, d->d_zoff,
@@ -506,17 +559,21 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
     dim3 g((unsigned)d->n_aca, 8);
     k_contract_apply<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_aca_list, (S* const*)d->d_face, d->d_frank,
                                               d->d_toff, (const cx<A>*)d->d_t, d->n_blocks, d->d_zoff,
-                                              d->d_row_perm, (const cx<A>*)d->d_z, Y);
+                                              d->d_row_perm, (const cx<A>*)d->d_z, yc);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
   }
   if (d->n_dense > 0) {
     dim3 g((unsigned)d->n_dense, (unsigned)d->K);
     k_apply_dense<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense, d->d_row_perm,
-                                           d->d_col_perm, X, Y, d->K, d->n_rows, d->n_cols, 1);
+                                           d->d_col_perm, X, yc, d->K, d->n_cols);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
   }
+  const int64_t ny = 3 * d->n_rows;
+  k_from_double<S><<<(unsigned)((ny + 255) / 256), 256, 0, st>>>((const double2*)yc, Y, ny);
+  GCQ_CUDA(ctx, cudaGetLastError());
+  count_launches(1);
   return BEM_OK;
 }
 

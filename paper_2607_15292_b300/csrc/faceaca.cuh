@@ -53,18 +53,23 @@ __host__ __device__ constexpr double face_tiny() {
   return sizeof(W) == 8 ? kTiny : 2.384185791015625e-7;
 }
 
-// A face of a far block and the scratch its compression uses.
+// One face of a far block and the scratch its compression uses.
 struct FaceJob {
-  int32_t blk, m, n, tcap, rank, pad;
-  int64_t nb;
-  void* const* face_tab;   // [slot][block] faces [i][j][3][3] (compression storage);
-                           // a face's factors overwrite its own storage
-  int32_t* frank;          // [slot][block] result: rank k >= 0 or -1 (dense)
-  void* U;                 // 3m x 3 tcap, column-major (working type)
-  void* W;                 // 3n x 3 tcap
-  void* J;                 // 2 (3 tcap)^2: Jacobi matrix and right vectors (when not in shared memory)
-  int32_t* used;           // tcap rows
+  int32_t m, n, tcap, pad;
+  const void* H;     // face [i][j][3][3] (compression storage)
+  void* U;           // 3m x 3 tcap, column-major (working type)
+  void* W;           // 3n x 3 tcap
+  void* J;           // 2 (3 tcap)^2: Jacobi matrix and right vectors
+  void* O;           // 3 tcap (3m + 3n): output factors U' then W'
+  int32_t* used;     // tcap rows
 };
+
+__host__ __device__ inline int face_tcap(int64_t m, int64_t n, int cap) {
+  const int64_t even = (5 * m * n) / (4 * (m + n)) + 1;   // 1.25 x the storage break-even steps
+  int64_t t = m < n ? m : n;
+  t = t < cap ? t : cap;
+  return (int)(t < even ? t : even);
+}
 
 // residual accumulators: value of H minus sums of products of the factors
 template <typename W>
@@ -360,12 +365,10 @@ struct FaceSm {
   W hist[TM];            // ACA error estimates ||u_t|| ||v_t|| / ||H||
 };
 
-// one face: ACA + recompression; returns the rank k (factors written over
-// the face's own storage, which they fit: 3k(m + n) < 9mn complex of at
-// most the storage's size) or -1 (dense face, storage untouched)
+// one face: ACA + recompression; returns the rank k (factors U' then W'
+// written to jb.O) or -1 (dense face)
 template <typename W>
-__device__ int face_one(const FaceJob& jb, typename FaceSt<W>::S* Hst, FaceSm<W>& sm, cx<W>* dynJ, int jsmem_n,
-                        W eps_face) {
+__device__ int face_one(const FaceJob& jb, FaceSm<W>& sm, W eps_face) {
   using S = typename FaceSt<W>::S;
   cx<W>* sUi = sm.sUi;
   cx<W>* sVj = sm.sVj;
@@ -375,7 +378,7 @@ __device__ int face_one(const FaceJob& jb, typename FaceSt<W>::S* Hst, FaceSm<W>
   W* hist = sm.hist;
   int &s_state = sm.s_state, &s_i = sm.s_i, &s_j = sm.s_j, &s_k = sm.s_k, &s_flag = sm.s_flag;
   const int64_t m = jb.m, n = jb.n, M3 = 3 * m, N3 = 3 * n;
-  const S* H = Hst;
+  const S* H = (const S*)jb.H;
   cx<W>* U = (cx<W>*)jb.U;
   cx<W>* Wf = (cx<W>*)jb.W;
   // power-of-two scale of the face
@@ -573,7 +576,7 @@ __device__ int face_one(const FaceJob& jb, typename FaceSt<W>::S* Hst, FaceSm<W>
   const int N = 3 * t;
   house_qr<W>(U, M3, N, sm.alphaU, sm.tauU, sh);
   house_qr<W>(Wf, N3, N, sm.alphaW, sm.tauW, sh);
-  cx<W>* G = N <= jsmem_n ? dynJ : (cx<W>*)jb.J;
+  cx<W>* G = (cx<W>*)jb.J;
   cx<W>* B = G + (int64_t)N * N;
   // G = R_U R_W^T (column-major), B = I
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
@@ -624,7 +627,7 @@ __device__ int face_one(const FaceJob& jb, typename FaceSt<W>::S* Hst, FaceSm<W>
   __syncthreads();
   const int k = s_k;
   if ((int64_t)k * (m + n) >= 3 * m * n) return -1;
-  cx<W>* OU = (cx<W>*)Hst;   // the face is not read any more
+  cx<W>* OU = (cx<W>*)jb.O;
   cx<W>* OW = OU + M3 * k;
   // OU = [G[:, order[:k]]; 0] (A_k Sigma_k), OW = [conj B[:, order[:k]]; 0], scaled back
   for (int64_t e = threadIdx.x; e < M3 * k; e += blockDim.x) {
@@ -643,67 +646,14 @@ __device__ int face_one(const FaceJob& jb, typename FaceSt<W>::S* Hst, FaceSm<W>
   return k;
 }
 
-// Persistent work queue over (block, slot) items ordered by slot: each CTA
-// takes the next item, skips it when a lower slot of that block already
-// stayed dense (stop[block] < slot), and otherwise compresses the face with
-// its own scratch (jobs[blockIdx.x]: U, W, J, used sized for the largest
-// item).  Items of one block thus run on several CTAs at once while the
-// faces after a dense one are (mostly) never attempted.
-struct FaceQueue {
-  const int2* items;       // (block, slot)
-  int64_t n_items;
-  int32_t* counter;        // next item
-  int32_t* stop;           // [block]: lowest slot found dense (K if none)
-  const int32_t* m;        // [block] rows, columns
-  const int32_t* n;
-};
-
-__host__ __device__ inline int face_tcap(int64_t m, int64_t n, int cap) {
-  const int64_t even = (5 * m * n) / (4 * (m + n)) + 1;   // 1.25 x the storage break-even steps
-  int64_t t = m < n ? m : n;
-  t = t < cap ? t : cap;
-  return (int)(t < even ? t : even);
-}
-
+// one CTA per face; out_rank[job] = k or -1
 template <typename W>
-__global__ void __launch_bounds__(kFaceThreads) k_face_aca(FaceQueue q, const FaceJob* __restrict__ scratch,
-                                                           double eps_face, int jsmem_n) {
-  extern __shared__ __align__(16) unsigned char face_dyn[];   // Jacobi G, B when N <= jsmem_n
+__global__ void __launch_bounds__(kFaceThreads) k_face_aca(const FaceJob* __restrict__ jobs,
+                                                           int32_t* __restrict__ out_rank, double eps_face) {
   __shared__ FaceSm<W> sm;
-  __shared__ int s_item, s_skip;
-  FaceJob jb = scratch[blockIdx.x];
-  while (true) {
-    // thread 0 takes the item and decides on skipping it (stop[] changes
-    // under other CTAs: one read, broadcast, keeps the CTA uniform)
-    if (threadIdx.x == 0) {
-      const int it = atomicAdd(q.counter, 1);
-      s_item = it;
-      s_skip = 0;
-      if (it < q.n_items) {
-        const int2 bp = q.items[it];
-        s_skip = bp.y > 0 && *((volatile int32_t*)q.stop + bp.x) < bp.y;   // a lower slot stayed dense
-        if (bp.x < 0 || bp.x >= jb.nb || jb.face_tab[(int64_t)bp.y * jb.nb + bp.x] == nullptr) s_skip = 1;
-      }
-    }
-    __syncthreads();
-    const int it = s_item, skip = s_skip;
-    __syncthreads();
-    if (it >= q.n_items) break;
-    if (skip) continue;
-    const int2 bp = q.items[it];
-    jb.blk = bp.x;
-    jb.m = q.m[bp.x];
-    jb.n = q.n[bp.x];
-    jb.tcap = face_tcap(jb.m, jb.n, face_tcap_max<W>());
-    const int64_t idx = (int64_t)bp.y * jb.nb + bp.x;
-    auto* H = (typename FaceSt<W>::S*)jb.face_tab[idx];
-    const int k = face_one<W>(jb, H, sm, (cx<W>*)face_dyn, jsmem_n, (W)eps_face);
-    if (threadIdx.x == 0) {
-      jb.frank[idx] = k;
-      if (k < 0) atomicMin(q.stop + bp.x, bp.y);
-    }
-    __syncthreads();
-  }
+  const FaceJob jb = jobs[blockIdx.x];
+  const int k = face_one<W>(jb, sm, (W)eps_face);
+  if (threadIdx.x == 0) out_rank[blockIdx.x] = k;
 }
 
 }  // namespace gcq
