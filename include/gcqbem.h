@@ -186,11 +186,19 @@ bem_status bem_tree_export(const bem_tree* tree, int32_t* row_perm, int32_t* col
 bem_status bem_op_compress(bem_tree* tree, void* stream, bem_op** out);
 void bem_op_destroy(bem_op* op);
 
-/* Apply (Eq. (3.15)).  BATCHED: X device K x n_cols x 3 complex,
- * Y device K x n_rows x 3 complex, Y_k = C(s_k) X_k (Y overwritten).
- * CONTRACTED: X as above, Y device n_rows x 3 complex, Y = sum_k C(s_k) X_k.
- * Complex type c128 (FP64) or c64 (MIXED).  transpose = 0 only (reserved).
- * Asynchronous on the stream; no host synchronisation. */
+/* Apply (Eq. (3.15)).  transpose = 0:
+ *   BATCHED: X device K x n_cols x 3 complex, Y device K x n_rows x 3
+ *   complex, Y_k = C(s_k) X_k (Y overwritten).
+ *   CONTRACTED: X as above, Y device n_rows x 3 complex,
+ *   Y = sum_k C(s_k) X_k.
+ * transpose = 1 (adjoint, conjugate transpose): the first buffer is the
+ * input and the second the output, both overwritten-free (input read only):
+ *   BATCHED: in K x n_rows x 3, out K x n_cols x 3, out_k = C(s_k)^H in_k.
+ *   CONTRACTED: in n_rows x 3, out K x n_cols x 3, out_k = C(s_k)^H in (the
+ *   adjoint of the contracted apply).
+ * Complex type c128 (FP64) or c64 (MIXED); FP32 products are summed in two
+ * levels and accumulated across blocks in FP64.  Asynchronous on the
+ * stream; no host synchronisation. */
 bem_status bem_op_apply(bem_op* op, int32_t mode, int32_t transpose,
                         const void* X, void* Y, void* stream);
 

@@ -280,3 +280,11 @@ def apply_contracted(blocks, W: np.ndarray, n_rows: int) -> np.ndarray:
 def apply_dense(C: np.ndarray, X: np.ndarray) -> np.ndarray:
     """Y[:, :, k] = C[:, :, k] X[:, :, k]: C (M, N, K, 3, 3), X (N, 3, K)."""
     return np.einsum("ijkab,jbk->iak", C, X)
+
+
+def apply_adjoint_dense(C: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """Conjugate-transpose apply, X[:, :, k] = C[:, :, k]^H Y[:, :, k]:
+    C (M, N, K, 3, 3), Y (M, 3, K) -> X (N, 3, K).  The 3M x 3N matrix of
+    frequency k has block (i, j) = C[i, j, k]; its conjugate transpose has
+    block (j, i) = C[i, j, k]^H."""
+    return np.einsum("ijkab,iak->jbk", C.conj(), Y)

@@ -307,8 +307,13 @@ class Operator:
         except Exception:
             pass
 
-    def apply(self, X, Y, mode: int = BEM_APPLY_BATCHED, stream=None):
-        _check(_lib.bem_op_apply(self._p, mode, 0, _dptr(X), _dptr(Y), _stream_ptr(stream)), self.ctx.ptr)
+    def apply(self, X, Y, mode: int = BEM_APPLY_BATCHED, stream=None, transpose: int = 0):
+        """transpose = 0: Y = C X; transpose = 1: Y = C^H X (X is then the
+        row-side input, Y the column-side output)."""
+        _check(_lib.bem_op_apply(self._p, mode, transpose, _dptr(X), _dptr(Y), _stream_ptr(stream)), self.ctx.ptr)
+
+    def apply_adjoint(self, Yin, Xout, mode: int = BEM_APPLY_BATCHED, stream=None):
+        self.apply(Yin, Xout, mode, stream, transpose=1)
 
     def dense(self, out, stream=None):
         _check(_lib.bem_op_dense(self._p, _dptr(out), _stream_ptr(stream)), self.ctx.ptr)

@@ -91,7 +91,14 @@ struct OpData {
   void* d_t = nullptr;
   int32_t* d_lr_items = nullptr;     // (block, slot, pseudo-row tile, k tile) int4
   int64_t n_lr_items = 0;
-  int32_t* d_lr_faces = nullptr;     // (block, slot) int2 of low-rank faces with k > 0
+  int32_t* d_lr_faces = nullptr;     // (block, slot, aca index, 0) int4 of low-rank faces with k > 0
+  // adjoint apply: items (block, column tile, k tile) and (block, slot, rank tile, k tile)
+  int32_t* d_adj_items = nullptr;
+  int64_t n_adj_items = 0;
+  int32_t* d_adj_lr_items = nullptr;
+  int64_t n_adj_lr_items = 0;
+  void* d_yq = nullptr;              // adjoint input in row cluster order, n_rows x K x 3
+  void* d_xacc = nullptr;            // adjoint output accumulator, n_cols x K x 3 complex double
   int64_t n_lr_faces = 0;
 };
 

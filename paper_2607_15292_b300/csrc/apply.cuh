@@ -373,6 +373,239 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_lr_t(const BlkDev* __re
   }
 }
 
+// ---- adjoint (conjugate-transpose) apply --------------------------------------
+// X_k = C(s_k)^H Y_k:  x_j[k] = sum_p f_p[k]^H sum_i H_p[i,j]^H y_i[k]
+// (the face is contracted over the rows first, the fibre applied after).
+// Yq: n_rows x K x 3 (input in cluster order), Xacc: n_cols x K x 3 complex
+// double (output accumulated with FP64 atomics).  A CTA owns kAN columns x
+// kAK frequencies of one block; each thread one column and 4 frequencies.
+constexpr int kAN = 32, kAK = 32, kAR = 16, kATPR = 8;
+constexpr int kASH = kAR * 9 + 1;   // padded column stride of the face tile
+
+template <typename S, typename A>
+__global__ void __launch_bounds__(kAN * kATPR) k_apply_faces_adj(const BlkDev* __restrict__ blk,
+                                                                 const int4* __restrict__ items,
+                                                                 S* const* __restrict__ face_tab,
+                                                                 S* const* __restrict__ fib_tab,
+                                                                 const int32_t* __restrict__ frank,
+                                                                 const int64_t* __restrict__ toff,
+                                                                 const cx<A>* __restrict__ T, int64_t nb,
+                                                                 const S* __restrict__ Yq, double* __restrict__ Xacc,
+                                                                 int K) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<A>* sH = reinterpret_cast<cx<A>*>(smem_raw);   // [col][row chunk x 9] or [col][rank chunk x 3]
+  cx<A>* sY = sH + kAN * kASH;                      // [row x 3 | rank][freq]
+  cx<A>* sF = sY + kAR * 3 * kAK;                   // [freq][9]
+  constexpr int NT = kAK / kATPR;
+  const int4 it = items[blockIdx.x];
+  const BlkDev& B = blk[it.x];
+  const int c = threadIdx.x / kATPR, kq = threadIdx.x % kATPR;
+  const int64_t j0 = (int64_t)it.y * kAN;
+  const int k0 = it.z * kAK;
+  const int nk = min(kAK, K - k0);
+  const int64_t M3 = 3 * B.m, N3 = 3 * B.n;
+  cx<A> xacc[NT][3];
+  for (int t = 0; t < NT; ++t)
+    for (int a = 0; a < 3; ++a) xacc[t][a] = {A(0), A(0)};
+  for (int p = 0; p < B.rank; ++p) {
+    const int64_t idx = (int64_t)p * nb + it.x;
+    const int fr = frank[idx];
+    if (fr == 0) continue;
+    const S* H = face_tab[idx];
+    const S* f = fib_tab[idx];
+    __syncthreads();
+    for (int e = threadIdx.x; e < kAK * 9; e += blockDim.x) {
+      const int kk = e / 9;
+      sF[e] = kk < nk ? Ld<S, A>::ld(f + (int64_t)(k0 + kk) * 9 + e % 9) : cx<A>{A(0), A(0)};
+    }
+    cx<A> w[NT][3];
+    for (int t = 0; t < NT; ++t)
+      for (int b = 0; b < 3; ++b) w[t][b] = {A(0), A(0)};
+    if (fr < 0) {
+      for (int64_t i0 = 0; i0 < B.m; i0 += kAR) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kAN * kAR * 9; e += blockDim.x) {
+          const int cc = e / (kAR * 9), rem = e % (kAR * 9), ii = rem / 9;
+          const int64_t gi = i0 + ii, gj = j0 + cc;
+          sH[cc * kASH + rem] = (gi < B.m && gj < B.n) ? Ld<S, A>::ld(H + (gi * B.n + gj) * 9 + rem % 9)
+                                                       : cx<A>{A(0), A(0)};
+        }
+        for (int e = threadIdx.x; e < kAR * 3 * kAK; e += blockDim.x) {
+          const int ra = e / kAK, kk = e % kAK;
+          const int64_t gi = i0 + ra / 3;
+          sY[e] = (gi < B.m && kk < nk) ? Ld<S, A>::ld(Yq + ((B.r0 + gi) * K + k0 + kk) * 3 + ra % 3)
+                                        : cx<A>{A(0), A(0)};
+        }
+        __syncthreads();
+        cx<A> part[NT][3];
+        for (int t = 0; t < NT; ++t)
+          for (int b = 0; b < 3; ++b) part[t][b] = {A(0), A(0)};
+        for (int ii = 0; ii < kAR; ++ii)
+          for (int a = 0; a < 3; ++a) {
+            cx<A> h[3];
+            for (int b = 0; b < 3; ++b) h[b] = conj(sH[c * kASH + ii * 9 + 3 * a + b]);
+            for (int t = 0; t < NT; ++t) {
+              const cx<A> y = sY[(ii * 3 + a) * kAK + kq + kATPR * t];
+              for (int b = 0; b < 3; ++b) part[t][b] = cfma(h[b], y, part[t][b]);
+            }
+          }
+        for (int t = 0; t < NT; ++t)
+          for (int b = 0; b < 3; ++b) w[t][b] = w[t][b] + part[t][b];
+      }
+    } else {
+      // low rank: sum_i H[i,j]^H y_i = conj(W')[(j,b), q] T'[q][k]
+      const S* Wp = H + M3 * (int64_t)fr;
+      const cx<A>* Tp = T + toff[idx];
+      for (int q0 = 0; q0 < fr; q0 += kAR * 3) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kAN * kAR * 9; e += blockDim.x) {
+          const int cc = e / (kAR * 9), rem = e % (kAR * 9);
+          const int qq = rem / 3, b = rem % 3;   // rem < 3 kAR x 3: rank qq < 3 kAR
+          const int64_t gj = j0 + cc;
+          const int gq = q0 + qq;
+          sH[cc * kASH + rem] = (gj < B.n && gq < fr && qq < 3 * kAR) ? Ld<S, A>::ld(Wp + (int64_t)gq * N3 + 3 * gj + b)
+                                                                       : cx<A>{A(0), A(0)};
+        }
+        for (int e = threadIdx.x; e < kAR * 3 * kAK; e += blockDim.x) {
+          const int qq = e / kAK, kk = e % kAK;
+          const int gq = q0 + qq;
+          sY[e] = (gq < fr && kk < nk) ? Tp[(int64_t)gq * K + k0 + kk] : cx<A>{A(0), A(0)};
+        }
+        __syncthreads();
+        cx<A> part[NT][3];
+        for (int t = 0; t < NT; ++t)
+          for (int b = 0; b < 3; ++b) part[t][b] = {A(0), A(0)};
+        for (int qq = 0; qq < kAR * 3; ++qq) {
+          cx<A> h[3];
+          for (int b = 0; b < 3; ++b) h[b] = conj(sH[c * kASH + qq * 3 + b]);
+          for (int t = 0; t < NT; ++t) {
+            const cx<A> y = sY[qq * kAK + kq + kATPR * t];
+            for (int b = 0; b < 3; ++b) part[t][b] = cfma(h[b], y, part[t][b]);
+          }
+        }
+        for (int t = 0; t < NT; ++t)
+          for (int b = 0; b < 3; ++b) w[t][b] = w[t][b] + part[t][b];
+      }
+    }
+    // fibre: x[c2] += sum_b conj(f[k][b][c2]) w[b]
+    for (int t = 0; t < NT; ++t) {
+      const cx<A>* fk = sF + (kq + kATPR * t) * 9;
+      for (int c2 = 0; c2 < 3; ++c2)
+        for (int b = 0; b < 3; ++b) xacc[t][c2] = cfma(conj(fk[3 * b + c2]), w[t][b], xacc[t][c2]);
+    }
+  }
+  const int64_t gj = j0 + c;
+  if (gj < B.n)
+    for (int t = 0; t < NT; ++t) {
+      const int kk = kq + kATPR * t;
+      if (kk < nk) {
+        double* x = Xacc + (((B.c0 + gj) * K + k0 + kk) * 3) * 2;
+        for (int a = 0; a < 3; ++a) atomic_add_c<double>(x + 2 * a, cx<double>{(double)xacc[t][a].x, (double)xacc[t][a].y});
+      }
+    }
+}
+
+// adjoint, low-rank faces: T'_p[q][k] = sum_(i,a) conj(U'[(i,a), q]) y_i[k][a]
+// item (block, slot, tile of 32 ranks, frequency tile); thread = (rank, 4 frequencies)
+template <typename S, typename A>
+__global__ void __launch_bounds__(kAN * kATPR) k_apply_lr_t_adj(const BlkDev* __restrict__ blk,
+                                                                const int4* __restrict__ items,
+                                                                S* const* __restrict__ face_tab,
+                                                                const int32_t* __restrict__ frank,
+                                                                const int64_t* __restrict__ toff,
+                                                                cx<A>* __restrict__ T, int64_t nb,
+                                                                const S* __restrict__ Yq, int K) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<A>* sU = reinterpret_cast<cx<A>*>(smem_raw);   // [rank][row chunk x 3]
+  cx<A>* sY = sU + kAN * kASH;
+  constexpr int NT = kAK / kATPR;
+  const int4 it = items[blockIdx.x];
+  const BlkDev& B = blk[it.x];
+  const int64_t idx = (int64_t)it.y * nb + it.x;
+  const int fr = frank[idx];
+  const S* Up = face_tab[idx];
+  const int64_t M3 = 3 * B.m;
+  const int q = threadIdx.x / kATPR, kq = threadIdx.x % kATPR;
+  const int q0 = it.z * kAN;
+  const int k0 = it.w * kAK;
+  const int nk = min(kAK, K - k0);
+  cx<A> acc[NT];
+  for (int t = 0; t < NT; ++t) acc[t] = {A(0), A(0)};
+  for (int64_t i0 = 0; i0 < B.m; i0 += kAR) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kAN * kAR * 3; e += blockDim.x) {
+      const int qq = e / (kAR * 3), ra = e % (kAR * 3);
+      const int gq = q0 + qq;
+      const int64_t r = 3 * i0 + ra;
+      sU[qq * kASH + ra] = (gq < fr && r < M3) ? conj(Ld<S, A>::ld(Up + (int64_t)gq * M3 + r)) : cx<A>{A(0), A(0)};
+    }
+    for (int e = threadIdx.x; e < kAR * 3 * kAK; e += blockDim.x) {
+      const int ra = e / kAK, kk = e % kAK;
+      const int64_t gi = i0 + ra / 3;
+      sY[e] = (gi < B.m && kk < nk) ? Ld<S, A>::ld(Yq + ((B.r0 + gi) * K + k0 + kk) * 3 + ra % 3) : cx<A>{A(0), A(0)};
+    }
+    __syncthreads();
+    cx<A> part[NT];
+    for (int t = 0; t < NT; ++t) part[t] = {A(0), A(0)};
+    for (int ra = 0; ra < kAR * 3; ++ra) {
+      const cx<A> u = sU[q * kASH + ra];
+      for (int t = 0; t < NT; ++t) part[t] = cfma(u, sY[ra * kAK + kq + kATPR * t], part[t]);
+    }
+    for (int t = 0; t < NT; ++t) acc[t] = acc[t] + part[t];
+  }
+  const int gq = q0 + q;
+  if (gq < fr)
+    for (int t = 0; t < NT; ++t) {
+      const int kk = kq + kATPR * t;
+      if (kk < nk) T[toff[idx] + (int64_t)gq * K + k0 + kk] = acc[t];
+    }
+}
+
+// adjoint, dense fallback blocks: x_j[k] += sum_i D_k[i,j]^H y_i[k]; CTA per
+// (block, k), warp per column
+template <typename S, typename A>
+__global__ void k_apply_dense_adj(const BlkDev* __restrict__ blk, const int32_t* __restrict__ list,
+                                  S* const* __restrict__ dense, const S* __restrict__ Yq, double* __restrict__ Xacc,
+                                  int K) {
+  const int b = list[blockIdx.x];
+  const int k = blockIdx.y;
+  const BlkDev& B = blk[b];
+  const S* D = dense[b] + (int64_t)k * B.m * B.n * 9;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t lj = w; lj < B.n; lj += nw) {
+    cx<A> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int64_t li = lane; li < B.m; li += 32) {
+      const S* yp = Yq + ((B.r0 + li) * K + k) * 3;
+      cx<A> y[3];
+      for (int a = 0; a < 3; ++a) y[a] = Ld<S, A>::ld(yp + a);
+      const S* d = D + (li * B.n + lj) * 9;
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) acc[c] = cfma(conj(Ld<S, A>::ld(d + 3 * a + c)), y[a], acc[c]);
+    }
+    for (int c = 0; c < 3; ++c)
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[c].x += __shfl_down_sync(0xffffffffu, acc[c].x, o);
+        acc[c].y += __shfl_down_sync(0xffffffffu, acc[c].y, o);
+      }
+    if (lane == 0) {
+      double* x = Xacc + (((B.c0 + lj) * K + k) * 3) * 2;
+      for (int c = 0; c < 3; ++c) atomic_add_c<double>(x + 2 * c, cx<double>{(double)acc[c].x, (double)acc[c].y});
+    }
+  }
+}
+
+// contracted adjoint input: Yq[pos][k] = y[row(pos)] for every k
+template <typename S>
+__global__ void k_bcast_y(const S* __restrict__ y, S* __restrict__ Yq, const int32_t* __restrict__ perm, int64_t n,
+                          int K) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * K) return;
+  const int64_t pos = t / K;
+  const S* src = y + (int64_t)perm[pos] * 3;
+  S* dst = Yq + t * 3;
+  for (int c = 0; c < 3; ++c) dst[c] = src[c];
+}
+
 // X[k][col][c] -> Xp[pos][k][c] (cluster order), Yp[pos][k][c] -> Y[k][row][c]
 template <typename S>
 __global__ void k_perm_x(const S* __restrict__ X, S* __restrict__ Xp, const int32_t* __restrict__ perm, int64_t n,
@@ -437,7 +670,7 @@ __global__ void k_apply_dense_p(const BlkDev* __restrict__ blk, const int32_t* _
 }
 
 bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
-  std::vector<int4> items, lr_items, lr_faces;
+  std::vector<int4> items, lr_items, lr_faces, adj_items, adj_lr_items;
   std::vector<int32_t> dense, aca;
   std::vector<int64_t> zoff;
   std::vector<int4> zitems;   // (block, face, 128-column chunk, aca index)
@@ -457,6 +690,8 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
           lr_faces.push_back(make_int4((int)b, p, (int)aca.size(), 0));
           for (int q = 0; q * 3 * kBM < fr; ++q)
             for (int kt = 0; kt * kBK < d->K; ++kt) lr_items.push_back(make_int4((int)b, p, q, kt));
+          for (int q = 0; q * kAN < fr; ++q)
+            for (int kt = 0; kt * kAK < d->K; ++kt) adj_lr_items.push_back(make_int4((int)b, p, q, kt));
         }
       }
       aca.push_back((int32_t)b);
@@ -464,6 +699,8 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
       z += (int64_t)B.rank * B.n * 3;
       for (int64_t rt = 0; rt * kBM < B.m; ++rt)
         for (int kt = 0; kt * kBK < d->K; ++kt) items.push_back(make_int4((int)b, (int)rt, kt, 0));
+      for (int64_t ct = 0; ct * kAN < B.n; ++ct)
+        for (int kt = 0; kt * kAK < d->K; ++kt) adj_items.push_back(make_int4((int)b, (int)ct, kt, 0));
     }
   }
   std::vector<void*>* own = &d->allocs;
@@ -487,12 +724,18 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
   GCQ_CUDA(ctx, up((int4**)&d->d_lr_items, lr_items));
   GCQ_CUDA(ctx, up((int4**)&d->d_lr_faces, lr_faces));
   GCQ_CUDA(ctx, up(&d->d_toff, toff));
+  GCQ_CUDA(ctx, up((int4**)&d->d_adj_items, adj_items));
+  GCQ_CUDA(ctx, up((int4**)&d->d_adj_lr_items, adj_lr_items));
+  d->n_adj_items = (int64_t)adj_items.size();
+  d->n_adj_lr_items = (int64_t)adj_lr_items.size();
   d->n_zitems = (int64_t)zitems.size();
   const size_t es = d->prec == BEM_FP64 ? sizeof(double2) : sizeof(float2);
   GCQ_CUDA(ctx, dmalloc(&d->d_xp, es * 3 * (size_t)d->K * d->n_cols, own));
   GCQ_CUDA(ctx, dmalloc(&d->d_yp, sizeof(double2) * 3 * (size_t)d->K * d->n_rows, own));
   GCQ_CUDA(ctx, dmalloc(&d->d_z, es * std::max<int64_t>(1, z), own));
   GCQ_CUDA(ctx, dmalloc(&d->d_t, es * std::max<int64_t>(1, tt), own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_yq, es * 3 * (size_t)d->K * d->n_rows, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_xacc, sizeof(double2) * 3 * (size_t)d->K * d->n_cols, own));
   // algorithmic bytes of one batched apply: stored operator + X + Y
   d->apply_bytes = (int64_t)d->stored_bytes + (int64_t)d->K * (d->n_rows + d->n_cols) * 3 * (int64_t)es;
   return BEM_OK;
@@ -577,7 +820,59 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
   return BEM_OK;
 }
 
-bem_status apply(bem_op* op, int mode, const void* X, void* Y, cudaStream_t st) {
+// conjugate transpose: BATCHED X_k = C_k^H Y_k; CONTRACTED X_k = C_k^H y for
+// every k (the adjoint of y = sum_k C_k X_k).  Yin: K x n_rows x 3 (BATCHED)
+// or n_rows x 3 (CONTRACTED); Xout: K x n_cols x 3.
+template <typename S, typename A>
+static bem_status apply_adj_t(bem_op* op, int mode, const void* Yv, void* Xv, cudaStream_t st) {
+  OpData* d = op->d;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  const S* Yin = (const S*)Yv;
+  S* Xout = (S*)Xv;
+  const int64_t nyq = (int64_t)d->n_rows * d->K, nxa = (int64_t)d->n_cols * d->K;
+  if (mode == BEM_APPLY_BATCHED)
+    k_perm_x<S><<<(unsigned)((nyq + 255) / 256), 256, 0, st>>>(Yin, (S*)d->d_yq, d->d_row_perm, d->n_rows, d->K);
+  else
+    k_bcast_y<S><<<(unsigned)((nyq + 255) / 256), 256, 0, st>>>(Yin, (S*)d->d_yq, d->d_row_perm, d->n_rows, d->K);
+  GCQ_CUDA(ctx, cudaGetLastError());
+  count_launches(1);
+  GCQ_CUDA(ctx, cudaMemsetAsync(d->d_xacc, 0, sizeof(double2) * 3 * nxa, st));
+  if (d->n_adj_lr_items > 0) {
+    const size_t sm = sizeof(cx<A>) * (kAN * kASH + kAR * 3 * kAK);
+    cudaFuncSetAttribute(k_apply_lr_t_adj<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_apply_lr_t_adj<S, A><<<(unsigned)d->n_adj_lr_items, kAN * kATPR, sm, st>>>(
+        d->d_blk, (const int4*)d->d_adj_lr_items, (S* const*)d->d_face, d->d_frank, d->d_toff, (cx<A>*)d->d_t,
+        d->n_blocks, (const S*)d->d_yq, d->K);
+    GCQ_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
+  }
+  if (d->n_adj_items > 0) {
+    const size_t sm = sizeof(cx<A>) * (kAN * kASH + kAR * 3 * kAK + kAK * 9);
+    cudaFuncSetAttribute(k_apply_faces_adj<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_apply_faces_adj<S, A><<<(unsigned)d->n_adj_items, kAN * kATPR, sm, st>>>(
+        d->d_blk, (const int4*)d->d_adj_items, (S* const*)d->d_face, (S* const*)d->d_fib, d->d_frank, d->d_toff,
+        (const cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_yq, (double*)d->d_xacc, d->K);
+    GCQ_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
+  }
+  if (d->n_dense > 0) {
+    dim3 g((unsigned)d->n_dense, (unsigned)d->K);
+    k_apply_dense_adj<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense,
+                                               (const S*)d->d_yq, (double*)d->d_xacc, d->K);
+    GCQ_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
+  }
+  k_unperm_y<S><<<(unsigned)((nxa + 255) / 256), 256, 0, st>>>((const double2*)d->d_xacc, Xout, d->d_col_perm,
+                                                               d->n_cols, d->K);
+  GCQ_CUDA(ctx, cudaGetLastError());
+  count_launches(1);
+  return BEM_OK;
+}
+
+bem_status apply(bem_op* op, int mode, int transpose, const void* X, void* Y, cudaStream_t st) {
+  if (transpose)
+    return op->d->prec == BEM_FP64 ? apply_adj_t<double2, double>(op, mode, X, Y, st)
+                                   : apply_adj_t<float2, float>(op, mode, X, Y, st);
   return op->d->prec == BEM_FP64 ? apply_t<double2, double>(op, mode, X, Y, st)
                                  : apply_t<float2, float>(op, mode, X, Y, st);
 }

@@ -742,12 +742,12 @@ void bem_op_destroy(bem_op* op) {
 bem_status bem_op_apply(bem_op* op, int32_t mode, int32_t transpose, const void* X, void* Y, void* stream) {
   if (!op) return BEM_ERR_ARG;
   bem_ctx* ctx = op->tree->mesh->ctx;
-  if ((mode != BEM_APPLY_BATCHED && mode != BEM_APPLY_CONTRACTED) || transpose != 0 || !X || !Y)
+  if ((mode != BEM_APPLY_BATCHED && mode != BEM_APPLY_CONTRACTED) || (transpose != 0 && transpose != 1) || !X || !Y)
     return set_err(ctx, BEM_ERR_ARG, "bem_op_apply: bad arguments");
   if (((uintptr_t)X & 15) || ((uintptr_t)Y & 15))
     return set_err(ctx, BEM_ERR_ARG, "bem_op_apply: X and Y must be 16-byte aligned");
   GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
-  return apply(op, mode, X, Y, (cudaStream_t)stream);
+  return apply(op, mode, transpose, X, Y, (cudaStream_t)stream);
 }
 
 bem_status bem_op_dense(bem_op* op, void* out, void* stream) {

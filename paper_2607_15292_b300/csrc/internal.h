@@ -146,7 +146,7 @@ bem_status launch_entries(bem_mesh* mesh, int rows, int kernel, const int32_t* r
                           void* out, int* d_flag, cudaStream_t st);
 bem_status compress(bem_tree* tree, cudaStream_t st, OpData** out);
 void free_op(OpData* d);
-bem_status apply(bem_op* op, int mode, const void* X, void* Y, cudaStream_t st);
+bem_status apply(bem_op* op, int mode, int transpose, const void* X, void* Y, cudaStream_t st);
 bem_status op_dense(bem_op* op, void* out, cudaStream_t st);
 bem_status op_stats(const bem_op* op, bem_op_stats* st);
 bem_status op_blocks(const bem_op* op, int64_t* info);

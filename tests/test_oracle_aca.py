@@ -111,3 +111,25 @@ def test_compressed_apply_matches_dense():
         cover[np.ix_(b.rows, b.cols)] += 1
     assert (cover == 1).all()
     assert any(b.far for b in blocks)
+
+
+def test_adjoint_apply_pins():
+    """Conjugate-transpose apply: against the conjugate transpose of the
+    explicit 3M x 3N matrix of each frequency (numpy) and by the inner-product
+    identity <C x, y> = <x, C^H y> with the forward apply."""
+    xyz, tri = syn.cube_grid(1)
+    s = bem.freqs_bdf2(16, 1e-4, 4)
+    op = bem.Operator(xyz, tri, syn.STEEL, rows=bem.ROWS_NODES, kernel=bem.KERNEL_DL)
+    D = op.dense(s)
+    M, N, K = D.shape[:3]
+    X = syn.complex_normal(2, (N, 3, K))
+    Y = syn.complex_normal(3, (M, 3, K))
+    XA = aca.apply_adjoint_dense(D, Y)
+    assert XA.shape == (N, 3, K)
+    for k in range(K):
+        A = bem.to_matrix(D[:, :, k])                     # (3M, 3N)
+        ref = A.conj().T @ Y[:, :, k].reshape(-1)
+        assert np.allclose(XA[:, :, k].reshape(-1), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+    lhs = np.vdot(Y, aca.apply_dense(D, X))               # <y, C x>
+    rhs = np.vdot(XA, X)                                  # <C^H y, x>
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
