@@ -119,3 +119,51 @@ def test_adjoint_inner_product_identity(name, precision):
     rhs = torch.vdot(CHY.flatten().to(torch.complex128), X.flatten().to(torch.complex128)).item()
     scale = (torch.linalg.norm(y.to(torch.complex128)) * torch.linalg.norm(cx.to(torch.complex128))).item()
     assert abs(lhs - rhs) <= tol * scale * np.sqrt(K)
+
+
+def test_autograd_function_gradcheck_fp64():
+    """torch.autograd.gradcheck of the differentiable apply (FP64, small
+    operator): the backward is the exact vector-Jacobian product."""
+    from paper_2607_15292_b300 import autograd as ga
+    xyz, tri = syn.cube_grid(1)
+    s = bem.freqs_bdf2(8, 1e-4, 2)
+    ctx = g.Context(eps=EPS, precision=0, leaf=4)
+    ctx.material(*syn.STEEL)
+    ctx.freqs(s)
+    op = ctx.mesh(xyz, tri).tree(g.BEM_ROWS_NODES, g.BEM_SL).compress()
+    X = torch.tensor(syn.complex_normal(1, (len(s), len(tri), 3)), dtype=torch.complex128, device="cuda",
+                     requires_grad=True)
+    for mode in (g.BEM_APPLY_BATCHED, g.BEM_APPLY_CONTRACTED):
+        assert torch.autograd.gradcheck(lambda x: ga.apply(op, x, mode), (X,), eps=1e-6, atol=1e-9, rtol=1e-6)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_receiver_energy_gradient_matches_oracle(precision):
+    """Gradient of a receiver energy L = sum_k sum_{i in R} |(C_k x_k)_i|^2
+    with respect to the traction loads x (single layer, node rows): autograd
+    through the compressed operator against C^H of the oracle's dense tensor
+    applied to the receiver residual (same convention, dL/dx*)."""
+    from paper_2607_15292_b300 import autograd as ga
+    s = bem.freqs_bdf2(16, 1e-4, 16)
+    K = len(s)
+    xyz, tri = syn.icosphere(2)
+    opo = bem.Operator(xyz, tri, syn.STEEL, rows="nodes", kernel="sl")
+    D = opo.dense(s)                                         # (M, N, K, 3, 3)
+    ctx = g.Context(eps=EPS, precision=precision, leaf=16)
+    ctx.material(*syn.STEEL)
+    ctx.freqs(s)
+    op = ctx.mesh(xyz, tri).tree(g.BEM_ROWS_NODES, g.BEM_SL).compress()
+    rec = np.sort(np.random.default_rng(4).choice(len(xyz), 16, replace=False))
+    cdt = torch.complex128 if precision == 0 else torch.complex64
+    x0 = syn.complex_normal(2, (K, len(tri), 3))
+    X = torch.tensor(x0, dtype=cdt, device="cuda", requires_grad=True)
+    Y = ga.apply(op, X)
+    L = (Y[:, torch.tensor(rec, device="cuda")].abs() ** 2).sum()
+    L.backward()
+    # the same loss on the oracle's output, differentiated by autograd with respect to Y only
+    Yo = torch.tensor(np.einsum("ijkab,kjb->kia", D, x0), dtype=torch.complex128, requires_grad=True)
+    (Yo[:, torch.tensor(rec)].abs() ** 2).sum().backward()
+    gY = Yo.grad.numpy()                                     # (K, M, 3)
+    gX = aca.apply_adjoint_dense(D, gY.transpose(1, 2, 0)).transpose(2, 0, 1)
+    got = X.grad.cpu().numpy().astype(np.complex128)
+    assert _rel(got, gX) < 10 * EPS * (1 if precision == 0 else 2)
