@@ -57,6 +57,7 @@ struct OpData {
   int32_t* d_ks = nullptr;     // [n_blocks][K] pivot frequencies
   uint8_t* d_used = nullptr;   // [n_blocks][K]
   double2* d_M = nullptr;      // [n_blocks][K][9] Gram of the current face
+  double* d_hn2 = nullptr;     // [n_blocks][K] ||H_p||_F^2 of every accepted face
   int64_t entries = 0;
   double t_entries_ms = 0, t_compress_ms = 0;
   int64_t apply_bytes = 0;
@@ -289,15 +290,16 @@ struct WorkOf<float4> {
 };
 
 template <typename R, typename S, int KERN, int ROWS>
-__global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restrict__ tiles,
+__global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 : 1) k_face(EntryView v, const Tile* __restrict__ tiles,
                                                 BlkDev* __restrict__ blk, S* const* __restrict__ face_tab,
                                                 S* const* __restrict__ fib_tab, int64_t nb, int slot,
                                                 const int32_t* __restrict__ row_perm,
                                                 const int32_t* __restrict__ col_perm, double* __restrict__ p_s3,
                                                 int64_t* __restrict__ p_idx, double* __restrict__ p_h2,
-                                                double2* __restrict__ p_M, int K) {
+                                                double2* __restrict__ p_M, const double* __restrict__ hn2, int K) {
   using W = typename WorkOf<S>::W;
   __shared__ S sf[64 * 9];     // f_p[k_d] for p < slot, in chunks of 64
+  __shared__ unsigned char ssmall[64];   // term p below 2^-10 of the first: plain FMA (MIXED)
   __shared__ double shv[32 * 18];
   __shared__ int64_t shi[32];
   const Tile t = tiles[blockIdx.x];
@@ -341,7 +343,24 @@ __global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restr
     for (int c = 0; c < 9; ++c) Hd64[c] = {0, 0};
     if (ok) entry<R, KERN, ROWS>(v, i, j, kd, s, is2, Hd64);
   }
-  // residual: H = E - sum_p H_p[i,j] f_p[k_d]
+  // residual: H = E - sum_p H_p[i,j] f_p[k_d].  MIXED: the terms whose
+  // ||H_p|| ||f_p[k_d]|| is below 2^-10 of the first term's take plain FMA
+  // (their FP32 rounding stays below 2^-34 of the face), the others
+  // error-free products in float-float
+  float fs[18];                   // sum of the small terms (MIXED)
+  for (int c = 0; c < 18; ++c) fs[c] = 0.f;
+  double ref = 0.0;
+  if constexpr (FF) {
+    if (slot > 0) {
+      const S* f0 = fib_tab[t.blk] + (int64_t)kd * 9;
+      double q = 0.0;
+      for (int c = 0; c < 9; ++c) {
+        const float4 y = reinterpret_cast<const float4*>(f0)[c];
+        q += (double)y.x * y.x + (double)y.y * y.y;
+      }
+      ref = hn2[(int64_t)t.blk * K] * q;
+    }
+  }
   for (int p0 = 0; p0 < slot; p0 += 64) {
     const int np = min(64, slot - p0);
     __syncthreads();
@@ -350,6 +369,18 @@ __global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restr
       sf[c] = fib_tab[(int64_t)p * nb + t.blk][(int64_t)kd * 9 + c % 9];
     }
     __syncthreads();
+    if constexpr (FF) {
+      if (threadIdx.x < np) {
+        const int p = p0 + threadIdx.x;
+        double q = 0.0;
+        for (int c = 0; c < 9; ++c) {
+          const float4 y = reinterpret_cast<const float4*>(sf)[9 * threadIdx.x + c];
+          q += (double)y.x * y.x + (double)y.y * y.y;
+        }
+        ssmall[threadIdx.x] = p > 0 && hn2[(int64_t)t.blk * K + p] * q <= 9.5367431640625e-7 * ref;   // 2^-20
+      }
+      __syncthreads();
+    }
     if (ok) {
       S nxt[9];
       {
@@ -365,6 +396,22 @@ __global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restr
         }
         const S* f = sf + 9 * p;
         if constexpr (FF) {
+          if (ssmall[p]) {
+            for (int a = 0; a < 3; ++a)
+              for (int c = 0; c < 3; ++c) {
+                const float4 x = reinterpret_cast<const float4*>(cur)[3 * a + c];
+                for (int b = 0; b < 3; ++b) {
+                  const float4 y = reinterpret_cast<const float4*>(f)[3 * c + b];
+                  float& sr = fs[2 * (3 * a + b)];
+                  float& si = fs[2 * (3 * a + b) + 1];
+                  sr = fmaf(x.x, y.x, sr);
+                  sr = fmaf(-x.y, y.y, sr);
+                  si = fmaf(x.x, y.y, si);
+                  si = fmaf(x.y, y.x, si);
+                }
+              }
+            continue;
+          }
           for (int a = 0; a < 3; ++a)
             for (int c = 0; c < 3; ++c) {
               const float4 x = reinterpret_cast<const float4*>(cur)[3 * a + c];
@@ -402,7 +449,9 @@ __global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restr
   if (ok) {
     for (int c = 0; c < 9; ++c) {
       if constexpr (FF) {
-        // renormalise (h, l) and store
+        // fold in the small terms, renormalise (h, l) and store
+        fl[2 * c] -= fs[2 * c];
+        fl[2 * c + 1] -= fs[2 * c + 1];
         float rh = fh[2 * c] + fl[2 * c];
         float rl = fl[2 * c] - (rh - fh[2 * c]);
         float ih = fh[2 * c + 1] + fl[2 * c + 1];
@@ -487,7 +536,7 @@ __global__ void __launch_bounds__(kTile) k_face(EntryView v, const Tile* __restr
 __global__ void k_block_red(BlkDev* __restrict__ blk, const int32_t* __restrict__ active, int slot,
                             const double* __restrict__ p_s3, const int64_t* __restrict__ p_idx,
                             const double* __restrict__ p_h2, const double2* __restrict__ p_M,
-                            double2* __restrict__ M, int K) {
+                            double2* __restrict__ M, double* __restrict__ hn2, int K) {
   __shared__ double shv[32 * 18];
   __shared__ int64_t shi[32];
   const int b = active[blockIdx.x];
@@ -513,6 +562,7 @@ __global__ void k_block_red(BlkDev* __restrict__ blk, const int32_t* __restrict_
     B.s3max = s3;
     B.piv = idx;
     B.h2 = h2;
+    hn2[(int64_t)b * K + slot] = h2;
   }
   // Gram blocks: thread per (face p, real component), fixed tile order
   const double* pm = reinterpret_cast<const double*>(p_M);
@@ -999,6 +1049,7 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   GCQ_CUDA(ctx, dmalloc(&d->d_ks, sizeof(int32_t) * nb * K, own));
   GCQ_CUDA(ctx, dmalloc(&d->d_used, nb * K, own));
   GCQ_CUDA(ctx, dmalloc(&d->d_M, sizeof(double2) * nb * K * 9, own));
+  GCQ_CUDA(ctx, dmalloc(&d->d_hn2, sizeof(double) * nb * K, own));
   GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_blk, d->h_blk.data(), sizeof(BlkDev) * nb, cudaMemcpyHostToDevice, st));
   GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_row_perm, tree->row_perm.data(), sizeof(int32_t) * tree->n_rows,
                                 cudaMemcpyHostToDevice, st));
@@ -1077,7 +1128,7 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
     GCQ_DISPATCH(d->kernel, d->rows,
                  (k_face<R, SC, KK, RR><<<(unsigned)tiles.size(), kTile, 0, st>>>(
                      v, d_tiles, d->d_blk, (S* const*)d->d_face, (S* const*)d->d_fib, nb, slot, d->d_row_perm,
-                     d->d_col_perm, p_s3, p_idx, p_h2, p_M, K)));
+                     d->d_col_perm, p_s3, p_idx, p_h2, p_M, d->d_hn2, K)));
     GCQ_CUDA(ctx, cudaGetLastError());
     cudaEventRecord(evf, st);
     d->face_launches++;
@@ -1086,7 +1137,7 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
     for (int32_t b : active)
       d->face_alg_bytes += (double)(slot + 1) * sizeof(SC) * 9.0 * (double)(d->h_blk[b].m * d->h_blk[b].n);
     k_block_red<<<(unsigned)active.size(), 256, 0, st>>>(d->d_blk, d_active, slot, p_s3, p_idx, p_h2, p_M, d->d_M,
-                                                         K);
+                                                         d->d_hn2, K);
     GCQ_CUDA(ctx, cudaGetLastError());
     const int tb = std::max(32, ((K + 31) / 32) * 32);
     const size_t fsm = sizeof(double2) * 9 * (size_t)K;
