@@ -586,7 +586,12 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
   __shared__ double shv[32 * 18];
   __shared__ int64_t shi[32];
   __shared__ int decision;
-  __shared__ cx<double> sP[9];
+  __shared__ cx<double> sP[9], sPi[9];
+  __shared__ int s_inv;
+  // MIXED (float-float storage): residual with error-free FP32 products,
+  // fibre Gram and next-frequency sigma_3 in FP32 (the FP64 pipe of the
+  // B300 is ~1/64 of FP32); FP64 mode unchanged
+  constexpr bool FF = std::is_same<S, float4>::value;
   const int b = active[blockIdx.x];
   BlkDev& B = blk[b];
   if (threadIdx.x == 0) {
@@ -608,8 +613,15 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
   const S* Hd = face_tab[(int64_t)slot * nb + b];
   if (threadIdx.x < 9) sP[threadIdx.x] = St<S>::ld(Hd + B.piv * 9 + threadIdx.x);
   __syncthreads();
+  if (threadIdx.x == 0) {
+    cx<double> P0[9];
+    s_inv = inv3(sP, P0);
+    for (int c = 0; c < 9; ++c) sPi[c] = P0[c];
+  }
+  __syncthreads();
   cx<double> Pi[9];
-  bool inv_ok = inv3(sP, Pi);
+  for (int c = 0; c < 9; ++c) Pi[c] = sPi[c];
+  const bool inv_ok = s_inv != 0;
   const int k = threadIdx.x;
   const bool ok = k < K;
   cx<double> f[9];
@@ -639,16 +651,50 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
       cx<double> s = freq(v, k, is2);
       entry<R, KERN, ROWS>(v, i, j, k, s, is2, E);
     }
-    for (int p = 0; p < slot; ++p) {
-      const S* Hp = face_tab[(int64_t)p * nb + b] + B.piv * 9;
-      const S* fp = fib_tab[(int64_t)p * nb + b] + (int64_t)k * 9;
-      cx<double> hp[9], ff[9], t9[9];
+    if constexpr (FF) {
+      // E is an FP32 entry: exact as the high part of a float-float value
+      float rh[18], rl[18];
       for (int c = 0; c < 9; ++c) {
-        hp[c] = St<S>::ld(Hp + c);
-        ff[c] = St<S>::ld(fp + c);
+        rh[2 * c] = (float)E[c].x;
+        rh[2 * c + 1] = (float)E[c].y;
+        rl[2 * c] = 0.f;
+        rl[2 * c + 1] = 0.f;
       }
-      mm3(hp, ff, t9);
-      for (int c = 0; c < 9; ++c) E[c] = E[c] - t9[c];
+      for (int p = 0; p < slot; ++p) {
+        const float4* Hp = reinterpret_cast<const float4*>(face_tab[(int64_t)p * nb + b] + B.piv * 9);
+        const float4* fp = reinterpret_cast<const float4*>(fib_tab[(int64_t)p * nb + b] + (int64_t)k * 9);
+        float4 hp[9], fq[9];
+        for (int c = 0; c < 9; ++c) {
+          hp[c] = Hp[c];
+          fq[c] = fp[c];
+        }
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) {
+            const float4 x = hp[3 * a + c];
+            for (int bb = 0; bb < 3; ++bb) {
+              const float4 y = fq[3 * c + bb];
+              const int o = 2 * (3 * a + bb);
+              ff_sub_prod(rh[o], rl[o], x.x, x.z, y.x, y.z);
+              ff_sub_prod(rh[o], rl[o], -x.y, -x.w, y.y, y.w);
+              ff_sub_prod(rh[o + 1], rl[o + 1], x.x, x.z, y.y, y.w);
+              ff_sub_prod(rh[o + 1], rl[o + 1], x.y, x.w, y.x, y.z);
+            }
+          }
+      }
+      for (int c = 0; c < 9; ++c)
+        E[c] = {(double)rh[2 * c] + (double)rl[2 * c], (double)rh[2 * c + 1] + (double)rl[2 * c + 1]};
+    } else {
+      for (int p = 0; p < slot; ++p) {
+        const S* Hp = face_tab[(int64_t)p * nb + b] + B.piv * 9;
+        const S* fp = fib_tab[(int64_t)p * nb + b] + (int64_t)k * 9;
+        cx<double> hp[9], ff[9], t9[9];
+        for (int c = 0; c < 9; ++c) {
+          hp[c] = St<S>::ld(Hp + c);
+          ff[c] = St<S>::ld(fp + c);
+        }
+        mm3(hp, ff, t9);
+        for (int c = 0; c < 9; ++c) E[c] = E[c] - t9[c];
+      }
     }
     mm3(Pi, E, f);
     for (int c = 0; c < 9; ++c) St<S>::st(fd + (int64_t)k * 9 + c, f[c]);
@@ -668,11 +714,22 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
     const int p = q / 9, a = (q % 9) / 3, c2 = q % 3;
     const S* fp = fib_tab[(int64_t)p * nb + b];
     cx<double> acc = {0, 0};
-    for (int kk = 0; kk < K; ++kk)
-      for (int c = 0; c < 3; ++c) {
-        const double2 x = sfd[(int64_t)kk * 9 + 3 * a + c];
-        acc = cfma(cx<double>{x.x, x.y}, conj(St<S>::ld(fp + (int64_t)kk * 9 + 3 * c2 + c)), acc);
-      }
+    if constexpr (FF) {
+      cx<float> af = {0.f, 0.f};
+      for (int kk = 0; kk < K; ++kk)
+        for (int c = 0; c < 3; ++c) {
+          const double2 x = sfd[(int64_t)kk * 9 + 3 * a + c];
+          const float4 y = reinterpret_cast<const float4*>(fp)[(int64_t)kk * 9 + 3 * c2 + c];
+          af = cfma(cx<float>{(float)x.x, (float)x.y}, cx<float>{y.x, -y.y}, af);
+        }
+      acc = {(double)af.x, (double)af.y};
+    } else {
+      for (int kk = 0; kk < K; ++kk)
+        for (int c = 0; c < 3; ++c) {
+          const double2 x = sfd[(int64_t)kk * 9 + 3 * a + c];
+          acc = cfma(cx<double>{x.x, x.y}, conj(St<S>::ld(fp + (int64_t)kk * 9 + 3 * c2 + c)), acc);
+        }
+    }
     // contribution of N_dp[a][c2] to tr(M_pd N_dp) = sum M_pd[c2][a] N_dp[a][c2]
     const double2 m = M[((int64_t)b * K + p) * 9 + 3 * c2 + a];
     const double tr = m.x * acc.x - m.y * acc.y;
@@ -709,7 +766,13 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
   double s3 = -1.0;
   int64_t idx = INT64_MAX;
   if (ok && !used[(int64_t)b * K + k]) {
-    s3 = sigma3<double>(f);
+    if constexpr (FF) {
+      cx<float> f32[9];
+      for (int c = 0; c < 9; ++c) f32[c] = {(float)f[c].x, (float)f[c].y};
+      s3 = (double)sigma3<float>(f32);
+    } else {
+      s3 = sigma3<double>(f);
+    }
     idx = k;
   }
   block_argmax(s3, idx, shv, shi);
