@@ -137,6 +137,30 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# small case for profiler captures (not a bench line)
+# ---------------------------------------------------------------------------
+
+def run_small():
+    import torch
+    import paper_2607_15292_b300 as g
+    xyz, tri = syn.icosphere(3)
+    s = g.freqs_bdf2(WORKLOAD["N"], WORKLOAD["dt"], WORKLOAD["K"])
+    ctx = g.Context(eps=WORKLOAD["eps"], leaf=WORKLOAD["leaf"], eta=WORKLOAD["eta"], precision=g.BEM_MIXED)
+    ctx.material(*syn.STEEL)
+    ctx.freqs(s)
+    t = ctx.mesh(xyz, tri).tree(g.BEM_ROWS_NODES, g.BEM_SL)
+    op = t.compress()
+    X = torch.tensor(syn.complex_normal(1, (len(s), t.n_cols, 3)), dtype=torch.complex64, device="cuda")
+    Y = torch.empty((len(s), t.n_rows, 3), dtype=torch.complex64, device="cuda")
+    op.apply(X, Y)
+    torch.cuda.synchronize()
+    st = op.stats()
+    print(json.dumps({"case": "icosphere-3 single layer, node rows, K=64, MIXED", "face_launches": st.face_launches,
+                      "face_alg_bytes": st.face_alg_bytes, "t_face_ms": st.t_face_ms,
+                      "t_compress_ms": st.t_compress_ms, "apply_bytes": st.apply_bytes}))
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -148,9 +172,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="one MIXED compression and batched apply of the icosphere-3 single layer "
+                         "(1,280 triangles, K = 64), for profiler captures; prints its statistics")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.small:
+        return run_small()
 
     import torch
     import paper_2607_15292_b300 as g
