@@ -202,6 +202,22 @@ void bem_op_destroy(bem_op* op);
 bem_status bem_op_apply(bem_op* op, int32_t mode, int32_t transpose,
                         const void* X, void* Y, void* stream);
 
+/* Solves C(s_k) x_k = b_k for every frequency k (square operators only:
+ * rows and columns on the same points, e.g. the double layer C + K with node
+ * rows, or the single layer with centroid rows) by BiCGstab without
+ * preconditioner, the solver of the paper's examples (Sec. 5); the K
+ * systems advance together, two batched applies per iteration.
+ * B, X: device K x n x 3 complex (c128 FP64, c64 MIXED), B read only, X
+ * overwritten (initial guess 0); tol: relative residual ||b_k - C x_k|| /
+ * ||b_k|| to reach for every k (the recursive residual of BiCGstab);
+ * max_iter >= 1 iterations.  iters, relres: host arrays of K: iterations used
+ * and final relative residual per frequency.  Allocates 6 K n 3 complex of
+ * device scratch per call and synchronises the stream every iteration.
+ * BEM_ERR_NOT_CONVERGED when a frequency ends above tol (breakdown or
+ * max_iter); X then holds the last iterate. */
+bem_status bem_op_solve(bem_op* op, const void* B, void* X, double tol, int32_t max_iter,
+                        int32_t* iters, double* relres, void* stream);
+
 /* Dense reconstruction of the compressed tensor (for checks on small
  * meshes): out device n_rows x n_cols x K 3x3 complex blocks, original
  * (not cluster) ordering.  Synchronises the stream. */

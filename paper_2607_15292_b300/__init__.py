@@ -80,6 +80,7 @@ _SIGS = {
     "bem_op_stats_get": (_i32, [_vp, _P(bem_op_stats)]),
     "bem_op_blocks": (_i32, [_vp, _P(_i64)]),
     "bem_op_face_ranks": (_i32, [_vp, _P(_i32)]),
+    "bem_op_solve": (_i32, [_vp, _vp, _vp, _dbl, _i32, _P(_i32), _P(_dbl), _vp]),
     "bem_face_compress": (_i32, [_vp, _vp, _i64, _i64, _dbl, _P(_i32), _vp, _vp]),
     "bem_kernel_launches": (_i64, []),
     "bem_cq_forward": (_i32, [_i32, _i64, _vp, _vp, _vp]),
@@ -311,6 +312,18 @@ class Operator:
         """transpose = 0: Y = C X; transpose = 1: Y = C^H X (X is then the
         row-side input, Y the column-side output)."""
         _check(_lib.bem_op_apply(self._p, mode, transpose, _dptr(X), _dptr(Y), _stream_ptr(stream)), self.ctx.ptr)
+
+    def solve(self, B, X, tol: float = 1e-8, max_iter: int = 200, stream=None, check: bool = True):
+        """X_k = C(s_k)^{-1} B_k for all k (BiCGstab); returns (iterations,
+        relative residuals) per frequency.  With check=False a frequency that
+        did not converge is not an error (the residuals tell)."""
+        it = np.zeros(self.K, dtype=np.int32)
+        rr = np.zeros(self.K, dtype=np.float64)
+        st = _lib.bem_op_solve(self._p, _dptr(B), _dptr(X), float(tol), int(max_iter),
+                               it.ctypes.data_as(_P(_i32)), rr.ctypes.data_as(_P(_dbl)), _stream_ptr(stream))
+        if check or st != BEM_ERR_NOT_CONVERGED:
+            _check(st, self.ctx.ptr)
+        return it, rr
 
     def apply_adjoint(self, Yin, Xout, mode: int = BEM_APPLY_BATCHED, stream=None):
         self.apply(Yin, Xout, mode, stream, transpose=1)

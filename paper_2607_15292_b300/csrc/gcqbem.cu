@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <atomic>
@@ -360,5 +361,6 @@ namespace gcq {}  // aca3d.cuh and apply.cuh reopen the namespace
 
 #include "aca3d.cuh"
 #include "apply.cuh"
+#include "solve.cuh"
 
 extern "C" int64_t bem_kernel_launches(void) { return gcq::g_launches.load(); }

@@ -776,6 +776,20 @@ bem_status bem_face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, 
   return face_compress(ctx, H, m, n, eps_face, rank, out, (cudaStream_t)stream);
 }
 
+bem_status bem_op_solve(bem_op* op, const void* B, void* X, double tol, int32_t max_iter, int32_t* iters,
+                        double* relres, void* stream) {
+  if (!op) return BEM_ERR_ARG;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  if (!B || !X || !iters || !relres || !(tol > 0 && tol < 1) || max_iter < 1 || B == X)
+    return set_err(ctx, BEM_ERR_ARG, "bem_op_solve: bad arguments");
+  if (op->tree->n_rows != op->tree->n_cols)
+    return set_err(ctx, BEM_ERR_ARG, "bem_op_solve: the operator is not square (rows != columns)");
+  if (((uintptr_t)B & 15) || ((uintptr_t)X & 15))
+    return set_err(ctx, BEM_ERR_ARG, "bem_op_solve: B and X must be 16-byte aligned");
+  GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
+  return solve(op, B, X, tol, max_iter, iters, relres, (cudaStream_t)stream);
+}
+
 bem_status bem_op_face_ranks(const bem_op* op, int32_t* ranks) {
   if (!op || !ranks) return BEM_ERR_ARG;
   return op_face_ranks(op, ranks);

@@ -1,0 +1,199 @@
+// K independent linear systems, one per frequency: C(s_k) x_k = b_k, solved
+// together by BiCGstab without preconditioner (the solver of Sec. 5) on the
+// batched apply of the compressed operator.  Every iteration applies C to
+// all K vectors at once (two batched applies), forms the per-frequency inner
+// products on the device (FP64 sums), and advances each frequency with its
+// own scalars; a frequency that has converged keeps its solution (its
+// coefficients are set so that x and r no longer change).
+#pragma once
+
+namespace gcq {
+
+// out[k] += sum_e conj(a[k][e]) b[k][e] over the n complex values of vector k
+template <typename S>
+__global__ void k_bdot(const S* __restrict__ a, const S* __restrict__ b, int64_t n, double2* __restrict__ out) {
+  const int k = blockIdx.y;
+  const S* ak = a + (int64_t)k * n;
+  const S* bk = b + (int64_t)k * n;
+  double re = 0.0, im = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const cx<double> x = St<S>::ld(ak + e), y = St<S>::ld(bk + e);
+    re += x.x * y.x + x.y * y.y;
+    im += x.x * y.y - x.y * y.x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+  }
+  __shared__ double sr[32], si[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    sr[w] = re;
+    si[w] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, ti = 0.0;
+    for (int q = 0; q < nw; ++q) {
+      tr += sr[q];
+      ti += si[q];
+    }
+    atomicAdd(&out[k].x, tr);
+    atomicAdd(&out[k].y, ti);
+  }
+}
+
+// y[k] = c[k][0] u[k] + c[k][1] v[k] + c[k][2] w[k] (elementwise; y may alias u, v or w)
+template <typename S>
+__global__ void k_lin3(S* y, const S* u, const S* v, const S* w, const double2* __restrict__ c, int64_t n) {
+  const int k = blockIdx.y;
+  const cx<double> c0 = {c[3 * k].x, c[3 * k].y}, c1 = {c[3 * k + 1].x, c[3 * k + 1].y},
+                   c2 = {c[3 * k + 2].x, c[3 * k + 2].y};
+  const int64_t o = (int64_t)k * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const cx<double> r = c0 * St<S>::ld(u + o + e) + c1 * St<S>::ld(v + o + e) + c2 * St<S>::ld(w + o + e);
+    St<S>::st(y + o + e, r);
+  }
+}
+
+template <typename S>
+static bem_status solve_t(bem_op* op, const void* Bv, void* Xv, double tol, int max_iter, int32_t* iters,
+                          double* relres, cudaStream_t st) {
+  OpData* d = op->d;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  const int K = d->K;
+  const int64_t n = 3 * d->n_rows;   // complex values per frequency
+  const size_t vb = sizeof(S) * (size_t)n * K;
+  S* buf = nullptr;
+  double2* dots = nullptr;
+  double2* coef = nullptr;
+  GCQ_CUDA(ctx, cudaMalloc(&buf, 6 * vb));
+  if (cudaMalloc(&dots, sizeof(double2) * K) != cudaSuccess || cudaMalloc(&coef, sizeof(double2) * 3 * K) != cudaSuccess) {
+    cudaFree(buf);
+    cudaFree(dots);
+    return set_err(ctx, BEM_ERR_OOM, "bem_op_solve: out of device memory");
+  }
+  S* x = (S*)Xv;
+  const S* b = (const S*)Bv;
+  S *r = buf, *rh = buf + n * K, *p = buf + 2 * n * K, *v = buf + 3 * n * K, *s = buf + 4 * n * K,
+    *t = buf + 5 * n * K;
+  const dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)K);
+  std::vector<double2> hd(K), hc(3 * K);
+  using C = std::complex<double>;
+  std::vector<C> rho(K, 1.0), alpha(K, 1.0), omega(K, 1.0), rho_new(K);
+  std::vector<double> bn(K);
+  std::vector<int> done(K, 0);
+  cudaError_t e = cudaSuccess;
+  bem_status res = BEM_OK;
+  auto dot = [&](const S* a, const S* c) -> cudaError_t {
+    cudaError_t q = cudaMemsetAsync(dots, 0, sizeof(double2) * K, st);
+    if (q != cudaSuccess) return q;
+    k_bdot<S><<<grid, 256, 0, st>>>(a, c, n, dots);
+    count_launches(1);
+    if ((q = cudaGetLastError()) != cudaSuccess) return q;
+    q = cudaMemcpyAsync(hd.data(), dots, sizeof(double2) * K, cudaMemcpyDeviceToHost, st);
+    if (q != cudaSuccess) return q;
+    return cudaStreamSynchronize(st);
+  };
+  auto lin3 = [&](S* y, const S* u, const S* vv, const S* w) -> cudaError_t {
+    cudaError_t q = cudaMemcpyAsync(coef, hc.data(), sizeof(double2) * 3 * K, cudaMemcpyHostToDevice, st);
+    if (q != cudaSuccess) return q;
+    k_lin3<S><<<grid, 256, 0, st>>>(y, u, vv, w, coef, n);
+    count_launches(1);
+    return cudaGetLastError();
+  };
+  auto setc = [&](int k, C a0, C a1, C a2) {
+    hc[3 * k] = make_double2(a0.real(), a0.imag());
+    hc[3 * k + 1] = make_double2(a1.real(), a1.imag());
+    hc[3 * k + 2] = make_double2(a2.real(), a2.imag());
+  };
+  const C one = 1.0, zero = 0.0;
+  // x = 0, r = rh = b, p = v = 0
+  e = cudaMemsetAsync(x, 0, vb, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rh, b, vb, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, 2 * vb, st);
+  if (e == cudaSuccess) e = dot(b, b);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    bn[k] = std::sqrt(std::max(hd[k].x, 0.0));
+    done[k] = !(bn[k] > 0.0);
+    iters[k] = 0;
+    relres[k] = 0.0;
+  }
+  int it = 0;
+  while (e == cudaSuccess && res == BEM_OK) {
+    int active = 0;
+    for (int k = 0; k < K; ++k) active += !done[k];
+    if (!active || it >= max_iter) break;
+    ++it;
+    if ((e = dot(rh, r)) != cudaSuccess) break;
+    for (int k = 0; k < K; ++k) {
+      rho_new[k] = C(hd[k].x, hd[k].y);
+      if (!done[k] && !(std::abs(rho_new[k]) > 0.0)) done[k] = 2;   // breakdown
+      if (done[k]) {
+        setc(k, one, zero, zero);   // p unchanged
+        continue;
+      }
+      const C beta = (rho_new[k] / rho[k]) * (alpha[k] / omega[k]);
+      setc(k, one, beta, zero - beta * omega[k]);   // p = r + beta (p - omega v)
+    }
+    if ((e = lin3(p, r, p, v)) != cudaSuccess) break;
+    if ((res = apply(op, BEM_APPLY_BATCHED, 0, p, v, st)) != BEM_OK) break;
+    if ((e = dot(rh, v)) != cudaSuccess) break;
+    for (int k = 0; k < K; ++k) {
+      const C rv(hd[k].x, hd[k].y);
+      if (!done[k] && !(std::abs(rv) > 0.0)) done[k] = 2;
+      alpha[k] = done[k] ? zero : rho_new[k] / rv;
+      setc(k, one, zero - alpha[k], zero);   // s = r - alpha v (s = r when done)
+    }
+    if ((e = lin3(s, r, v, v)) != cudaSuccess) break;
+    if ((e = dot(s, s)) != cudaSuccess) break;
+    std::vector<int> early(K, 0);
+    for (int k = 0; k < K; ++k)
+      if (!done[k] && std::sqrt(std::max(hd[k].x, 0.0)) <= tol * bn[k]) early[k] = 1;
+    if ((res = apply(op, BEM_APPLY_BATCHED, 0, s, t, st)) != BEM_OK) break;
+    if ((e = dot(t, s)) != cudaSuccess) break;
+    std::vector<C> ts(K);
+    for (int k = 0; k < K; ++k) ts[k] = C(hd[k].x, hd[k].y);
+    if ((e = dot(t, t)) != cudaSuccess) break;
+    for (int k = 0; k < K; ++k) {
+      if (done[k]) {
+        omega[k] = zero;
+      } else if (early[k]) {
+        omega[k] = zero;   // x = x + alpha p, r = s
+      } else {
+        omega[k] = hd[k].x > 0.0 ? ts[k] / hd[k].x : zero;
+      }
+      setc(k, one, alpha[k], omega[k]);   // x = x + alpha p + omega s
+    }
+    if ((e = lin3(x, x, p, s)) != cudaSuccess) break;
+    for (int k = 0; k < K; ++k) setc(k, one, zero - omega[k], zero);   // r = s - omega t
+    if ((e = lin3(r, s, t, t)) != cudaSuccess) break;
+    if ((e = dot(r, r)) != cudaSuccess) break;
+    for (int k = 0; k < K; ++k) {
+      if (done[k]) continue;
+      relres[k] = std::sqrt(std::max(hd[k].x, 0.0)) / bn[k];
+      iters[k] = it;
+      if (early[k] || relres[k] <= tol) done[k] = 1;
+      rho[k] = rho_new[k];
+      if (!early[k] && !(std::abs(omega[k]) > 0.0)) done[k] = 2;
+    }
+  }
+  cudaFree(buf);
+  cudaFree(dots);
+  cudaFree(coef);
+  if (res != BEM_OK) return res;
+  if (e != cudaSuccess) return cuda_err(ctx, e, "bem_op_solve");
+  for (int k = 0; k < K; ++k)
+    if (!(relres[k] <= tol))
+      return set_err(ctx, BEM_ERR_NOT_CONVERGED, "bem_op_solve: a frequency did not reach the tolerance");
+  return BEM_OK;
+}
+
+bem_status solve(bem_op* op, const void* B, void* X, double tol, int max_iter, int32_t* iters, double* relres,
+                 cudaStream_t st) {
+  return op->d->prec == BEM_FP64 ? solve_t<double2>(op, B, X, tol, max_iter, iters, relres, st)
+                                 : solve_t<float2>(op, B, X, tol, max_iter, iters, relres, st);
+}
+
+}  // namespace gcq
