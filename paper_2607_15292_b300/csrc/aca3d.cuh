@@ -349,16 +349,16 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   // error-free products in float-float
   float fs[18];                   // sum of the small terms (MIXED)
   for (int c = 0; c < 18; ++c) fs[c] = 0.f;
-  double ref = 0.0;
+  __shared__ double sref;          // ||H_0|| ||f_0[k_d]|| squared (MIXED), read after the first barrier
   if constexpr (FF) {
-    if (slot > 0) {
+    if (slot > 0 && threadIdx.x == 0) {
       const S* f0 = fib_tab[t.blk] + (int64_t)kd * 9;
       double q = 0.0;
       for (int c = 0; c < 9; ++c) {
         const float4 y = reinterpret_cast<const float4*>(f0)[c];
         q += (double)y.x * y.x + (double)y.y * y.y;
       }
-      ref = hn2[(int64_t)t.blk * K] * q;
+      sref = hn2[(int64_t)t.blk * K] * q;
     }
   }
   for (int p0 = 0; p0 < slot; p0 += 64) {
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
           const float4 y = reinterpret_cast<const float4*>(sf)[9 * threadIdx.x + c];
           q += (double)y.x * y.x + (double)y.y * y.y;
         }
-        ssmall[threadIdx.x] = p > 0 && hn2[(int64_t)t.blk * K + p] * q <= 9.5367431640625e-7 * ref;   // 2^-20
+        ssmall[threadIdx.x] = p > 0 && hn2[(int64_t)t.blk * K + p] * q <= 9.5367431640625e-7 * sref;   // 2^-20
       }
       __syncthreads();
     }

@@ -319,6 +319,8 @@ struct EntryView {
   const double2* inv_s2;     // K
   const float4* sw;          // [K][2] s_k / c_a float-float (MIXED path)
   const float4* ef;          // [n_tris][4] FP32 element frames (MIXED path)
+  const float4* cff;         // [n_tris][2] centroid (hi, h), (lo, 0) (MIXED path)
+  const float4* nff;         // [n_nodes][2] node (hi, 0), (lo, 0) (MIXED path)
   int64_t n_nodes, n_tris;
   int32_t K;
   double nu;

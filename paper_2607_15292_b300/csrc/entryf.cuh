@@ -52,7 +52,7 @@ struct FAcc {
 };
 
 // FP64 rule decision with the tie band (same as the oracle), no square root
-__device__ __forceinline__ int rule_index2(const ElemGeo& g, const double* x) {
+__device__ __noinline__ int rule_index2(const ElemGeo& g, const double* x) {
   const double dx = g.c[0] - x[0], dy = g.c[1] - x[1], dz = g.c[2] - x[2];
   const double d2 = dx * dx + dy * dy + dz * dz;
   const double hb = g.h * (1.0 - 1e-12);
@@ -61,6 +61,46 @@ __device__ __forceinline__ int rule_index2(const ElemGeo& g, const double* x) {
   if (d2 >= rule_dist(1) * rule_dist(1) * h2) return 1;
   if (d2 >= rule_dist(2) * rule_dist(2) * h2) return 2;
   return 3;
+}
+
+// row point x_i as a float pair (hi, lo): node coordinates or the centroid
+template <int ROWS>
+__device__ __forceinline__ void row_point_ff(const EntryView& v, int i, float4& hi, float4& lo) {
+  const float4* p = (ROWS == BEM_ROWS_NODES ? v.nff : v.cff) + 2 * (int64_t)i;
+  hi = p[0];
+  lo = p[1];
+}
+
+// the same decision as rule_index2 from an FP32 |c - x|^2 (relative error
+// below 2^-20): thresholds 16 h^2, 4 h^2, h^2 in FP32 carry a relative error
+// below 2^-21, so outside a band of 2^-17 around a threshold both sides of
+// the comparison are certain; inside it the FP64 decision is taken
+__device__ __forceinline__ int rule_index_f(float d2, float h, int e, const EntryView& v, const double* x) {
+  const float h2 = h * h;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float T = (float)(rule_dist(r) * rule_dist(r)) * h2;
+    if (d2 >= T * (1.f + 0x1p-17f)) return r;
+    if (d2 > T * (1.f - 0x1p-17f)) return rule_index2(v.geo[e], x);
+  }
+  return 3;
+}
+
+// rule of element e for row point x from the float pairs: |D|^2 with
+// D = (c_hi - x_hi) + (c_lo - x_lo) per component
+__device__ __forceinline__ int rule_ff(const EntryView& v, int e, const float4& xh, const float4& xl, const double* x) {
+  const float4 ch = v.cff[2 * (int64_t)e], cl = v.cff[2 * (int64_t)e + 1];
+  const float dx = (ch.x - xh.x) + (cl.x - xl.x);
+  const float dy = (ch.y - xh.y) + (cl.y - xl.y);
+  const float dz = (ch.z - xh.z) + (cl.z - xl.z);
+  return rule_index_f(dx * dx + dy * dy + dz * dz, ch.w, e, v, x);
+}
+
+// s + e = a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fadd_rn(s, -a);
+  e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
 }
 
 // CPV int_e rh / r^2 dA in FP32, x inside the flat element (closed form per
@@ -154,29 +194,46 @@ __device__ __forceinline__ void ref_exp(const EntryView& v, int k, float r0, cx<
 }
 
 // reference data of a regular element integral for row point x: D = c - x
-// (FP64 difference rounded once), r0 = |D| rounded to FP32, c0 = |D|^2 - r0^2,
-// and the quadrature rule chosen from |D|^2 (same decision as the FP64 path)
+// rounded to FP32, r0 = |D| rounded to FP32, c0 = |c - x|^2 - r0^2 to about
+// 2^-40 |D|^2, and the quadrature rule (the FP64 decision).  All in FP32:
+// c - x = (c_hi - x_hi) + (c_lo - x_lo) with the first difference split
+// exactly (two-sum), |D|^2 - r0^2 from the exact squares (FMA residuals).
 struct RefF {
   float D[3], r0, c0;
   int ri;
   bool use;
 };
-__device__ __forceinline__ RefF ref_f(const ElemGeo& g, const double* x, float s_abs) {
+__device__ __forceinline__ RefF ref_f(const EntryView& v, int e, const float4& xh, const float4& xl,
+                                      const double* x) {
   RefF R;
-  const double dx = g.c[0] - x[0], dy = g.c[1] - x[1], dz = g.c[2] - x[2];
-  const double d2 = dx * dx + dy * dy + dz * dz;
-  const double hb = g.h * (1.0 - 1e-12);
-  const double h2 = hb * hb;
-  R.ri = d2 >= rule_dist(0) * rule_dist(0) * h2 ? 0
-       : d2 >= rule_dist(1) * rule_dist(1) * h2 ? 1
-       : d2 >= rule_dist(2) * rule_dist(2) * h2 ? 2 : 3;
-  R.D[0] = (float)dx;
-  R.D[1] = (float)dy;
-  R.D[2] = (float)dz;
-  R.r0 = sqrtf((float)d2);
-  R.c0 = (float)(d2 - (double)R.r0 * (double)R.r0);
+  const float4 ch = v.cff[2 * (int64_t)e], cl = v.cff[2 * (int64_t)e + 1];
+  const float hc[3] = {ch.x, ch.y, ch.z}, lc[3] = {cl.x, cl.y, cl.z};
+  const float hx[3] = {xh.x, xh.y, xh.z}, lx[3] = {xl.x, xl.y, xl.z};
+  float Dl[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float a, ea;
+    two_sum_f(hc[k], -hx[k], a, ea);
+    const float b = __fadd_rn(__fadd_rn(lc[k], -lx[k]), ea);
+    two_sum_f(a, b, R.D[k], Dl[k]);
+  }
+  // |D + Dl|^2 = q0 + q1 + q2 + (f0 + f1 + f2) + 2 D.Dl + |Dl|^2 (last term dropped)
+  float q[3], f[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    q[k] = __fmul_rn(R.D[k], R.D[k]);
+    f[k] = fmaf(R.D[k], R.D[k], -q[k]);
+  }
+  float s1, e1, s2, e2;
+  two_sum_f(q[0], q[1], s1, e1);
+  two_sum_f(s1, q[2], s2, e2);
+  R.r0 = sqrtf(s2);
+  const float rr = __fmul_rn(R.r0, R.r0), er = fmaf(R.r0, R.r0, -rr);
+  const float dot = R.D[0] * Dl[0] + R.D[1] * Dl[1] + R.D[2] * Dl[2];
+  const float tail = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(f[0], f[1]), f[2])) - er + 2.f * dot;
+  R.c0 = __fadd_rn(s2, -rr) + tail;   // s2 - rr exact (Sterbenz: rr within 2 ulp of s2)
+  R.ri = rule_index_f(s2, ch.w, e, v, x);
   R.use = false;
-  (void)s_abs;
   return R;
 }
 
@@ -235,8 +292,8 @@ __device__ void entry_sl_f(const EntryView& v, int i, int e, cx<float> s, cx<flo
   acc.init();
   cx<float>* SA = reinterpret_cast<cx<float>*>(acc.t);
   cx<float>* SB = reinterpret_cast<cx<float>*>(acc.t + 2);
-  const FrameF f = frame_f(g, x);
   if (apex >= 0) {
+    const FrameF f = frame_f(g, x);
     // sub-triangles with apex x, coordinates relative to p0; x - p0 = -d0
     const float xr[3] = {-f.d0[0], -f.d0[1], -f.d0[2]};
     const int nsub = apex == 3 ? 3 : 1;
@@ -261,7 +318,9 @@ __device__ void entry_sl_f(const EntryView& v, int i, int e, cx<float> s, cx<flo
       acc.tick();
     }
   } else {
-    const RefF R = ref_f(g, x, 0.f);
+    float4 xh, xl;
+    row_point_ff<ROWS>(v, i, xh, xl);
+    const RefF R = ref_f(v, e, xh, xl, x);
     const int q0 = rule_offset(R.ri), q1 = rule_offset(R.ri + 1);
     const float4 a0 = v.ef[4 * (int64_t)e], fe1 = v.ef[4 * (int64_t)e + 1], fe2 = v.ef[4 * (int64_t)e + 2];
     cx<float> E0[2], w[2];
@@ -299,6 +358,8 @@ template <int ROWS>
 __device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<float> is2, int kf, int lane, int nl,
                            float* out18) {
   const double* x = row_point<ROWS>(v, i);
+  float4 xh, xl;
+  row_point_ff<ROWS>(v, i, xh, xl);
   FAcc<18> acc;
   acc.init();
   cx<float>* A9 = reinterpret_cast<cx<float>*>(acc.t);
@@ -316,7 +377,7 @@ __device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<flo
     else if (e == i)
       apex = 3;
     if (apex < 0) {
-      const RefF R = ref_f(g, x, 0.f);
+      const RefF R = ref_f(v, e, xh, xl, x);
       const int q0 = rule_offset(R.ri), q1 = rule_offset(R.ri + 1);
       const float4 a0 = v.ef[4 * (int64_t)e], fe1 = v.ef[4 * (int64_t)e + 1], fe2 = v.ef[4 * (int64_t)e + 2];
       const float4 fn = v.ef[4 * (int64_t)e + 3];
@@ -404,16 +465,18 @@ __device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<flo
 template <int KERN, int ROWS>
 __device__ __forceinline__ bool entry_heavy(const EntryView& v, int i, int j) {
   const double* x = row_point<ROWS>(v, i);
+  float4 xh, xl;
+  row_point_ff<ROWS>(v, i, xh, xl);
   if constexpr (KERN == BEM_SL) {
     const int32_t* t = v.tri + 3 * (int64_t)j;
     if (ROWS == BEM_ROWS_NODES ? (t[0] == i || t[1] == i || t[2] == i) : j == i) return true;
-    return rule_index2(v.geo[j], x) >= 2;
+    return rule_ff(v, j, xh, xl, x) >= 2;
   } else {
     for (int p = v.ne_ptr[j]; p < v.ne_ptr[j + 1]; ++p) {
       const int e = v.ne_elem[p];
       const int32_t* t = v.tri + 3 * (int64_t)e;
       if (ROWS == BEM_ROWS_NODES ? (t[0] == i || t[1] == i || t[2] == i) : e == i) return true;
-      if (rule_index2(v.geo[e], x) >= 2) return true;
+      if (rule_ff(v, e, xh, xl, x) >= 2) return true;
     }
     return false;
   }

@@ -75,6 +75,8 @@ static EntryView make_view(const bem_mesh* m) {
   v.inv_s2 = m->ctx->d_inv_s2;
   v.sw = m->ctx->d_sw;
   v.ef = m->d_ef;
+  v.cff = m->d_cff;
+  v.nff = m->d_nff;
   v.n_nodes = m->n_nodes;
   v.n_tris = m->n_tris;
   v.K = m->ctx->K;

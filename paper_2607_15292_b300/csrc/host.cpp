@@ -515,6 +515,8 @@ static void mesh_free(bem_mesh* m) {
   cudaFree(m->d_ne_loc);
   cudaFree(m->d_rb);
   cudaFree(m->d_ef);
+  cudaFree(m->d_cff);
+  cudaFree(m->d_nff);
   delete m;
 }
 
@@ -601,6 +603,19 @@ bem_status bem_mesh_create(bem_ctx* ctx, const double* xyz, int64_t nn, const in
     }
     q[3] = (float)g.area2;
   }
+  // coordinates as unevaluated float pairs hi + lo (hi = x rounded to FP32,
+  // lo = the remainder rounded): the MIXED entries form c - x from them
+  std::vector<float> cff(8 * ne, 0.f), nff(8 * nn, 0.f);
+  auto split = [](double x, float* hi, float* lo) {
+    *hi = (float)x;
+    *lo = (float)(x - (double)*hi);
+  };
+  for (int64_t e = 0; e < ne; ++e) {
+    for (int k = 0; k < 3; ++k) split(m->geo[e].c[k], &cff[8 * e + k], &cff[8 * e + 4 + k]);
+    cff[8 * e + 3] = (float)m->geo[e].h;
+  }
+  for (int64_t i = 0; i < nn; ++i)
+    for (int k = 0; k < 3; ++k) split(xyz[3 * i + k], &nff[8 * i + k], &nff[8 * i + 4 + k]);
   cudaError_t ce = cudaSetDevice(ctx->device);
 #define MCPY(dst, src, bytes)                                                   \
   if (ce == cudaSuccess) ce = cudaMalloc(&dst, bytes);                         \
@@ -613,6 +628,8 @@ bem_status bem_mesh_create(bem_ctx* ctx, const double* xyz, int64_t nn, const in
   MCPY(m->d_ne_elem, m->ne_elem.data(), sizeof(int32_t) * 3 * ne);
   MCPY(m->d_ne_loc, m->ne_loc.data(), sizeof(int32_t) * 3 * ne);
   MCPY(m->d_ef, ef.data(), sizeof(float) * ef.size());
+  MCPY(m->d_cff, cff.data(), sizeof(float) * cff.size());
+  MCPY(m->d_nff, nff.data(), sizeof(float) * nff.size());
 #undef MCPY
   if (ce != cudaSuccess) {
     mesh_free(m);

@@ -92,6 +92,8 @@ struct bem_mesh {
   int32_t* d_ne_loc = nullptr;
   double* d_rb = nullptr;         // rigid-body static diagonal (node rows), n_nodes x 9, lazily
   float4* d_ef = nullptr;         // FP32 element frames: [p0 - c, 2 area], [e1, 0], [e2, 0], [n, 0]
+  float4* d_cff = nullptr;        // centroids as float pairs: [c_hi, h], [c_lo, 0] per element
+  float4* d_nff = nullptr;        // nodes as float pairs: [x_hi, 0], [x_lo, 0] per node
 };
 
 struct BlockDesc {
