@@ -41,6 +41,10 @@ from . import kernels, quadrature as quad
 
 ROWS_CENTROIDS, ROWS_NODES = "centroids", "nodes"
 KERNEL_SL, KERNEL_DL = "sl", "dl"
+# wave-speed derivatives of the single layer at fixed density: dV/dc1 (P
+# wave) and dV/dc2 (S wave); integrand dU/dc_a, same columns and quadrature
+KERNEL_SL_DCP, KERNEL_SL_DCS = "sl_dcp", "sl_dcs"
+SL_KINDS = (KERNEL_SL, KERNEL_SL_DCP, KERNEL_SL_DCS)
 
 
 def freqs_bdf2(N: int, dt: float, K: int | None = None) -> np.ndarray:
@@ -79,7 +83,7 @@ class Geometry:
         return self.centroid if kind == ROWS_CENTROIDS else self.xyz
 
     def n_cols(self, kernel):
-        return self.n_tris if kernel == KERNEL_SL else self.n_nodes
+        return self.n_tris if kernel in SL_KINDS else self.n_nodes
 
     def barycentric(self, e, y):
         """Barycentric coordinates (phi_0, phi_1, phi_2) of points y on e."""
@@ -148,7 +152,9 @@ def _on_element(geo: Geometry, kind, i, e):
 
 
 class Operator:
-    """Dense collocation V or C + K at a list of frequencies."""
+    """Dense collocation V or C + K at a list of frequencies; with kernel
+    KERNEL_SL_DCP / KERNEL_SL_DCS the wave-speed derivative dV/dc1 / dV/dc2
+    of the single layer (same quadrature, integrand kernels.dU_dc)."""
 
     def __init__(self, xyz, tri, material, rows=ROWS_NODES, kernel=KERNEL_SL):
         self.geo = Geometry(xyz, tri)
@@ -160,6 +166,10 @@ class Operator:
 
     # ---- integrands ------------------------------------------------------
     def _U(self, r, s, dynamic=False):
+        if self.kernel == KERNEL_SL_DCP:
+            return kernels.dU_dc(r, s, self.rho, self.lam, self.mu, "p")
+        if self.kernel == KERNEL_SL_DCS:
+            return kernels.dU_dc(r, s, self.rho, self.lam, self.mu, "s")
         return kernels.U(r, s, self.rho, self.lam, self.mu, dynamic)
 
     def _TT(self, r, n, s, dynamic=False):
@@ -260,7 +270,7 @@ class Operator:
         K = len(s)
         out = np.zeros((len(rows), len(cols), K, 3, 3), dtype=np.complex128)
         geo = self.geo
-        if self.kernel == KERNEL_SL:
+        if self.kernel in SL_KINDS:
             for a, i in enumerate(rows):
                 i = int(i)
                 sing = [b for b, e in enumerate(cols) if _on_element(geo, self.rows_kind, i, int(e))]

@@ -32,7 +32,9 @@ cancels; there the exact power series in z = s r / c2 (rc = c2 / c1) is used:
 and A', B' follow term by term (d/dr of r^{m-1} = (m-1) r^{m-2}).
 Pins: symmetry, conjugate symmetry in s, the static Kelvin limit, the
 Navier residual by finite differences, traction by finite differences of U,
-series/closed-form agreement (tests/test_oracle_kernels.py).
+series/closed-form agreement (tests/test_oracle_kernels.py).  The wave-speed
+derivatives dU/dc1, dU/dc2 (dU_dc) are pinned by finite differences of U in
+c1, c2 and by the derivatives of the Kelvin solution written in c1, c2.
 """
 from __future__ import annotations
 
@@ -127,6 +129,48 @@ def U(rvec, s, rho: float, lam: float, mu: float, dynamic=False):
     rh = np.broadcast_to(rh, A.shape + (3,))
     eye = np.eye(3)
     return (A[..., None, None] * eye + B[..., None, None] * rh[..., :, None] * rh[..., None, :]) / (4.0 * math.pi * rho)
+
+
+def dcoeffs_dc(r, s, c1: float, c2: float, wave: str):
+    """dA/dc_a and dB/dc_a at fixed rho, a = 1 (wave "p") or 2 (wave "s").
+
+    The wave speeds (Eq. (2.2)) enter A and B only through k_a = s / c_a in
+    h_a, P_a, Q_a and through the explicit 1 / c2^2 of A.  With
+    dk_a/dc_a = -k_a / c_a, dP_a/dk_a = -k_a e_a / r,
+    dQ_a/dk_a = -k_a (1 + k_a r) e_a / r and k_a^2 / s^2 = 1 / c_a^2
+    (e_a = exp(-k_a r)):
+
+        dA/dc1 = -e1 / (r c1^3),            dB/dc1 = (1 + k1 r) e1 / (r c1^3)
+        dA/dc2 = (k2 r - 1) e2 / (r c2^3),  dB/dc2 = -(1 + k2 r) e2 / (r c2^3)
+
+    The 1 / s^2 factors cancel, so no series branch is needed at small |s| r."""
+    r, s = np.broadcast_arrays(np.asarray(r, dtype=np.float64),
+                               np.asarray(s, dtype=np.complex128))
+    c = c1 if wave == "p" else c2
+    kr = s * r / c
+    e = np.exp(-kr) / (r * c ** 3)
+    if wave == "p":
+        return -e, (1.0 + kr) * e
+    return (kr - 1.0) * e, -(1.0 + kr) * e
+
+
+def dU_dc(rvec, s, rho: float, lam: float, mu: float, wave: str):
+    """Derivative of U (shape (..., 3, 3)) with respect to the P-wave speed
+    c1 (wave = "p") or the S-wave speed c2 (wave = "s") at fixed density:
+    [dA/dc delta_ij + dB/dc rh_i rh_j] / (4 pi rho)."""
+    c1, c2 = wave_speeds(rho, lam, mu)
+    rvec = np.asarray(rvec, dtype=np.float64)
+    r = np.linalg.norm(rvec, axis=-1)
+    rh = rvec / r[..., None]
+    A, B = dcoeffs_dc(r, s, c1, c2, wave)
+    rh = np.broadcast_to(rh, A.shape + (3,))
+    eye = np.eye(3)
+    return (A[..., None, None] * eye + B[..., None, None] * rh[..., :, None] * rh[..., None, :]) / (4.0 * math.pi * rho)
+
+
+def lame_from_speeds(rho: float, c1: float, c2: float) -> tuple[float, float]:
+    """Inverse of Eq. (2.2): mu = rho c2^2, lambda = rho (c1^2 - 2 c2^2)."""
+    return rho * (c1 * c1 - 2.0 * c2 * c2), rho * c2 * c2
 
 
 def T(rvec, n, s, rho: float, lam: float, mu: float, dynamic=False):

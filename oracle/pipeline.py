@@ -14,7 +14,7 @@ from . import aca, bem, hmatrix
 
 
 def col_kind(kernel):
-    return "elements" if kernel == bem.KERNEL_SL else "p1nodes"
+    return "elements" if kernel in bem.SL_KINDS else "p1nodes"
 
 
 def trees(op: bem.Operator, leaf: int, eta: float):

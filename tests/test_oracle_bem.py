@@ -124,3 +124,28 @@ def test_sphere_closed_form_static_limit():
     c1 = math.sqrt((lam + 2 * mu) / rho)
     u = sphere.radial_displacement(1.0, 1e-3 * c1, 1.0, rho, lam, mu)   # k a = 1e-3
     assert abs(u - (-1.0 / (3 * lam + 2 * mu))) < 1e-5 * abs(u)
+
+
+@pytest.mark.parametrize("rows", [bem.ROWS_CENTROIDS, bem.ROWS_NODES])
+@pytest.mark.parametrize("kern,wave", [(bem.KERNEL_SL_DCP, "p"), (bem.KERNEL_SL_DCS, "s")])
+def test_speed_derivative_operator_by_fd(rows, kern, wave):
+    """dV/dc_a (singular, near and far element integrals) against central
+    differences of the single layer V in c_a at fixed density."""
+    xyz, tri = syn.icosphere(1)
+    s = bem.freqs_bdf2(16, 2e-5, 16)[[0, 9]]
+    rho = syn.STEEL[0]
+    c1, c2 = kernels.wave_speeds(*syn.STEEL)
+    c = c1 if wave == "p" else c2
+    h = 1e-4 * c
+    rws = np.array([0, 5, 17])
+
+    def v(dc):
+        cc1, cc2 = (c1 + dc, c2) if wave == "p" else (c1, c2 + dc)
+        mat = (rho,) + kernels.lame_from_speeds(rho, cc1, cc2)
+        op = bem.Operator(xyz, tri, mat, rows=rows, kernel=bem.KERNEL_SL)
+        return op.block(rws, np.arange(op.n_cols), s)
+    fd = (-v(2 * h) + 8 * v(h) - 8 * v(-h) + v(-2 * h)) / (12 * h)
+    op = bem.Operator(xyz, tri, syn.STEEL, rows=rows, kernel=kern)
+    d = op.block(rws, np.arange(op.n_cols), s)
+    assert op.n_cols == len(tri)
+    np.testing.assert_allclose(d, fd, rtol=0, atol=1e-7 * np.abs(fd).max())

@@ -136,3 +136,57 @@ def test_series_matches_closed_form(mat):
             K.SERIES_Z = old
         for x, y in zip(a + ad, b + bd):
             np.testing.assert_allclose(x, y, rtol=1e-12)
+
+
+def _speed_perturbed(mat, wave, dc):
+    """Material (rho, lam, mu) with one wave speed moved by dc at fixed rho."""
+    rho = mat[0]
+    c1, c2 = K.wave_speeds(*mat)
+    if wave == "p":
+        c1 += dc
+    else:
+        c2 += dc
+    return (rho,) + K.lame_from_speeds(rho, c1, c2)
+
+
+@pytest.mark.parametrize("mat", MATS)
+@pytest.mark.parametrize("wave", ["p", "s"])
+@pytest.mark.parametrize("zabs", [0.3, 2.5, 30.0])
+def test_speed_derivative_by_fd_of_U(mat, wave, zabs):
+    """dU/dc_a against 4th-order central differences of U in c_a (rho fixed)."""
+    c1, c2 = _speeds(mat)
+    rng = np.random.default_rng(11)
+    r = rng.normal(size=(6, 3))
+    s = zabs * c2 / np.linalg.norm(r, axis=1).mean() * np.exp(0.6j)
+    c = c1 if wave == "p" else c2
+    h = 1e-4 * c
+
+    def u(dc):
+        return K.U(r, s, *_speed_perturbed(mat, wave, dc))
+    fd = (-u(2 * h) + 8 * u(h) - 8 * u(-h) + u(-2 * h)) / (12 * h)
+    d = K.dU_dc(r, s, *mat, wave)
+    np.testing.assert_allclose(d, fd, rtol=0, atol=1e-8 * np.abs(fd).max())
+    assert np.abs(d).max() > 0
+
+
+@pytest.mark.parametrize("mat", MATS)
+def test_speed_derivative_kelvin_limit(mat):
+    """s -> 0: Kelvin U written in the wave speeds,
+    [(1/c1^2 + 1/c2^2) I + (1/c2^2 - 1/c1^2) rh rh^T] / (8 pi rho r), equals
+    kelvin_U, and its c-derivatives are [rh rh^T - I] / (4 pi rho r c1^3) and
+    -[I + rh rh^T] / (4 pi rho r c2^3)."""
+    rho, lam, mu = mat
+    c1, c2 = _speeds(mat)
+    rng = np.random.default_rng(5)
+    r = rng.normal(size=(8, 3))
+    rr = np.linalg.norm(r, axis=1)
+    rh = r / rr[:, None]
+    I = np.eye(3)
+    P = rh[:, :, None] * rh[:, None, :]
+    uk = ((1 / c1 ** 2 + 1 / c2 ** 2) * I + (1 / c2 ** 2 - 1 / c1 ** 2) * P) / (8 * math.pi * rho * rr[:, None, None])
+    np.testing.assert_allclose(uk, K.kelvin_U(r, lam, mu), rtol=1e-13)
+    s = 1e-9 * c2 / rr.max() * np.exp(0.4j)
+    dp = (P - I) / (4 * math.pi * rho * rr[:, None, None] * c1 ** 3)
+    ds = -(I + P) / (4 * math.pi * rho * rr[:, None, None] * c2 ** 3)
+    np.testing.assert_allclose(K.dU_dc(r, s, rho, lam, mu, "p"), dp, rtol=0, atol=1e-8 * np.abs(dp).max())
+    np.testing.assert_allclose(K.dU_dc(r, s, rho, lam, mu, "s"), ds, rtol=0, atol=1e-8 * np.abs(ds).max())
