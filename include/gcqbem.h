@@ -63,8 +63,16 @@ typedef enum { BEM_FP64 = 0, BEM_MIXED = 1 } bem_precision;
  * rows), Sec. 2.3 after Eq. (2.15). */
 typedef enum { BEM_ROWS_CENTROIDS = 0, BEM_ROWS_NODES = 1 } bem_rows;
 /* Single layer V (columns = elements, P0) or double layer C + K (columns =
- * nodes, P1; the integral-free term C of Eq. (2.7) included), Eq. (2.15). */
-typedef enum { BEM_SL = 0, BEM_DL = 1 } bem_kernel;
+ * nodes, P1; the integral-free term C of Eq. (2.7) included), Eq. (2.15).
+ * BEM_SL_DCP / BEM_SL_DCS: the derivative of V with respect to the P-wave
+ * speed c1 / the S-wave speed c2 of Eq. (2.2) at fixed density (columns =
+ * elements, the same rows, quadrature and compression as V; the integrand
+ * dU/dc_a = [dA/dc_a I + dB/dc_a rh rh^T] / (4 pi rho) with
+ *   dA/dc1 = -e1 / (r c1^3),            dB/dc1 = (1 + k1 r) e1 / (r c1^3),
+ *   dA/dc2 = (k2 r - 1) e2 / (r c2^3),  dB/dc2 = -(1 + k2 r) e2 / (r c2^3),
+ * k_a = s / c_a, e_a = exp(-k_a r)).  For the wave-speed gradient of a
+ * functional of V X (adjoint method). */
+typedef enum { BEM_SL = 0, BEM_DL = 1, BEM_SL_DCP = 2, BEM_SL_DCS = 3 } bem_kernel;
 /* Batched: Y_k = C(s_k) X_k for all k.  Contracted: y = sum_k C(s_k) X_k,
  * the gCQ history sum of Eq. (3.15). */
 typedef enum { BEM_APPLY_BATCHED = 0, BEM_APPLY_CONTRACTED = 1 } bem_apply_mode;
@@ -217,6 +225,20 @@ bem_status bem_op_apply(bem_op* op, int32_t mode, int32_t transpose,
  * max_iter); X then holds the last iterate. */
 bem_status bem_op_solve(bem_op* op, const void* B, void* X, double tol, int32_t max_iter,
                         int32_t* iters, double* relres, void* stream);
+
+/* Inner product <G, C X>: BATCHED, sum over k, rows i and components of
+ * conj(G_k[i]) (C(s_k) X_k)[i]; CONTRACTED, sum over i of
+ * conj(g[i]) (sum_k C(s_k) X_k)[i].  One complex number accumulated in FP64,
+ * written to the host array out[2] (real, imaginary part).  G: device, the
+ * layout of the apply's output; X: device, the layout of its input; both of
+ * the operator's complex type, 16-byte aligned.  With a wave-speed
+ * derivative operator (BEM_SL_DCP, BEM_SL_DCS) and G the adjoint field of a
+ * real functional J of Y = V X (PyTorch's convention, G = 2 dJ/dY*),
+ * Re <G, dV/dc X> = dJ/dc: the wave-speed gradient of the adjoint method.
+ * Allocates one output-sized device vector; synchronises the stream.
+ * Errors: BEM_ERR_ARG (mode, null or misaligned pointer), BEM_ERR_OOM,
+ * BEM_ERR_CUDA. */
+bem_status bem_op_inner(bem_op* op, int32_t mode, const void* G, const void* X, double* out, void* stream);
 
 /* Dense reconstruction of the compressed tensor (for checks on small
  * meshes): out device n_rows x n_cols x K 3x3 complex blocks, original

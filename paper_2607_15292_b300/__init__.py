@@ -29,6 +29,8 @@ BEM_OK, BEM_ERR_ARG, BEM_ERR_CUDA, BEM_ERR_OOM, BEM_ERR_MESH, BEM_ERR_NOT_CONVER
 BEM_FP64, BEM_MIXED = 0, 1
 BEM_ROWS_CENTROIDS, BEM_ROWS_NODES = 0, 1
 BEM_SL, BEM_DL = 0, 1
+# wave-speed derivatives of the single layer, dV/dc_p and dV/dc_s (fixed density)
+BEM_SL_DCP, BEM_SL_DCS = 2, 3
 BEM_APPLY_BATCHED, BEM_APPLY_CONTRACTED = 0, 1
 
 _STATUS = {0: "BEM_OK", 1: "BEM_ERR_ARG", 2: "BEM_ERR_CUDA", 3: "BEM_ERR_OOM", 4: "BEM_ERR_MESH",
@@ -81,6 +83,7 @@ _SIGS = {
     "bem_op_blocks": (_i32, [_vp, _P(_i64)]),
     "bem_op_face_ranks": (_i32, [_vp, _P(_i32)]),
     "bem_op_solve": (_i32, [_vp, _vp, _vp, _dbl, _i32, _P(_i32), _P(_dbl), _vp]),
+    "bem_op_inner": (_i32, [_vp, _i32, _vp, _vp, _P(_dbl), _vp]),
     "bem_face_compress": (_i32, [_vp, _vp, _i64, _i64, _dbl, _P(_i32), _vp, _vp]),
     "bem_kernel_launches": (_i64, []),
     "bem_cq_forward": (_i32, [_i32, _i64, _vp, _vp, _vp]),
@@ -327,6 +330,13 @@ class Operator:
 
     def apply_adjoint(self, Yin, Xout, mode: int = BEM_APPLY_BATCHED, stream=None):
         self.apply(Yin, Xout, mode, stream, transpose=1)
+
+    def inner(self, G, X, mode: int = BEM_APPLY_BATCHED, stream=None) -> complex:
+        """<G, C X> (bem_op_inner): sum of conj(G) times the apply of X."""
+        out = np.zeros(2, dtype=np.float64)
+        _check(_lib.bem_op_inner(self._p, mode, _dptr(G), _dptr(X), out.ctypes.data_as(_P(_dbl)),
+                                 _stream_ptr(stream)), self.ctx.ptr)
+        return complex(out[0], out[1])
 
     def dense(self, out, stream=None):
         _check(_lib.bem_op_dense(self._p, _dptr(out), _stream_ptr(stream)), self.ctx.ptr)

@@ -5,6 +5,11 @@ through the C ABI (marshalling only; no arithmetic here).
 For a real loss L of complex inputs PyTorch propagates dL/dz* (the conjugate
 Wirtinger derivative); for Y = C X that is dL/dX* = C^H dL/dY*, which is
 what bem_op_apply with transpose = 1 computes (Eq. (3.15) transposed).
+
+Wave-speed gradients (the adjoint method): for Y = V(c) X with c = (c_p,
+c_s) at fixed density, dL/dc_a = Re <G, dV/dc_a X> with G PyTorch's
+gradient of Y; bem_op_inner evaluates it on the compressed derivative
+operators (kernels BEM_SL_DCP, BEM_SL_DCS).
 """
 from __future__ import annotations
 
@@ -43,4 +48,42 @@ def apply(op: Operator, X: torch.Tensor, mode: int = BEM_APPLY_BATCHED) -> torch
     return OperatorApply.apply(X, op, mode)
 
 
-__all__ = ["OperatorApply", "apply", "BEM_APPLY_BATCHED", "BEM_APPLY_CONTRACTED"]
+class WaveSpeedApply(torch.autograd.Function):
+    """Y = V(c) X of a single-layer operator, differentiable in X (adjoint
+    apply) and in the wave speeds c = (c_p, c_s) (real tensor of shape (2,),
+    the speeds the operators were compressed at; its value is not read).
+    dops = (dV/dc_p, dV/dc_s): operators of kernels BEM_SL_DCP, BEM_SL_DCS on
+    the same mesh, rows and frequencies."""
+
+    @staticmethod
+    def forward(ctx, X: torch.Tensor, c: torch.Tensor, op: Operator, dops, mode: int = BEM_APPLY_BATCHED):
+        X = X.contiguous()
+        t = op.tree
+        shape = (op.K, t.n_rows, 3) if mode == BEM_APPLY_BATCHED else (t.n_rows, 3)
+        Y = torch.empty(shape, dtype=X.dtype, device=X.device)
+        op.apply(X, Y, mode)
+        ctx.save_for_backward(X)
+        ctx.op, ctx.dops, ctx.mode, ctx.cdev, ctx.cdt = op, dops, mode, c.device, c.dtype
+        return Y
+
+    @staticmethod
+    def backward(ctx, gY: torch.Tensor):
+        (X,) = ctx.saved_tensors
+        gY = gY.contiguous()
+        gX = gc = None
+        if ctx.needs_input_grad[0]:
+            gX = torch.empty(X.shape, dtype=gY.dtype, device=gY.device)
+            ctx.op.apply_adjoint(gY, gX, ctx.mode)
+        if ctx.needs_input_grad[1]:
+            gc = torch.tensor([d.inner(gY, X, ctx.mode).real for d in ctx.dops], dtype=ctx.cdt, device=ctx.cdev)
+        return gX, gc, None, None, None
+
+
+def apply_speeds(op: Operator, dops, X: torch.Tensor, c: torch.Tensor,
+                 mode: int = BEM_APPLY_BATCHED) -> torch.Tensor:
+    """Differentiable apply of V(c) with gradients to X and to c = (c_p, c_s)."""
+    return WaveSpeedApply.apply(X, c, op, tuple(dops), mode)
+
+
+__all__ = ["OperatorApply", "WaveSpeedApply", "apply", "apply_speeds", "BEM_APPLY_BATCHED",
+           "BEM_APPLY_CONTRACTED"]

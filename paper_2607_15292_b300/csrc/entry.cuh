@@ -83,6 +83,7 @@ __device__ __forceinline__ cx<float> cexp_neg(cx<float> z) {
 template <typename R>
 struct KC {
   R c1, c2, c1s, c2s, ic1, ic2, ic2s, inv4pirho, inv4pi, alpha, beta;
+  R ic1c, ic2c;   // 1 / c1^3, 1 / c2^3 (wave-speed derivatives)
   R ta[kSeriesTerms], tb[kSeriesTerms];
 };
 
@@ -100,6 +101,8 @@ KC<R> make_kc(const Material& m) {
   k.inv4pi = (R)(1.0 / (4.0 * M_PI));
   k.alpha = (R)(0.5 * (1.0 / (m.c1 * m.c1) + 1.0 / (m.c2 * m.c2)));
   k.beta = (R)(0.5 * (1.0 / (m.c2 * m.c2) - 1.0 / (m.c1 * m.c1)));
+  k.ic1c = (R)(1.0 / (m.c1 * m.c1 * m.c1));
+  k.ic2c = (R)(1.0 / (m.c2 * m.c2 * m.c2));
   for (int i = 0; i < kSeriesTerms; ++i) {
     k.ta[i] = (R)m.ta[i];
     k.tb[i] = (R)m.tb[i];
@@ -211,6 +214,49 @@ __device__ __forceinline__ void kernel_coeffs(const KC<R>& k, R r, cx<R> s, cx<R
   closed_coeffs<R, D, DYN>(k, r, kr1, kr2, cexp_neg(kr1), cexp_neg(kr2), is2, A, B, dA, dB, S3);
 }
 
+// wave-speed derivatives of A, B at fixed rho (DC = 1: c1, DC = 2: c2),
+// from kr = k_a r and e = exp(-k_a r) of that wave:
+//   dA/dc1 = -e1 / (r c1^3),            dB/dc1 = (1 + k1 r) e1 / (r c1^3)
+//   dA/dc2 = (k2 r - 1) e2 / (r c2^3),  dB/dc2 = -(1 + k2 r) e2 / (r c2^3)
+// (the 1 / s^2 of A and B cancels against k_a^2 = s^2 / c_a^2: no series)
+template <typename R, int DC>
+__device__ __forceinline__ void dcoeffs_from(const KC<R>& k, R r, cx<R> kr, cx<R> e, cx<R>& A, cx<R>& B) {
+  const cx<R> f = ((DC == 1 ? k.ic1c : k.ic2c) / r) * e;
+  const cx<R> g = f * (kr + mk<R>(R(1), R(0)));
+  if (DC == 1) {
+    A = mk<R>(-f.x, -f.y);
+    B = g;
+  } else {
+    A = f * (kr - mk<R>(R(1), R(0)));
+    B = mk<R>(-g.x, -g.y);
+  }
+}
+
+// accumulate w dU/dc_a(d) into (SA, SB[6])
+template <typename R, int DC>
+__device__ __forceinline__ void acc_dU(const KC<R>& k, R wq, R dx, R dy, R dz, cx<R> s, cx<R>& SA, cx<R>* SB) {
+  R r = sqrt(dx * dx + dy * dy + dz * dz);
+  R ir = R(1) / r;
+  R h[3] = {dx * ir, dy * ir, dz * ir};
+  const R ic = DC == 1 ? k.ic1 : k.ic2;
+  const cx<R> kr = mk<R>(s.x * r * ic, s.y * r * ic);
+  cx<R> A, B;
+  dcoeffs_from<R, DC>(k, r, kr, cexp_neg(kr), A, B);
+  SA = SA + wq * A;
+  cx<R> wb = wq * B;
+  SB[0] = SB[0] + (h[0] * h[0]) * wb;
+  SB[1] = SB[1] + (h[0] * h[1]) * wb;
+  SB[2] = SB[2] + (h[0] * h[2]) * wb;
+  SB[3] = SB[3] + (h[1] * h[1]) * wb;
+  SB[4] = SB[4] + (h[1] * h[2]) * wb;
+  SB[5] = SB[5] + (h[2] * h[2]) * wb;
+}
+
+// the single-layer integrand: U (DC = 0) or dU/dc_a (DC = 1, 2)
+template <typename R, int DC>
+__device__ __forceinline__ void acc_sl(const KC<R>& k, R wq, R dx, R dy, R dz, cx<R> s, cx<R> is2, cx<R>& SA,
+                                       cx<R>* SB);
+
 // accumulate w U into (SA, SB[6]) from the coefficients, unit vector h
 template <typename R>
 __device__ __forceinline__ void acc_U_from(R wq, const R* h, cx<R> A, cx<R> B, cx<R>& SA, cx<R>* SB) {
@@ -263,6 +309,15 @@ __device__ __forceinline__ void acc_U(const KC<R>& k, R wq, R dx, R dy, R dz, cx
   SB[3] = SB[3] + (h[1] * h[1]) * wb;
   SB[4] = SB[4] + (h[1] * h[2]) * wb;
   SB[5] = SB[5] + (h[2] * h[2]) * wb;
+}
+
+template <typename R, int DC>
+__device__ __forceinline__ void acc_sl(const KC<R>& k, R wq, R dx, R dy, R dz, cx<R> s, cx<R> is2, cx<R>& SA,
+                                       cx<R>* SB) {
+  if constexpr (DC == 0)
+    acc_U<R>(k, wq, dx, dy, dz, s, is2, SA, SB);
+  else
+    acc_dU<R, DC>(k, wq, dx, dy, dz, s, SA, SB);
 }
 
 // accumulate w T^T(d, n) (double-layer integrand, 9 entries [a*3+b] = T_ba)
@@ -334,8 +389,9 @@ __device__ __forceinline__ const double* row_point(const EntryView& v, int i) {
 }
 
 // ---- single layer -----------------------------------------------------------
-// V[i, e](s) = int_e U(y - x_i, s) dy; R = compute type of regular far rules
-template <typename R, int ROWS>
+// V[i, e](s) = int_e U(y - x_i, s) dy; R = compute type of regular far rules;
+// DC = 1, 2: the wave-speed derivative dV/dc_a (integrand dU/dc_a)
+template <typename R, int ROWS, int DC>
 __device__ void entry_sl(const EntryView& v, int i, int e, cx<double> s, cx<double> is2, cx<double>* out) {
   const ElemGeo& g = v.geo[e];
   const double* x = row_point<ROWS>(v, i);
@@ -382,7 +438,7 @@ __device__ void entry_sl(const EntryView& v, int i, int e, cx<double> s, cx<doub
           double d0 = ax[0] + u * (ba[0] + vv * cb[0]);
           double d1 = ax[1] + u * (ba[1] + vv * cb[1]);
           double d2 = ax[2] + u * (ba[2] + vv * cb[2]);
-          acc_U<double>(v.kd, wu * wv * ar2 * u, d0, d1, d2, s, is2, SA, SB);
+          acc_sl<double, DC>(v.kd, wu * wv * ar2 * u, d0, d1, d2, s, is2, SA, SB);
         }
       }
     }
@@ -402,16 +458,16 @@ __device__ void entry_sl(const EntryView& v, int i, int e, cx<double> s, cx<doub
       float ar = (float)g.area2;
       for (int q = q0; q < q1; ++q) {
         float xi = (float)c_rule[3 * q], et = (float)c_rule[3 * q + 1], wq = (float)c_rule[3 * q + 2] * ar;
-        acc_U<float>(v.kf, wq, f0[0] + xi * f1[0] + et * f2[0], f0[1] + xi * f1[1] + et * f2[1],
-                     f0[2] + xi * f1[2] + et * f2[2], sf, isf, SAf, SBf);
+        acc_sl<float, DC>(v.kf, wq, f0[0] + xi * f1[0] + et * f2[0], f0[1] + xi * f1[1] + et * f2[1],
+                          f0[2] + xi * f1[2] + et * f2[2], sf, isf, SAf, SBf);
       }
       SA = {SAf.x, SAf.y};
       for (int c = 0; c < 6; ++c) SB[c] = {SBf[c].x, SBf[c].y};
     } else {
       for (int q = q0; q < q1; ++q) {
         double xi = c_rule[3 * q], et = c_rule[3 * q + 1], wq = c_rule[3 * q + 2] * g.area2;
-        acc_U<double>(v.kd, wq, d0[0] + xi * g.e1[0] + et * g.e2[0], d0[1] + xi * g.e1[1] + et * g.e2[1],
-                      d0[2] + xi * g.e1[2] + et * g.e2[2], s, is2, SA, SB);
+        acc_sl<double, DC>(v.kd, wq, d0[0] + xi * g.e1[0] + et * g.e2[0], d0[1] + xi * g.e1[1] + et * g.e2[1],
+                           d0[2] + xi * g.e1[2] + et * g.e2[2], s, is2, SA, SB);
       }
     }
   }
@@ -596,21 +652,26 @@ __device__ void entry_dl(const EntryView& v, int i, int j, cx<double> s, cx<doub
 }
 
 // launch with compile-time (kernel, rows): LAUNCH may use KK and RR
-#define GCQ_DISPATCH(kernel, rows, LAUNCH)                                                       \
+#define GCQ_DISPATCH_ROWS(KIND, rows, LAUNCH)                                                   \
   do {                                                                                           \
-    if ((kernel) == BEM_SL && (rows) == BEM_ROWS_NODES) {                                        \
-      constexpr int KK = BEM_SL, RR = BEM_ROWS_NODES;                                            \
-      LAUNCH;                                                                                    \
-    } else if ((kernel) == BEM_SL) {                                                             \
-      constexpr int KK = BEM_SL, RR = BEM_ROWS_CENTROIDS;                                        \
-      LAUNCH;                                                                                    \
-    } else if ((rows) == BEM_ROWS_NODES) {                                                       \
-      constexpr int KK = BEM_DL, RR = BEM_ROWS_NODES;                                            \
+    if ((rows) == BEM_ROWS_NODES) {                                                              \
+      constexpr int KK = KIND, RR = BEM_ROWS_NODES;                                              \
       LAUNCH;                                                                                    \
     } else {                                                                                     \
-      constexpr int KK = BEM_DL, RR = BEM_ROWS_CENTROIDS;                                        \
+      constexpr int KK = KIND, RR = BEM_ROWS_CENTROIDS;                                          \
       LAUNCH;                                                                                    \
     }                                                                                            \
+  } while (0)
+#define GCQ_DISPATCH(kernel, rows, LAUNCH)                                                       \
+  do {                                                                                           \
+    if ((kernel) == BEM_SL)                                                                      \
+      GCQ_DISPATCH_ROWS(BEM_SL, rows, LAUNCH);                                                   \
+    else if ((kernel) == BEM_DL)                                                                 \
+      GCQ_DISPATCH_ROWS(BEM_DL, rows, LAUNCH);                                                   \
+    else if ((kernel) == BEM_SL_DCP)                                                             \
+      GCQ_DISPATCH_ROWS(BEM_SL_DCP, rows, LAUNCH);                                               \
+    else                                                                                         \
+      GCQ_DISPATCH_ROWS(BEM_SL_DCS, rows, LAUNCH);                                               \
   } while (0)
 
 }  // namespace gcq

@@ -276,8 +276,20 @@ __device__ __forceinline__ void coeffs_ref(const KC<float>& k, float r, float dr
   closed_coeffs<float, D, false>(k, r, kr1, kr2, e1, e2, is2, A, B, dA, dB, S3);
 }
 
+// wave-speed derivative coefficients at a regular point (DC = 1: c1, 2: c2),
+// exp(-k_a r) through the reference exponential when it is in use
+template <int DC>
+__device__ __forceinline__ void dcoeffs_ref(const KC<float>& k, float r, float dr, bool use, const cx<float>* E0,
+                                            const cx<float>* w, cx<float>& A, cx<float>& B) {
+  const cx<float> wa = w[DC - 1];
+  const cx<float> kr = {wa.x * r, wa.y * r};
+  const cx<float> e = use ? E0[DC - 1] * cexp_neg(cx<float>{wa.x * dr, wa.y * dr}) : cexp_neg(kr);
+  dcoeffs_from<float, DC>(k, r, kr, e, A, B);
+}
+
 // ---- single layer: V[i, e] partial sum over points lane, lane + nl, ... -------
-template <int ROWS>
+// (DC = 1, 2: the wave-speed derivative dV/dc_a)
+template <int ROWS, int DC>
 __device__ void entry_sl_f(const EntryView& v, int i, int e, cx<float> s, cx<float> is2, int kf, int lane, int nl,
                            float* out18) {
   const ElemGeo& g = v.geo[e];
@@ -313,8 +325,8 @@ __device__ void entry_sl_f(const EntryView& v, int i, int e, cx<float> s, cx<flo
       const float u = c_gl16_f[a], wu = c_gl16_f[16 + a];
       const float vv = c_gl16_f[b], wv = c_gl16_f[16 + b];
       // y - x = (A - x) + u (ba + v cb) with A = x
-      acc_U<float>(v.kf, wu * wv * st.ar2 * u, u * (st.ba[0] + vv * st.cb[0]), u * (st.ba[1] + vv * st.cb[1]),
-                   u * (st.ba[2] + vv * st.cb[2]), s, is2, *SA, SB);
+      acc_sl<float, DC>(v.kf, wu * wv * st.ar2 * u, u * (st.ba[0] + vv * st.cb[0]),
+                        u * (st.ba[1] + vv * st.cb[1]), u * (st.ba[2] + vv * st.cb[2]), s, is2, *SA, SB);
       acc.tick();
     }
   } else {
@@ -334,8 +346,13 @@ __device__ void entry_sl_f(const EntryView& v, int i, int e, cx<float> s, cx<flo
       ref_point(R, a0, fe1, fe2, xi, et, d, r, dr);
       const float ir = 1.f / r;
       const float hh[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
-      cx<float> A, Bc, dA, dB, S3;
-      coeffs_ref<false>(v.kf, r, dr, s, is2, use, E0, w, A, Bc, dA, dB, S3);
+      cx<float> A, Bc;
+      if constexpr (DC == 0) {
+        cx<float> dA, dB, S3;
+        coeffs_ref<false>(v.kf, r, dr, s, is2, use, E0, w, A, Bc, dA, dB, S3);
+      } else {
+        dcoeffs_ref<DC>(v.kf, r, dr, use, E0, w, A, Bc);
+      }
       acc_U_from<float>(wq, hh, A, Bc, *SA, SB);
       acc.tick();
     }
@@ -467,7 +484,7 @@ __device__ __forceinline__ bool entry_heavy(const EntryView& v, int i, int j) {
   const double* x = row_point<ROWS>(v, i);
   float4 xh, xl;
   row_point_ff<ROWS>(v, i, xh, xl);
-  if constexpr (KERN == BEM_SL) {
+  if constexpr (kern_sl(KERN)) {
     const int32_t* t = v.tri + 3 * (int64_t)j;
     if (ROWS == BEM_ROWS_NODES ? (t[0] == i || t[1] == i || t[2] == i) : j == i) return true;
     return rule_ff(v, j, xh, xl, x) >= 2;
@@ -485,8 +502,8 @@ __device__ __forceinline__ bool entry_heavy(const EntryView& v, int i, int j) {
 template <int KERN, int ROWS>
 __device__ __forceinline__ void entry_f(const EntryView& v, int i, int j, cx<float> s, cx<float> is2, int kf,
                                         int lane, int nl, float* out18) {
-  if (KERN == BEM_SL)
-    entry_sl_f<ROWS>(v, i, j, s, is2, kf, lane, nl, out18);
+  if constexpr (kern_sl(KERN))
+    entry_sl_f<ROWS, kern_dc(KERN)>(v, i, j, s, is2, kf, lane, nl, out18);
   else
     entry_dl_f<ROWS>(v, i, j, s, is2, kf, lane, nl, out18);
 }
@@ -514,8 +531,8 @@ __device__ __forceinline__ void entry(const EntryView& v, int i, int j, int kf, 
                         o);
     for (int c = 0; c < 9; ++c) out[c] = {(double)o[2 * c], (double)o[2 * c + 1]};
   } else {
-    if (KERN == BEM_SL)
-      entry_sl<double, ROWS>(v, i, j, s, is2, out);
+    if constexpr (kern_sl(KERN))
+      entry_sl<double, ROWS, kern_dc(KERN)>(v, i, j, s, is2, out);
     else
       entry_dl<double, ROWS>(v, i, j, s, is2, out);
   }

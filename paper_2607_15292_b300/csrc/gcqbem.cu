@@ -141,7 +141,7 @@ __global__ void k_entries_req(EntryView v, const int32_t* __restrict__ req, int6
   if (t >= n) return;
   int i = req[3 * t], j = req[3 * t + 1], k = req[3 * t + 2];
   int64_t nr = rows == BEM_ROWS_NODES ? v.n_nodes : v.n_tris;
-  int64_t nc = kernel == BEM_SL ? v.n_tris : v.n_nodes;
+  int64_t nc = kern_sl(kernel) ? v.n_tris : v.n_nodes;
   S* o = out + 9 * t;
   if (i < 0 || i >= nr || j < 0 || j >= nc || k < -1 || k >= v.K) {
     for (int c = 0; c < 9; ++c) St<S>::st(o + c, {NAN, NAN});
@@ -275,7 +275,7 @@ __global__ void k_entries_req_noalloc(EntryView v, const int32_t* __restrict__ r
   if (t >= n) return;
   const int i = req[3 * t], j = req[3 * t + 1], k = req[3 * t + 2];
   const int64_t nr = ROWS == BEM_ROWS_NODES ? v.n_nodes : v.n_tris;
-  const int64_t nc = KERN == BEM_SL ? v.n_tris : v.n_nodes;
+  const int64_t nc = kern_sl(KERN) ? v.n_tris : v.n_nodes;
   S* o = out + 9 * t;
   if (i < 0 || i >= nr || j < 0 || j >= nc || k < -1 || k >= v.K) {
     for (int c = 0; c < 9; ++c) St<S>::st(o + c, {NAN, NAN});
@@ -312,7 +312,7 @@ extern "C" bem_status bem_entries_noalloc(bem_mesh* mesh, int32_t rows, int32_t 
   using namespace gcq;
   if (!mesh) return BEM_ERR_ARG;
   bem_ctx* ctx = mesh->ctx;
-  if ((rows != BEM_ROWS_CENTROIDS && rows != BEM_ROWS_NODES) || (kernel != BEM_SL && kernel != BEM_DL) || n < 0 ||
+  if ((rows != BEM_ROWS_CENTROIDS && rows != BEM_ROWS_NODES) || !kern_valid(kernel) || n < 0 ||
       (n > 0 && (!req || !out)))
     return set_err_c(ctx, BEM_ERR_ARG, "bem_entries_noalloc: bad arguments");
   if (n > (int64_t)kNoAllocSlots * kNoAllocChunk)

@@ -278,7 +278,7 @@ bem_status build_trees(bem_tree* t) {
   rlo = rp;
   rhi = rp;
   // columns: supports
-  if (t->kernel == BEM_SL) {
+  if (gcq::kern_sl(t->kernel)) {
     cp.resize(3 * ne);
     clo.resize(3 * ne);
     chi.resize(3 * ne);
@@ -648,7 +648,7 @@ bem_status bem_entries(bem_mesh* mesh, int32_t rows, int32_t kernel, const int32
                        void* stream) {
   if (!mesh) return BEM_ERR_ARG;
   bem_ctx* ctx = mesh->ctx;
-  if ((rows != BEM_ROWS_CENTROIDS && rows != BEM_ROWS_NODES) || (kernel != BEM_SL && kernel != BEM_DL) || n < 0 ||
+  if ((rows != BEM_ROWS_CENTROIDS && rows != BEM_ROWS_NODES) || !gcq::kern_valid(kernel) || n < 0 ||
       (n > 0 && (!req || !out)))
     return set_err(ctx, BEM_ERR_ARG, "bem_entries: bad arguments");
   if (ctx->device < 0) return set_err(ctx, BEM_ERR_STATE, "bem_entries: host-only context (device -1)");
@@ -675,7 +675,7 @@ bem_status bem_entries(bem_mesh* mesh, int32_t rows, int32_t kernel, const int32
 bem_status bem_tree_build(bem_mesh* mesh, int32_t rows, int32_t kernel, bem_tree** out) {
   if (!mesh) return BEM_ERR_ARG;
   bem_ctx* ctx = mesh->ctx;
-  if (!out || (rows != BEM_ROWS_CENTROIDS && rows != BEM_ROWS_NODES) || (kernel != BEM_SL && kernel != BEM_DL))
+  if (!out || (rows != BEM_ROWS_CENTROIDS && rows != BEM_ROWS_NODES) || !gcq::kern_valid(kernel))
     return set_err(ctx, BEM_ERR_ARG, "bem_tree_build: bad arguments");
   *out = nullptr;
   auto* t = new (std::nothrow) bem_tree;
@@ -805,6 +805,17 @@ bem_status bem_op_solve(bem_op* op, const void* B, void* X, double tol, int32_t 
     return set_err(ctx, BEM_ERR_ARG, "bem_op_solve: B and X must be 16-byte aligned");
   GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
   return solve(op, B, X, tol, max_iter, iters, relres, (cudaStream_t)stream);
+}
+
+bem_status bem_op_inner(bem_op* op, int32_t mode, const void* G, const void* X, double* out, void* stream) {
+  if (!op) return BEM_ERR_ARG;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  if ((mode != BEM_APPLY_BATCHED && mode != BEM_APPLY_CONTRACTED) || !G || !X || !out)
+    return set_err(ctx, BEM_ERR_ARG, "bem_op_inner: bad arguments");
+  if (((uintptr_t)G & 15) || ((uintptr_t)X & 15))
+    return set_err(ctx, BEM_ERR_ARG, "bem_op_inner: G and X must be 16-byte aligned");
+  GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
+  return inner(op, mode, G, X, out, (cudaStream_t)stream);
 }
 
 bem_status bem_op_face_ranks(const bem_op* op, int32_t* ranks) {

@@ -25,6 +25,11 @@ __host__ __device__ constexpr double rule_dist(int r) { return r == 0 ? 4.0 : (r
 __host__ __device__ constexpr int rule_offset(int r) {
   return r <= 0 ? 0 : (r == 1 ? 9 : (r == 2 ? 34 : (r == 3 ? 98 : 354)));
 }
+// kernel kinds: single-layer-like (V and its wave-speed derivatives, columns
+// = elements) and the wave-speed derivative selected (0 none, 1 c1, 2 c2)
+__host__ __device__ constexpr bool kern_sl(int k) { return k != BEM_DL; }
+__host__ __device__ constexpr int kern_dc(int k) { return k == BEM_SL_DCP ? 1 : (k == BEM_SL_DCS ? 2 : 0); }
+inline bool kern_valid(int k) { return k == BEM_SL || k == BEM_DL || k == BEM_SL_DCP || k == BEM_SL_DCS; }
 constexpr int kSeriesTerms = 26;
 constexpr double kSeriesZ = 1.0;                    // series where |s| r / c2 < 1
 
@@ -155,6 +160,7 @@ bem_status op_blocks(const bem_op* op, int64_t* info);
 bem_status op_face_ranks(const bem_op* op, int32_t* ranks);
 bem_status solve(bem_op* op, const void* B, void* X, double tol, int max_iter, int32_t* iters, double* relres,
                  cudaStream_t st);
+bem_status inner(bem_op* op, int mode, const void* G, const void* X, double* out, cudaStream_t st);
 bem_status face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, double eps, int32_t* rank, void* out,
                          cudaStream_t st);
 bem_status cq_transform(int N, int64_t nvec, const void* in, void* out, bool inverse, cudaStream_t st);

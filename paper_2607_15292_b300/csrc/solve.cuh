@@ -190,6 +190,49 @@ static bem_status solve_t(bem_op* op, const void* Bv, void* Xv, double tol, int 
   return BEM_OK;
 }
 
+// <G, C X> over every frequency, row and component (FP64 sums), the
+// wave-speed gradient Re <G, dV/dc X> of the adjoint method when C is a
+// derivative operator
+template <typename S>
+static bem_status inner_t(bem_op* op, int mode, const void* G, const void* X, double* out, cudaStream_t st) {
+  OpData* d = op->d;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  const int64_t n = 3 * d->n_rows * (mode == BEM_APPLY_BATCHED ? (int64_t)d->K : 1);
+  S* Y = nullptr;
+  double2* dot = nullptr;
+  GCQ_CUDA(ctx, cudaMalloc(&Y, sizeof(S) * (size_t)n));
+  if (cudaMalloc(&dot, sizeof(double2)) != cudaSuccess) {
+    cudaFree(Y);
+    return set_err(ctx, BEM_ERR_OOM, "bem_op_inner: out of device memory");
+  }
+  bem_status res = apply(op, mode, 0, X, Y, st);
+  cudaError_t e = cudaSuccess;
+  double2 h = {0.0, 0.0};
+  if (res == BEM_OK) {
+    e = cudaMemsetAsync(dot, 0, sizeof(double2), st);
+    if (e == cudaSuccess) {
+      const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1184));
+      k_bdot<S><<<dim3(gx, 1), 256, 0, st>>>((const S*)G, Y, n, dot);
+      count_launches(1);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dot, sizeof(double2), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFree(Y);
+  cudaFree(dot);
+  if (res != BEM_OK) return res;
+  if (e != cudaSuccess) return cuda_err(ctx, e, "bem_op_inner");
+  out[0] = h.x;
+  out[1] = h.y;
+  return BEM_OK;
+}
+
+bem_status inner(bem_op* op, int mode, const void* G, const void* X, double* out, cudaStream_t st) {
+  return op->d->prec == BEM_FP64 ? inner_t<double2>(op, mode, G, X, out, st)
+                                 : inner_t<float2>(op, mode, G, X, out, st);
+}
+
 bem_status solve(bem_op* op, const void* B, void* X, double tol, int max_iter, int32_t* iters, double* relres,
                  cudaStream_t st) {
   return op->d->prec == BEM_FP64 ? solve_t<double2>(op, B, X, tol, max_iter, iters, relres, st)
