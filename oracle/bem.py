@@ -45,6 +45,11 @@ KERNEL_SL, KERNEL_DL = "sl", "dl"
 # wave) and dV/dc2 (S wave); integrand dU/dc_a, same columns and quadrature
 KERNEL_SL_DCP, KERNEL_SL_DCS = "sl_dcp", "sl_dcs"
 SL_KINDS = (KERNEL_SL, KERNEL_SL_DCP, KERNEL_SL_DCS)
+# and of the double layer C + K: integrands dT/dc_a, static parts dT0/dc_a,
+# the CPV coefficient differentiated through nu, no free term (C = I/2 at a
+# smooth point does not depend on the speeds; node rows: rigid-body identity)
+KERNEL_DL_DCP, KERNEL_DL_DCS = "dl_dcp", "dl_dcs"
+WAVE = {KERNEL_SL_DCP: "p", KERNEL_SL_DCS: "s", KERNEL_DL_DCP: "p", KERNEL_DL_DCS: "s"}
 
 
 def freqs_bdf2(N: int, dt: float, K: int | None = None) -> np.ndarray:
@@ -154,7 +159,9 @@ def _on_element(geo: Geometry, kind, i, e):
 class Operator:
     """Dense collocation V or C + K at a list of frequencies; with kernel
     KERNEL_SL_DCP / KERNEL_SL_DCS the wave-speed derivative dV/dc1 / dV/dc2
-    of the single layer (same quadrature, integrand kernels.dU_dc)."""
+    of the single layer (same quadrature, integrand kernels.dU_dc), with
+    KERNEL_DL_DCP / KERNEL_DL_DCS d(C + K)/dc1, d(C + K)/dc2 (integrands
+    kernels.dT_dc and dkelvin_T_dc)."""
 
     def __init__(self, xyz, tri, material, rows=ROWS_NODES, kernel=KERNEL_SL):
         self.geo = Geometry(xyz, tri)
@@ -174,10 +181,18 @@ class Operator:
 
     def _TT(self, r, n, s, dynamic=False):
         """Transposed traction kernel T^T (double-layer integrand)."""
-        return np.swapaxes(kernels.T(r, n, s, self.rho, self.lam, self.mu, dynamic), -1, -2)
+        if self.kernel in (KERNEL_DL_DCP, KERNEL_DL_DCS):
+            t = kernels.dT_dc(r, n, s, self.rho, self.lam, self.mu, WAVE[self.kernel], dynamic)
+        else:
+            t = kernels.T(r, n, s, self.rho, self.lam, self.mu, dynamic)
+        return np.swapaxes(t, -1, -2)
 
     def _T0T(self, r, n):
-        return np.swapaxes(kernels.kelvin_T(r, n, self.lam, self.mu), -1, -2)
+        if self.kernel in (KERNEL_DL_DCP, KERNEL_DL_DCS):
+            t = kernels.dkelvin_T_dc(r, n, self.rho, self.lam, self.mu, WAVE[self.kernel])
+        else:
+            t = kernels.kelvin_T(r, n, self.lam, self.mu)
+        return np.swapaxes(t, -1, -2)
 
     # ---- element integrals -------------------------------------------------
     def _elem_points(self, i, e):
@@ -222,10 +237,16 @@ class Operator:
         G = geo.cpv_rh_over_r2(e, x)
         # CPV int T0^T: T0^T_bc = -(1-2nu)(rh_c n_b - n_c rh_b) / (8 pi (1-nu) r^2)
         cpv = -(1.0 - 2.0 * nu) * (np.outer(n, G) - np.outer(G, n)) / (8.0 * math.pi * (1.0 - nu))
+        free = np.eye(3) / 6.0
+        if self.kernel in (KERNEL_DL_DCP, KERNEL_DL_DCS):
+            # d/dnu of -(1-2nu)/(1-nu) is 1/(1-nu)^2; the free term I/2 is fixed
+            dnu = kernels.dnu_dc(self.rho, self.lam, self.mu, WAVE[self.kernel])
+            cpv = dnu * (np.outer(n, G) - np.outer(G, n)) / (8.0 * math.pi * (1.0 - nu) ** 2)
+            free = np.zeros((3, 3))
         for a in range(3):
             out[:, a] = (np.einsum("q,q,kqbc->kbc", w, phi[:, a], Tdyn)
                          + np.einsum("q,q,qbc->bc", w, phi[:, a] - 1.0 / 3.0, T0)[None]
-                         + (cpv / 3.0 + np.eye(3) / 6.0)[None])
+                         + (cpv / 3.0 + free)[None])
         return out
 
     def _regular_groups(self, i, elems):

@@ -34,7 +34,9 @@ Pins: symmetry, conjugate symmetry in s, the static Kelvin limit, the
 Navier residual by finite differences, traction by finite differences of U,
 series/closed-form agreement (tests/test_oracle_kernels.py).  The wave-speed
 derivatives dU/dc1, dU/dc2 (dU_dc) are pinned by finite differences of U in
-c1, c2 and by the derivatives of the Kelvin solution written in c1, c2.
+c1, c2 and by the derivatives of the Kelvin solution written in c1, c2;
+dT/dc1, dT/dc2 (dT_dc) and dT0/dc_a by finite differences of T and of
+kelvin_T, and by their static limit.
 """
 from __future__ import annotations
 
@@ -166,6 +168,98 @@ def dU_dc(rvec, s, rho: float, lam: float, mu: float, wave: str):
     rh = np.broadcast_to(rh, A.shape + (3,))
     eye = np.eye(3)
     return (A[..., None, None] * eye + B[..., None, None] * rh[..., :, None] * rh[..., None, :]) / (4.0 * math.pi * rho)
+
+
+def dcoeffs2_dc(r, s, c1: float, c2: float, wave: str, dynamic: bool = False):
+    """c_a-derivatives (fixed rho) of A, B, A', B' and S3 = A' + B' + 2B/r,
+    the coefficients of the traction kernel, from dcoeffs_dc by d/dr
+    (e = exp(-k r), k = k_a, x = k r, c = c_a):
+
+        wave p: A = -e/(r c^3),         B = (1 + x) e/(r c^3),
+                A' = (1 + x) e/(r^2 c^3),  B' = -(1 + x + x^2) e/(r^2 c^3),
+                S3 = (2 + 2x - x^2) e/(r^2 c^3)
+        wave s: A = (x - 1) e/(r c^3),  B = -(1 + x) e/(r c^3),
+                A' = (1 + x - x^2) e/(r^2 c^3), B' = (1 + x + x^2) e/(r^2 c^3),
+                S3 = 0  (S3 depends on c1 only: -(1 + k1 r) e1/(c1^2 r^2)).
+
+    ``dynamic`` subtracts the s = 0 values (the c-derivatives of the static
+    coefficients), as coeffs does."""
+    r, s = np.broadcast_arrays(np.asarray(r, dtype=np.float64),
+                               np.asarray(s, dtype=np.complex128))
+    c = c1 if wave == "p" else c2
+    x = s * r / c
+    e = np.exp(-x)
+    em = np.expm1(-x) if dynamic else e       # e - 1 when the static part goes
+    f1, f2 = 1.0 / (r * c ** 3), 1.0 / (r * r * c ** 3)
+    if wave == "p":
+        A = -em * f1
+        B = (em + x * e) * f1
+        Ap = (em + x * e) * f2
+        Bp = -(em + (x + x * x) * e) * f2
+        S3 = (2.0 * em + (2.0 * x - x * x) * e) * f2
+    else:
+        A = (x * e - em) * f1
+        B = -(em + x * e) * f1
+        Ap = (em + (x - x * x) * e) * f2
+        Bp = (em + (x + x * x) * e) * f2
+        S3 = np.zeros_like(A)
+    return A, B, Ap, Bp, S3
+
+
+def dT_dc(rvec, n, s, rho: float, lam: float, mu: float, wave: str, dynamic=False):
+    """Derivative of T (same layout as T) with respect to c1 (wave "p") or c2
+    (wave "s") at fixed density.  T's coefficients f1 = c2^2 (A' + B/r),
+    f2 = 2 c2^2 (B' - 2B/r), f3 = (c1^2 - 2 c2^2) S3 + 2 c2^2 B/r are
+    differentiated by the product rule, the A, B, A', B', S3 parts by
+    dcoeffs2_dc.  ``dynamic``: the derivative of T(s) - T0."""
+    c1, c2 = wave_speeds(rho, lam, mu)
+    rvec = np.asarray(rvec, dtype=np.float64)
+    n = np.broadcast_to(np.asarray(n, dtype=np.float64), rvec.shape)
+    r = np.linalg.norm(rvec, axis=-1)
+    rh = rvec / r[..., None]
+    A, B, dA, dB = coeffs(r, s, c1, c2, dynamic)
+    DA, DB, DAp, DBp, DS3 = dcoeffs2_dc(r, s, c1, c2, wave, dynamic)
+    r, rh, n = (np.broadcast_to(a, A.shape + a.shape[r.ndim:]) for a in (r, rh, n))
+    S3 = dA + dB + 2.0 * B / r
+    c1s, c2s = c1 * c1, c2 * c2
+    d1s, d2s = (2.0 * c1, 0.0) if wave == "p" else (0.0, 2.0 * c2)
+    f1 = d2s * (dA + B / r) + c2s * (DAp + DB / r)
+    f2 = 2.0 * d2s * (dB - 2.0 * B / r) + 2.0 * c2s * (DBp - 2.0 * DB / r)
+    f3 = (d1s - 2.0 * d2s) * S3 + (c1s - 2.0 * c2s) * DS3 + 2.0 * d2s * B / r + 2.0 * c2s * DB / r
+    rn = (rh * n).sum(-1)
+    eye = np.eye(3)
+    t = (f1[..., None, None] * (rn[..., None, None] * eye + rh[..., :, None] * n[..., None, :])
+         + (f2 * rn)[..., None, None] * rh[..., :, None] * rh[..., None, :]
+         + f3[..., None, None] * n[..., :, None] * rh[..., None, :])
+    return t / (4.0 * math.pi)
+
+
+def dnu_dc(rho: float, lam: float, mu: float, wave: str) -> float:
+    """d nu / d c_a at fixed rho, nu = (c1^2 - 2 c2^2) / (2 (c1^2 - c2^2)):
+    c1 c2^2 / (c1^2 - c2^2)^2 (wave p), -c1^2 c2 / (c1^2 - c2^2)^2 (wave s)."""
+    c1, c2 = wave_speeds(rho, lam, mu)
+    d = (c1 * c1 - c2 * c2) ** 2
+    return c1 * c2 * c2 / d if wave == "p" else -c1 * c1 * c2 / d
+
+
+def dkelvin_T_dnu(rvec, n, lam: float, mu: float):
+    """d T0 / d nu: with T0 = -[g P + h Q] / (8 pi r^2), g = (1-2nu)/(1-nu),
+    h = 1/(1-nu), P = rh.n I + rh n^T - n rh^T, Q = 3 rh.n rh rh^T:
+    -[Q - P] / (8 pi (1-nu)^2 r^2)."""
+    nu = lam / (2.0 * (lam + mu))
+    rvec = np.asarray(rvec, dtype=np.float64)
+    n = np.broadcast_to(np.asarray(n, dtype=np.float64), rvec.shape)
+    r = np.linalg.norm(rvec, axis=-1)
+    rh = rvec / r[..., None]
+    rn = (rh * n).sum(-1)
+    P = (rn[..., None, None] * np.eye(3) + rh[..., :, None] * n[..., None, :] - n[..., :, None] * rh[..., None, :])
+    Q = 3.0 * rn[..., None, None] * rh[..., :, None] * rh[..., None, :]
+    return -(Q - P) / (8.0 * math.pi * (1.0 - nu) ** 2 * (r ** 2)[..., None, None])
+
+
+def dkelvin_T_dc(rvec, n, rho: float, lam: float, mu: float, wave: str):
+    """d T0 / d c_a at fixed rho (T0 depends on the speeds through nu only)."""
+    return dnu_dc(rho, lam, mu, wave) * dkelvin_T_dnu(rvec, n, lam, mu)
 
 
 def lame_from_speeds(rho: float, c1: float, c2: float) -> tuple[float, float]:

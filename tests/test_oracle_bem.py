@@ -149,3 +149,29 @@ def test_speed_derivative_operator_by_fd(rows, kern, wave):
     d = op.block(rws, np.arange(op.n_cols), s)
     assert op.n_cols == len(tri)
     np.testing.assert_allclose(d, fd, rtol=0, atol=1e-7 * np.abs(fd).max())
+
+
+@pytest.mark.parametrize("rows", [bem.ROWS_CENTROIDS, bem.ROWS_NODES])
+@pytest.mark.parametrize("kern,wave", [(bem.KERNEL_DL_DCP, "p"), (bem.KERNEL_DL_DCS, "s")])
+def test_dl_speed_derivative_operator_by_fd(rows, kern, wave):
+    """d(C + K)/dc_a (rigid-body diagonal or CPV + free term, Duffy
+    remainders, near and far elements) against central differences of the
+    double layer in c_a at fixed density."""
+    xyz, tri = syn.icosphere(1)
+    s = bem.freqs_bdf2(16, 2e-5, 16)[[0, 9]]
+    rho = syn.STEEL[0]
+    c1, c2 = kernels.wave_speeds(*syn.STEEL)
+    c = c1 if wave == "p" else c2
+    h = 1e-4 * c
+    rws = np.array([0, 5, 17])
+
+    def k(dc):
+        cc1, cc2 = (c1 + dc, c2) if wave == "p" else (c1, c2 + dc)
+        mat = (rho,) + kernels.lame_from_speeds(rho, cc1, cc2)
+        op = bem.Operator(xyz, tri, mat, rows=rows, kernel=bem.KERNEL_DL)
+        return op.block(rws, np.arange(op.n_cols), s)
+    fd = (-k(2 * h) + 8 * k(h) - 8 * k(-h) + k(-2 * h)) / (12 * h)
+    op = bem.Operator(xyz, tri, syn.STEEL, rows=rows, kernel=kern)
+    d = op.block(rws, np.arange(op.n_cols), s)
+    assert op.n_cols == len(xyz)
+    np.testing.assert_allclose(d, fd, rtol=0, atol=1e-7 * np.abs(fd).max())

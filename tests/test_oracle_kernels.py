@@ -190,3 +190,46 @@ def test_speed_derivative_kelvin_limit(mat):
     ds = -(I + P) / (4 * math.pi * rho * rr[:, None, None] * c2 ** 3)
     np.testing.assert_allclose(K.dU_dc(r, s, rho, lam, mu, "p"), dp, rtol=0, atol=1e-8 * np.abs(dp).max())
     np.testing.assert_allclose(K.dU_dc(r, s, rho, lam, mu, "s"), ds, rtol=0, atol=1e-8 * np.abs(ds).max())
+
+
+@pytest.mark.parametrize("mat", MATS)
+@pytest.mark.parametrize("wave", ["p", "s"])
+@pytest.mark.parametrize("zabs", [0.3, 2.5, 30.0])
+def test_traction_speed_derivative_by_fd(mat, wave, zabs):
+    """dT/dc_a, d(T - T0)/dc_a and dT0/dc_a against 4th-order central
+    differences of T, T - T0 and kelvin_T in c_a (rho fixed)."""
+    c1, c2 = _speeds(mat)
+    rng = np.random.default_rng(13)
+    r = rng.normal(size=(6, 3))
+    n = rng.normal(size=(6, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    s = zabs * c2 / np.linalg.norm(r, axis=1).mean() * np.exp(0.6j)
+    c = c1 if wave == "p" else c2
+    h = 1e-4 * c
+
+    def fd(f):
+        return (-f(2 * h) + 8 * f(h) - 8 * f(-h) + f(-2 * h)) / (12 * h)
+    m = lambda dc: _speed_perturbed(mat, wave, dc)                  # noqa: E731
+    for dyn in (False, True):
+        want = fd(lambda dc: K.T(r, n, s, *m(dc), dynamic=dyn))
+        got = K.dT_dc(r, n, s, *mat, wave, dynamic=dyn)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-8 * np.abs(want).max())
+    want = fd(lambda dc: K.kelvin_T(r, n, *m(dc)[1:]))
+    got = K.dkelvin_T_dc(r, n, *mat, wave)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-8 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("mat", MATS)
+@pytest.mark.parametrize("wave", ["p", "s"])
+def test_traction_speed_derivative_static_limit(mat, wave):
+    """s -> 0: dT/dc_a tends to dT0/dc_a = (dnu/dc_a) dT0/dnu, and the
+    dynamic part vanishes."""
+    c2 = _speeds(mat)[1]
+    rng = np.random.default_rng(17)
+    r = rng.normal(size=(8, 3))
+    n = rng.normal(size=(8, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    s = 1e-7 * c2 / np.linalg.norm(r, axis=1).max() * np.exp(0.2j)
+    d0 = K.dkelvin_T_dc(r, n, *mat, wave)
+    np.testing.assert_allclose(K.dT_dc(r, n, s, *mat, wave), d0, rtol=0, atol=1e-6 * np.abs(d0).max())
+    assert np.abs(K.dT_dc(r, n, s, *mat, wave, dynamic=True)).max() < 1e-6 * np.abs(d0).max()
