@@ -70,9 +70,20 @@ typedef enum { BEM_ROWS_CENTROIDS = 0, BEM_ROWS_NODES = 1 } bem_rows;
  * dU/dc_a = [dA/dc_a I + dB/dc_a rh rh^T] / (4 pi rho) with
  *   dA/dc1 = -e1 / (r c1^3),            dB/dc1 = (1 + k1 r) e1 / (r c1^3),
  *   dA/dc2 = (k2 r - 1) e2 / (r c2^3),  dB/dc2 = -(1 + k2 r) e2 / (r c2^3),
- * k_a = s / c_a, e_a = exp(-k_a r)).  For the wave-speed gradient of a
- * functional of V X (adjoint method). */
-typedef enum { BEM_SL = 0, BEM_DL = 1, BEM_SL_DCP = 2, BEM_SL_DCS = 3 } bem_kernel;
+ * k_a = s / c_a, e_a = exp(-k_a r)).  BEM_DL_DCP / BEM_DL_DCS: the same
+ * derivatives of C + K (columns = nodes): integrand dT/dc_a (product rule on
+ * T's coefficients), static parts dT0/dc_a = (dnu/dc_a) dT0/dnu, the CPV
+ * coefficient differentiated through nu, no free term for centroid rows,
+ * and for node rows the rigid-body diagonal of dT0/dnu.  For the
+ * wave-speed gradient of a functional of C X (adjoint method). */
+typedef enum {
+  BEM_SL = 0,
+  BEM_DL = 1,
+  BEM_SL_DCP = 2,
+  BEM_SL_DCS = 3,
+  BEM_DL_DCP = 4,
+  BEM_DL_DCS = 5
+} bem_kernel;
 /* Batched: Y_k = C(s_k) X_k for all k.  Contracted: y = sum_k C(s_k) X_k,
  * the gCQ history sum of Eq. (3.15). */
 typedef enum { BEM_APPLY_BATCHED = 0, BEM_APPLY_CONTRACTED = 1 } bem_apply_mode;
@@ -160,9 +171,10 @@ bem_status bem_entries(bem_mesh* mesh, int32_t rows, int32_t kernel,
  *  - All calls share the array: calls whose device work overlaps (other
  *    streams, other host threads) race on it and must be serialised by the
  *    caller.  The words used are reset at the start of every call.
- *  - BEM_DL with BEM_ROWS_NODES needs the mesh's rigid-body diagonal, which
- *    is computed (and allocated) by the first bem_entries or bem_op_compress
- *    of that kind on the mesh; without it this call returns BEM_ERR_STATE.
+ *  - BEM_DL (BEM_DL_DCP, BEM_DL_DCS) with BEM_ROWS_NODES needs the mesh's
+ *    rigid-body diagonal (its nu-derivative), which is computed (and
+ *    allocated) by the first bem_entries or bem_op_compress of that kind on
+ *    the mesh; without it this call returns BEM_ERR_STATE.
  *  - Synchronises the stream; an out-of-range request yields a NaN block and
  *    BEM_ERR_ARG naming the first offending request. */
 bem_status bem_entries_noalloc(bem_mesh* mesh, int32_t rows, int32_t kernel,

@@ -31,6 +31,8 @@ BEM_ROWS_CENTROIDS, BEM_ROWS_NODES = 0, 1
 BEM_SL, BEM_DL = 0, 1
 # wave-speed derivatives of the single layer, dV/dc_p and dV/dc_s (fixed density)
 BEM_SL_DCP, BEM_SL_DCS = 2, 3
+# and of the double layer C + K, d(C + K)/dc_p and d(C + K)/dc_s
+BEM_DL_DCP, BEM_DL_DCS = 4, 5
 BEM_APPLY_BATCHED, BEM_APPLY_CONTRACTED = 0, 1
 
 _STATUS = {0: "BEM_OK", 1: "BEM_ERR_ARG", 2: "BEM_ERR_CUDA", 3: "BEM_ERR_OOM", 4: "BEM_ERR_MESH",

@@ -1075,8 +1075,8 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   const int K = ctx->K;
   const int64_t nb = (int64_t)tree->blocks.size();
   auto t_start = std::chrono::steady_clock::now();
-  if (tree->kernel == BEM_DL && tree->rows == BEM_ROWS_NODES) {
-    bem_status s = ensure_rigid_body(mesh, st);
+  if (!kern_sl(tree->kernel) && tree->rows == BEM_ROWS_NODES) {
+    bem_status s = ensure_rigid_body(mesh, st, kern_dc(tree->kernel) != 0);
     if (s != BEM_OK) return s;
   }
   EntryView v = make_view(mesh);

@@ -78,12 +78,27 @@ __device__ __forceinline__ cx<float> cexp_neg(cx<float> z) {
   float m = expf(-z.x);
   return {m * cs, -m * sn};
 }
+// exp(-z) - 1 without cancellation at small |z|:
+// re = expm1(-x) cos y - 2 sin^2(y / 2), im = -exp(-x) sin y
+__device__ __forceinline__ cx<double> cexpm1_neg(cx<double> z) {
+  double sn, cs, sh, ch;
+  sincos(z.y, &sn, &cs);
+  sincos(0.5 * z.y, &sh, &ch);
+  return {expm1(-z.x) * cs - 2.0 * sh * sh, -exp(-z.x) * sn};
+}
+__device__ __forceinline__ cx<float> cexpm1_neg(cx<float> z) {
+  float sn, cs, sh, ch;
+  sincosf(z.y, &sn, &cs);
+  sincosf(0.5f * z.y, &sh, &ch);
+  return {expm1f(-z.x) * cs - 2.f * sh * sh, -expf(-z.x) * sn};
+}
 
 // kernel constants in the compute type
 template <typename R>
 struct KC {
   R c1, c2, c1s, c2s, ic1, ic2, ic2s, inv4pirho, inv4pi, alpha, beta;
   R ic1c, ic2c;   // 1 / c1^3, 1 / c2^3 (wave-speed derivatives)
+  R dnu1, dnu2;   // d nu / d c1, d nu / d c2 at fixed rho
   R ta[kSeriesTerms], tb[kSeriesTerms];
 };
 
@@ -103,6 +118,10 @@ KC<R> make_kc(const Material& m) {
   k.beta = (R)(0.5 * (1.0 / (m.c2 * m.c2) - 1.0 / (m.c1 * m.c1)));
   k.ic1c = (R)(1.0 / (m.c1 * m.c1 * m.c1));
   k.ic2c = (R)(1.0 / (m.c2 * m.c2 * m.c2));
+  // nu = (c1^2 - 2 c2^2) / (2 (c1^2 - c2^2))
+  const double dd = (m.c1 * m.c1 - m.c2 * m.c2) * (m.c1 * m.c1 - m.c2 * m.c2);
+  k.dnu1 = (R)(m.c1 * m.c2 * m.c2 / dd);
+  k.dnu2 = (R)(-m.c1 * m.c1 * m.c2 / dd);
   for (int i = 0; i < kSeriesTerms; ++i) {
     k.ta[i] = (R)m.ta[i];
     k.tb[i] = (R)m.tb[i];
@@ -252,6 +271,111 @@ __device__ __forceinline__ void acc_dU(const KC<R>& k, R wq, R dx, R dy, R dz, c
   SB[5] = SB[5] + (h[2] * h[2]) * wb;
 }
 
+// c_a-derivatives of A, B, A', B' and S3 = A' + B' + 2B/r (traction kernel),
+// x = k_a r, e = exp(-x), em = e (DYN: e - 1, the static parts removed):
+//   c1: A = -em/(r c^3), B = (em + x e)/(r c^3), A' = (em + x e)/(r^2 c^3),
+//       B' = -(em + (x + x^2) e)/(r^2 c^3), S3 = (2 em + (2x - x^2) e)/(r^2 c^3)
+//   c2: A = (x e - em)/(r c^3), B = -(em + x e)/(r c^3),
+//       A' = (em + (x - x^2) e)/(r^2 c^3), B' = (em + (x + x^2) e)/(r^2 c^3), S3 = 0
+template <typename R, int DC>
+__device__ __forceinline__ void dcoeffs2_from(const KC<R>& k, R r, cx<R> x, cx<R> e, cx<R> em, cx<R>& A, cx<R>& B,
+                                              cx<R>& Ap, cx<R>& Bp, cx<R>& S3) {
+  const R f1 = (DC == 1 ? k.ic1c : k.ic2c) / r, f2 = f1 / r;
+  const cx<R> xe = x * e, x2e = x * xe;
+  if (DC == 1) {
+    A = mk<R>(-f1 * em.x, -f1 * em.y);
+    B = f1 * (em + xe);
+    Ap = f2 * (em + xe);
+    const cx<R> t = em + xe + x2e;
+    Bp = mk<R>(-f2 * t.x, -f2 * t.y);
+    S3 = f2 * (R(2) * em + R(2) * xe - x2e);
+  } else {
+    A = f1 * (xe - em);
+    const cx<R> t = em + xe;
+    B = mk<R>(-f1 * t.x, -f1 * t.y);
+    Ap = f2 * (em + xe - x2e);
+    Bp = f2 * (em + xe + x2e);
+    S3 = mk<R>(R(0), R(0));
+  }
+}
+
+// T^T accumulation from the three coefficient functions (already weighted):
+// [a*3+b] = T_ba = f1 (rn d_ab + h_b n_a) + f2 rn h_a h_b + f3 n_b h_a
+template <typename R>
+__device__ __forceinline__ void acc_T_tensor(const R* h, const R* n, cx<R> f1, cx<R> f2, cx<R> f3, cx<R>* acc) {
+  R rn = h[0] * n[0] + h[1] * n[1] + h[2] * n[2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      R c1v = (a == b ? rn : R(0)) + h[b] * n[a];
+      R c2v = rn * h[a] * h[b];
+      R c3v = n[b] * h[a];
+      acc[3 * a + b] = acc[3 * a + b] + c1v * f1 + c2v * f2 + c3v * f3;
+    }
+}
+
+// w dT^T/dc_a: product rule on f1 = c2^2 (A' + B/r), f2 = 2 c2^2 (B' - 2B/r),
+// f3 = (c1^2 - 2 c2^2) S3 + 2 c2^2 B/r (B, dA, dB, S3: T's coefficients;
+// DB, DAp, DBp, DS3: their c_a-derivatives)
+template <typename R, int DC>
+__device__ __forceinline__ void acc_dTT_from(const KC<R>& k, R wq, R r, const R* h, const R* n, cx<R> B, cx<R> dA,
+                                             cx<R> dB, cx<R> S3, cx<R> DB, cx<R> DAp, cx<R> DBp, cx<R> DS3,
+                                             cx<R>* acc) {
+  const R ir = R(1) / r, w = wq * k.inv4pi;
+  const R d1s = DC == 1 ? R(2) * k.c1 : R(0), d2s = DC == 2 ? R(2) * k.c2 : R(0);
+  const cx<R> Bir = ir * B, DBir = ir * DB;
+  const cx<R> f1 = w * (d2s * (dA + Bir) + k.c2s * (DAp + DBir));
+  const cx<R> f2 = (R(2) * w) * (d2s * (dB - R(2) * Bir) + k.c2s * (DBp - R(2) * DBir));
+  const cx<R> f3 = w * ((d1s - R(2) * d2s) * S3 + (k.c1s - R(2) * k.c2s) * DS3 + (R(2) * d2s) * Bir +
+                        (R(2) * k.c2s) * DBir);
+  acc_T_tensor<R>(h, n, f1, f2, f3, acc);
+}
+
+// accumulate w dT^T/dc_a(d, n); DYN: of T - T0
+template <typename R, bool DYN, int DC>
+__device__ __forceinline__ void acc_dTT(const KC<R>& k, R wq, R dx, R dy, R dz, const R* n, cx<R> s, cx<R> is2,
+                                        cx<R>* acc) {
+  R r = sqrt(dx * dx + dy * dy + dz * dz);
+  R ir = R(1) / r;
+  R h[3] = {dx * ir, dy * ir, dz * ir};
+  cx<R> A, B, dA, dB, S3;
+  kernel_coeffs<R, true, DYN>(k, r, s, is2, A, B, dA, dB, S3);
+  const R ic = DC == 1 ? k.ic1 : k.ic2;
+  const cx<R> x = mk<R>(s.x * r * ic, s.y * r * ic);
+  const cx<R> e = cexp_neg(x);
+  cx<R> DA, DB, DAp, DBp, DS3;
+  dcoeffs2_from<R, DC>(k, r, x, e, DYN ? cexpm1_neg(x) : e, DA, DB, DAp, DBp, DS3);
+  acc_dTT_from<R, DC>(k, wq, r, h, n, B, dA, dB, S3, DB, DAp, DBp, DS3, acc);
+}
+
+// w dT0^T/dnu (real): dT0/dnu = -[Q - P] / (8 pi (1-nu)^2 r^2) with
+// P = rn I + rh n^T - n rh^T, Q = 3 rn rh rh^T; [a*3+b] = (dT0/dnu)_ba
+template <typename R>
+__device__ __forceinline__ void acc_dT0T_dnu(R nu, R wq, R dx, R dy, R dz, const R* n, R* acc) {
+  R r2 = dx * dx + dy * dy + dz * dz;
+  R ir = R(1) / sqrt(r2);
+  R h[3] = {dx * ir, dy * ir, dz * ir};
+  R rn = h[0] * n[0] + h[1] * n[1] + h[2] * n[2];
+  R f = -wq / (R(8.0 * M_PI) * (R(1) - nu) * (R(1) - nu) * r2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      R v = R(3) * rn * h[a] * h[b] - ((a == b ? rn : R(0)) + h[b] * n[a] - n[b] * h[a]);
+      acc[3 * a + b] += f * v;
+    }
+}
+
+// the double-layer integrand T^T (DC = 0) or dT^T/dc_a (DC = 1, 2)
+template <typename R, bool DYN, int DC>
+__device__ __forceinline__ void acc_dl(const KC<R>& k, R wq, R dx, R dy, R dz, const R* n, cx<R> s, cx<R> is2,
+                                       cx<R>* acc);
+
+// its static part T0^T (DC = 0) or dT0^T/dc_a = (dnu/dc_a) dT0^T/dnu
+template <typename R, int DC>
+__device__ __forceinline__ void acc_dl0(const KC<R>& k, R nu, R wq, R dx, R dy, R dz, const R* n, R* acc);
+
 // the single-layer integrand: U (DC = 0) or dU/dc_a (DC = 1, 2)
 template <typename R, int DC>
 __device__ __forceinline__ void acc_sl(const KC<R>& k, R wq, R dx, R dy, R dz, cx<R> s, cx<R> is2, cx<R>& SA,
@@ -333,6 +457,15 @@ __device__ __forceinline__ void acc_TT(const KC<R>& k, R wq, R dx, R dy, R dz, c
   acc_TT_from<R>(k, wq, r, h, n, A, B, dA, dB, S3, acc);
 }
 
+template <typename R, bool DYN, int DC>
+__device__ __forceinline__ void acc_dl(const KC<R>& k, R wq, R dx, R dy, R dz, const R* n, cx<R> s, cx<R> is2,
+                                       cx<R>* acc) {
+  if constexpr (DC == 0)
+    acc_TT<R, DYN>(k, wq, dx, dy, dz, n, s, is2, acc);
+  else
+    acc_dTT<R, DYN, DC>(k, wq, dx, dy, dz, n, s, is2, acc);
+}
+
 // static Kelvin T0^T (real), [a*3+b] = T0_ba
 template <typename R>
 __device__ __forceinline__ void acc_T0T(R nu, R wq, R dx, R dy, R dz, const R* n, R* acc) {
@@ -350,6 +483,14 @@ __device__ __forceinline__ void acc_T0T(R nu, R wq, R dx, R dy, R dz, const R* n
       R v = rn * ((a == b ? a12 : R(0)) + R(3) * h[a] * h[b]) + a12 * (h[b] * n[a] - n[b] * h[a]);
       acc[3 * a + b] += f * v;
     }
+}
+
+template <typename R, int DC>
+__device__ __forceinline__ void acc_dl0(const KC<R>& k, R nu, R wq, R dx, R dy, R dz, const R* n, R* acc) {
+  if constexpr (DC == 0)
+    acc_T0T<R>(nu, wq, dx, dy, dz, n, acc);
+  else
+    acc_dT0T_dnu<R>(nu, wq * (DC == 1 ? k.dnu1 : k.dnu2), dx, dy, dz, n, acc);
 }
 
 __device__ __forceinline__ int rule_index(double dist, double h) {
@@ -370,6 +511,7 @@ struct EntryView {
   const int32_t* ne_elem;
   const int32_t* ne_loc;
   const double* rb;          // n_nodes x 9 (node rows, double layer) or null
+  const double* rb_dnu;      // its derivative in nu (wave-speed derivative operators) or null
   const double2* s;          // K
   const double2* inv_s2;     // K
   const float4* sw;          // [K][2] s_k / c_a float-float (MIXED path)
@@ -520,7 +662,10 @@ __device__ void cpv_rh_r2(const ElemGeo& g, const double* x, double* G) {
 // (C+K)[i, j](s) = sum_{e ni j} int_e T^T(x_i, y, s) phi_j(y) dy with the
 // singular treatments (node rows: Duffy + rigid-body static diagonal;
 // centroid rows: free term I/6, CPV of the static part, Duffy remainders).
-template <typename R, int ROWS>
+// DC = 1, 2: the wave-speed derivative d(C + K)/dc_a (integrands dT/dc_a and
+// dT0/dc_a, CPV coefficient through nu, no free term, rigid-body diagonal
+// of dT0/dnu times dnu/dc_a).
+template <typename R, int ROWS, int DC>
 __device__ void entry_dl(const EntryView& v, int i, int j, cx<double> s, cx<double> is2, cx<double>* out) {
   const double* x = row_point<ROWS>(v, i);
   cx<double> acc[9];
@@ -560,8 +705,8 @@ __device__ void entry_dl(const EntryView& v, int i, int j, cx<double> s, cx<doub
           float xi = (float)c_rule[3 * q], et = (float)c_rule[3 * q + 1];
           float phi = a == 0 ? 1.f - xi - et : (a == 1 ? xi : et);
           float wq = (float)c_rule[3 * q + 2] * ar * phi;
-          acc_TT<float, false>(v.kf, wq, f0[0] + xi * f1[0] + et * f2[0], f0[1] + xi * f1[1] + et * f2[1],
-                               f0[2] + xi * f1[2] + et * f2[2], nf, sf, isf, af);
+          acc_dl<float, false, DC>(v.kf, wq, f0[0] + xi * f1[0] + et * f2[0], f0[1] + xi * f1[1] + et * f2[1],
+                                   f0[2] + xi * f1[2] + et * f2[2], nf, sf, isf, af);
         }
 #pragma unroll
         for (int c = 0; c < 9; ++c) acc[c] = acc[c] + mk<double>(af[c].x, af[c].y);
@@ -570,8 +715,9 @@ __device__ void entry_dl(const EntryView& v, int i, int j, cx<double> s, cx<doub
           double xi = c_rule[3 * q], et = c_rule[3 * q + 1];
           double phi = a == 0 ? 1.0 - xi - et : (a == 1 ? xi : et);
           double wq = c_rule[3 * q + 2] * g.area2 * phi;
-          acc_TT<double, false>(v.kd, wq, d0[0] + xi * g.e1[0] + et * g.e2[0], d0[1] + xi * g.e1[1] + et * g.e2[1],
-                                d0[2] + xi * g.e1[2] + et * g.e2[2], n, s, is2, acc);
+          acc_dl<double, false, DC>(v.kd, wq, d0[0] + xi * g.e1[0] + et * g.e2[0],
+                                    d0[1] + xi * g.e1[1] + et * g.e2[1], d0[2] + xi * g.e1[2] + et * g.e2[2], n, s,
+                                    is2, acc);
         }
       }
       continue;
@@ -624,12 +770,12 @@ __device__ void entry_dl(const EntryView& v, int i, int j, cx<double> s, cx<doub
             phi = (a == apex) ? 1.0 - u : (a == lb ? lam_b : lam_c);
           }
           if (apex == 3) {
-            acc_TT<double, true>(v.kd, wq * phi, d0, d1, d2, n, s, is2, acc);
-            acc_T0T(v.nu, wq * (phi - 1.0 / 3.0), d0, d1, d2, n, acc0);
+            acc_dl<double, true, DC>(v.kd, wq * phi, d0, d1, d2, n, s, is2, acc);
+            acc_dl0<double, DC>(v.kd, v.nu, wq * (phi - 1.0 / 3.0), d0, d1, d2, n, acc0);
           } else if (a == apex) {
-            acc_TT<double, true>(v.kd, wq * phi, d0, d1, d2, n, s, is2, acc);
+            acc_dl<double, true, DC>(v.kd, wq * phi, d0, d1, d2, n, s, is2, acc);
           } else {
-            acc_TT<double, false>(v.kd, wq * phi, d0, d1, d2, n, s, is2, acc);
+            acc_dl<double, false, DC>(v.kd, wq * phi, d0, d1, d2, n, s, is2, acc);
           }
         }
       }
@@ -637,15 +783,23 @@ __device__ void entry_dl(const EntryView& v, int i, int j, cx<double> s, cx<doub
     if (apex == 3) {
       // free term C = I/2 at the centroid: I/6 per vertex; CPV of T0^T / 3:
       // CPV T0^T_ab = -(1-2nu)(G_b n_a - n_b G_a) / (8 pi (1-nu))
+      // (DC: d/dnu of -(1-2nu)/(1-nu) is 1/(1-nu)^2; the free term is fixed)
       double G[3];
       cpv_rh_r2(g, x, G);
-      double f = -(1.0 - 2.0 * v.nu) / (8.0 * M_PI * (1.0 - v.nu)) / 3.0;
+      const double f = DC == 0 ? -(1.0 - 2.0 * v.nu) / (8.0 * M_PI * (1.0 - v.nu)) / 3.0
+                               : (DC == 1 ? v.kd.dnu1 : v.kd.dnu2) / (8.0 * M_PI * (1.0 - v.nu) * (1.0 - v.nu)) / 3.0;
+      const double fr = DC == 0 ? 1.0 / 6.0 : 0.0;
       for (int aa = 0; aa < 3; ++aa)
-        for (int bb = 0; bb < 3; ++bb) acc0[3 * aa + bb] += f * (G[bb] * n[aa] - n[bb] * G[aa]) + (aa == bb ? 1.0 / 6.0 : 0.0);
+        for (int bb = 0; bb < 3; ++bb) acc0[3 * aa + bb] += f * (G[bb] * n[aa] - n[bb] * G[aa]) + (aa == bb ? fr : 0.0);
     }
   }
-  if (ROWS == BEM_ROWS_NODES && j == i && v.rb) {
-    for (int c = 0; c < 9; ++c) acc0[c] += v.rb[9 * (int64_t)i + c];
+  if (ROWS == BEM_ROWS_NODES && j == i) {
+    if (DC == 0 && v.rb) {
+      for (int c = 0; c < 9; ++c) acc0[c] += v.rb[9 * (int64_t)i + c];
+    } else if (DC != 0 && v.rb_dnu) {
+      const double dn = DC == 1 ? v.kd.dnu1 : v.kd.dnu2;
+      for (int c = 0; c < 9; ++c) acc0[c] += dn * v.rb_dnu[9 * (int64_t)i + c];
+    }
   }
 #pragma unroll
   for (int c = 0; c < 9; ++c) out[c] = {acc[c].x + acc0[c], acc[c].y};
@@ -670,8 +824,12 @@ __device__ void entry_dl(const EntryView& v, int i, int j, cx<double> s, cx<doub
       GCQ_DISPATCH_ROWS(BEM_DL, rows, LAUNCH);                                                   \
     else if ((kernel) == BEM_SL_DCP)                                                             \
       GCQ_DISPATCH_ROWS(BEM_SL_DCP, rows, LAUNCH);                                               \
-    else                                                                                         \
+    else if ((kernel) == BEM_SL_DCS)                                                             \
       GCQ_DISPATCH_ROWS(BEM_SL_DCS, rows, LAUNCH);                                               \
+    else if ((kernel) == BEM_DL_DCP)                                                             \
+      GCQ_DISPATCH_ROWS(BEM_DL_DCP, rows, LAUNCH);                                               \
+    else                                                                                         \
+      GCQ_DISPATCH_ROWS(BEM_DL_DCS, rows, LAUNCH);                                               \
   } while (0)
 
 }  // namespace gcq

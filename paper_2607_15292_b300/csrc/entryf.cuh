@@ -371,7 +371,8 @@ __device__ void entry_sl_f(const EntryView& v, int i, int e, cx<float> s, cx<flo
 }
 
 // ---- double layer (C + K)[i, j] partial sum ---------------------------------
-template <int ROWS>
+// (DC = 1, 2: the wave-speed derivative d(C + K)/dc_a)
+template <int ROWS, int DC>
 __device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<float> is2, int kf, int lane, int nl,
                            float* out18) {
   const double* x = row_point<ROWS>(v, i);
@@ -413,7 +414,16 @@ __device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<flo
         const float hh[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
         cx<float> A, Bc, dA, dB, S3;
         coeffs_ref<true>(v.kf, r, dr, s, is2, use, E0, w, A, Bc, dA, dB, S3);
-        acc_TT_from<float>(v.kf, wq, r, hh, nf, A, Bc, dA, dB, S3, A9);
+        if constexpr (DC == 0) {
+          acc_TT_from<float>(v.kf, wq, r, hh, nf, A, Bc, dA, dB, S3, A9);
+        } else {
+          const cx<float> wa = w[DC - 1];
+          const cx<float> xr = {wa.x * r, wa.y * r};
+          const cx<float> ea = use ? E0[DC - 1] * cexp_neg(cx<float>{wa.x * dr, wa.y * dr}) : cexp_neg(xr);
+          cx<float> DA, DB, DAp, DBp, DS3;
+          dcoeffs2_from<float, DC>(v.kf, r, xr, ea, ea, DA, DB, DAp, DBp, DS3);
+          acc_dTT_from<float, DC>(v.kf, wq, r, hh, nf, Bc, dA, dB, S3, DB, DAp, DBp, DS3, A9);
+        }
         acc.tick();
       }
       continue;
@@ -450,27 +460,36 @@ __device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<flo
       else
         phi = (a == apex) ? 1.f - u : (a == lb ? lam_b : lam_c);
       if (apex == 3) {
-        acc_TT<float, true>(v.kf, wq * phi, d0, d1, d2, f.n, s, is2, A9);
-        acc_T0T<float>(nu, wq * (phi - 1.f / 3.f), d0, d1, d2, f.n, st0);
+        acc_dl<float, true, DC>(v.kf, wq * phi, d0, d1, d2, f.n, s, is2, A9);
+        acc_dl0<float, DC>(v.kf, nu, wq * (phi - 1.f / 3.f), d0, d1, d2, f.n, st0);
       } else if (a == apex) {
-        acc_TT<float, true>(v.kf, wq * phi, d0, d1, d2, f.n, s, is2, A9);
+        acc_dl<float, true, DC>(v.kf, wq * phi, d0, d1, d2, f.n, s, is2, A9);
       } else {
-        acc_TT<float, false>(v.kf, wq * phi, d0, d1, d2, f.n, s, is2, A9);
+        acc_dl<float, false, DC>(v.kf, wq * phi, d0, d1, d2, f.n, s, is2, A9);
       }
       acc.tick();
     }
     if (apex == 3 && lane == 0) {
       float G[3];
       cpv_rh_r2_f(f.e1, f.e2, xr, G);
-      const float fc = -(1.f - 2.f * nu) / (8.f * (float)M_PI * (1.f - nu)) / 3.f;
+      // (DC: d/dnu of -(1-2nu)/(1-nu) is 1/(1-nu)^2; the free term is fixed)
+      const float fc = DC == 0 ? -(1.f - 2.f * nu) / (8.f * (float)M_PI * (1.f - nu)) / 3.f
+                               : (DC == 1 ? v.kf.dnu1 : v.kf.dnu2) / (8.f * (float)M_PI * (1.f - nu) * (1.f - nu)) / 3.f;
+      const float fr = DC == 0 ? 1.f / 6.f : 0.f;
       for (int aa = 0; aa < 3; ++aa)
         for (int bb = 0; bb < 3; ++bb)
-          st0[3 * aa + bb] += fc * (G[bb] * f.n[aa] - f.n[bb] * G[aa]) + (aa == bb ? 1.f / 6.f : 0.f);
+          st0[3 * aa + bb] += fc * (G[bb] * f.n[aa] - f.n[bb] * G[aa]) + (aa == bb ? fr : 0.f);
     }
   }
   acc.flush();
-  if (ROWS == BEM_ROWS_NODES && j == i && v.rb && lane == 0)
-    for (int c = 0; c < 9; ++c) st0[c] += (float)v.rb[9 * (int64_t)i + c];
+  if (ROWS == BEM_ROWS_NODES && j == i && lane == 0) {
+    if (DC == 0 && v.rb) {
+      for (int c = 0; c < 9; ++c) st0[c] += (float)v.rb[9 * (int64_t)i + c];
+    } else if (DC != 0 && v.rb_dnu) {
+      const double dn = DC == 1 ? v.kd.dnu1 : v.kd.dnu2;
+      for (int c = 0; c < 9; ++c) st0[c] += (float)(dn * v.rb_dnu[9 * (int64_t)i + c]);
+    }
+  }
   for (int c = 0; c < 9; ++c) {
     acc.add_const(2 * c, st0[c]);
     out18[2 * c] = acc.s[2 * c];
@@ -505,7 +524,7 @@ __device__ __forceinline__ void entry_f(const EntryView& v, int i, int j, cx<flo
   if constexpr (kern_sl(KERN))
     entry_sl_f<ROWS, kern_dc(KERN)>(v, i, j, s, is2, kf, lane, nl, out18);
   else
-    entry_dl_f<ROWS>(v, i, j, s, is2, kf, lane, nl, out18);
+    entry_dl_f<ROWS, kern_dc(KERN)>(v, i, j, s, is2, kf, lane, nl, out18);
 }
 
 // warp-cooperative evaluation: every lane of the warp calls this with the
@@ -534,7 +553,7 @@ __device__ __forceinline__ void entry(const EntryView& v, int i, int j, int kf, 
     if constexpr (kern_sl(KERN))
       entry_sl<double, ROWS, kern_dc(KERN)>(v, i, j, s, is2, out);
     else
-      entry_dl<double, ROWS>(v, i, j, s, is2, out);
+      entry_dl<double, ROWS, kern_dc(KERN)>(v, i, j, s, is2, out);
   }
 }
 

@@ -71,6 +71,7 @@ static EntryView make_view(const bem_mesh* m) {
   v.ne_elem = m->d_ne_elem;
   v.ne_loc = m->d_ne_loc;
   v.rb = m->d_rb;
+  v.rb_dnu = m->d_rb_dnu;
   v.s = m->ctx->d_s;
   v.inv_s2 = m->ctx->d_inv_s2;
   v.sw = m->ctx->d_sw;
@@ -159,6 +160,8 @@ __global__ void k_entries_req(EntryView v, const int32_t* __restrict__ req, int6
 // rigid-body static diagonal of node rows: RB[i] = -sum_{j != i} K_0[i, j]
 // = -sum_e int_e T0^T(x_i, y) (1 - [i in e] phi_i(y)) dy   (one CTA per row)
 // ---------------------------------------------------------------------------
+// DNU: the same sum for dT0/dnu (wave-speed derivative operators)
+template <bool DNU>
 __global__ void k_rigid_body(EntryView v, double* __restrict__ rb) {
   const int i = blockIdx.x;
   const double* x = v.nodes + 3 * (int64_t)i;
@@ -188,7 +191,10 @@ __global__ void k_rigid_body(EntryView v, double* __restrict__ rb) {
           double d1 = u * (ba[1] + vv * cb[1]);
           double d2 = u * (ba[2] + vv * cb[2]);
           // weight (1 - phi_i) = u at the Duffy point
-          acc_T0T(v.nu, wu * wv * g.area2 * u * u, d0, d1, d2, n, acc);
+          if (DNU)
+            acc_dT0T_dnu(v.nu, wu * wv * g.area2 * u * u, d0, d1, d2, n, acc);
+          else
+            acc_T0T(v.nu, wu * wv * g.area2 * u * u, d0, d1, d2, n, acc);
         }
       }
     } else {
@@ -198,8 +204,12 @@ __global__ void k_rigid_body(EntryView v, double* __restrict__ rb) {
       double d0[3] = {g.p0[0] - x[0], g.p0[1] - x[1], g.p0[2] - x[2]};
       for (int q = rule_offset(ri); q < rule_offset(ri + 1); ++q) {
         double xi = c_rule[3 * q], et = c_rule[3 * q + 1], wq = c_rule[3 * q + 2] * g.area2;
-        acc_T0T(v.nu, wq, d0[0] + xi * g.e1[0] + et * g.e2[0], d0[1] + xi * g.e1[1] + et * g.e2[1],
-                d0[2] + xi * g.e1[2] + et * g.e2[2], n, acc);
+        const double dx = d0[0] + xi * g.e1[0] + et * g.e2[0], dy = d0[1] + xi * g.e1[1] + et * g.e2[1],
+                     dz = d0[2] + xi * g.e1[2] + et * g.e2[2];
+        if (DNU)
+          acc_dT0T_dnu(v.nu, wq, dx, dy, dz, n, acc);
+        else
+          acc_T0T(v.nu, wq, dx, dy, dz, n, acc);
       }
     }
   }
@@ -215,12 +225,16 @@ __global__ void k_rigid_body(EntryView v, double* __restrict__ rb) {
   if (threadIdx.x < 9) rb[9 * (int64_t)i + threadIdx.x] = -red[threadIdx.x][0];
 }
 
-bem_status ensure_rigid_body(bem_mesh* m, cudaStream_t st) {
-  if (m->d_rb) return BEM_OK;
+bem_status ensure_rigid_body(bem_mesh* m, cudaStream_t st, bool dnu) {
+  double*& rb = dnu ? m->d_rb_dnu : m->d_rb;
+  if (rb) return BEM_OK;
   bem_ctx* ctx = m->ctx;
-  GCQ_CUDA(ctx, cudaMalloc(&m->d_rb, sizeof(double) * 9 * m->n_nodes));
+  GCQ_CUDA(ctx, cudaMalloc(&rb, sizeof(double) * 9 * m->n_nodes));
   EntryView v = make_view(m);
-  k_rigid_body<<<(unsigned)m->n_nodes, 256, 0, st>>>(v, m->d_rb);
+  if (dnu)
+    k_rigid_body<true><<<(unsigned)m->n_nodes, 256, 0, st>>>(v, rb);
+  else
+    k_rigid_body<false><<<(unsigned)m->n_nodes, 256, 0, st>>>(v, rb);
   GCQ_CUDA(ctx, cudaGetLastError());
   count_launches(1);
   return BEM_OK;
@@ -229,8 +243,8 @@ bem_status ensure_rigid_body(bem_mesh* m, cudaStream_t st) {
 bem_status launch_entries(bem_mesh* m, int rows, int kernel, const int32_t* req, int64_t n, void* out, int* d_flag,
                           cudaStream_t st) {
   bem_ctx* ctx = m->ctx;
-  if (kernel == BEM_DL && rows == BEM_ROWS_NODES) {
-    bem_status s = ensure_rigid_body(m, st);
+  if (!kern_sl(kernel) && rows == BEM_ROWS_NODES) {
+    bem_status s = ensure_rigid_body(m, st, kern_dc(kernel) != 0);
     if (s != BEM_OK) return s;
   }
   EntryView v = make_view(m);
@@ -321,10 +335,10 @@ extern "C" bem_status bem_entries_noalloc(bem_mesh* mesh, int32_t rows, int32_t 
   if (ctx->device < 0) return set_err_c(ctx, BEM_ERR_STATE, "bem_entries_noalloc: host-only context (device -1)");
   if (!ctx->has_material) return set_err_c(ctx, BEM_ERR_STATE, "bem_entries_noalloc: material not set");
   if (ctx->K < 1) return set_err_c(ctx, BEM_ERR_STATE, "bem_entries_noalloc: frequencies not set");
-  if (kernel == BEM_DL && rows == BEM_ROWS_NODES && !mesh->d_rb)
+  if (!kern_sl(kernel) && rows == BEM_ROWS_NODES && !(kern_dc(kernel) ? mesh->d_rb_dnu : mesh->d_rb))
     return set_err_c(ctx, BEM_ERR_STATE,
                      "bem_entries_noalloc: rigid-body diagonal not prepared; call bem_entries or bem_op_compress "
-                     "once for this mesh with BEM_DL and BEM_ROWS_NODES first");
+                     "once for this mesh with this kernel and BEM_ROWS_NODES first");
   if (n == 0) return BEM_OK;
   GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
   unsigned int* slots = nullptr;

@@ -514,6 +514,7 @@ static void mesh_free(bem_mesh* m) {
   cudaFree(m->d_ne_elem);
   cudaFree(m->d_ne_loc);
   cudaFree(m->d_rb);
+  cudaFree(m->d_rb_dnu);
   cudaFree(m->d_ef);
   cudaFree(m->d_cff);
   cudaFree(m->d_nff);

@@ -27,9 +27,11 @@ __host__ __device__ constexpr int rule_offset(int r) {
 }
 // kernel kinds: single-layer-like (V and its wave-speed derivatives, columns
 // = elements) and the wave-speed derivative selected (0 none, 1 c1, 2 c2)
-__host__ __device__ constexpr bool kern_sl(int k) { return k != BEM_DL; }
-__host__ __device__ constexpr int kern_dc(int k) { return k == BEM_SL_DCP ? 1 : (k == BEM_SL_DCS ? 2 : 0); }
-inline bool kern_valid(int k) { return k == BEM_SL || k == BEM_DL || k == BEM_SL_DCP || k == BEM_SL_DCS; }
+__host__ __device__ constexpr bool kern_sl(int k) { return k == BEM_SL || k == BEM_SL_DCP || k == BEM_SL_DCS; }
+__host__ __device__ constexpr int kern_dc(int k) {
+  return (k == BEM_SL_DCP || k == BEM_DL_DCP) ? 1 : ((k == BEM_SL_DCS || k == BEM_DL_DCS) ? 2 : 0);
+}
+inline bool kern_valid(int k) { return k >= BEM_SL && k <= BEM_DL_DCS; }
 constexpr int kSeriesTerms = 26;
 constexpr double kSeriesZ = 1.0;                    // series where |s| r / c2 < 1
 
@@ -96,6 +98,7 @@ struct bem_mesh {
   int32_t* d_ne_elem = nullptr;
   int32_t* d_ne_loc = nullptr;
   double* d_rb = nullptr;         // rigid-body static diagonal (node rows), n_nodes x 9, lazily
+  double* d_rb_dnu = nullptr;     // its derivative in nu (wave-speed derivative operators), lazily
   float4* d_ef = nullptr;         // FP32 element frames: [p0 - c, 2 area], [e1, 0], [e2, 0], [n, 0]
   float4* d_cff = nullptr;        // centroids as float pairs: [c_hi, h], [c_lo, 0] per element
   float4* d_nff = nullptr;        // nodes as float pairs: [x_hi, 0], [x_lo, 0] per node
@@ -148,7 +151,7 @@ bem_status build_trees(bem_tree* t);
 
 // device-side entry points (entry.cu, aca3d.cu, apply.cu, cq.cu) ---------------
 bem_status upload_quadrature(bem_ctx* ctx);
-bem_status ensure_rigid_body(bem_mesh* mesh, cudaStream_t st);
+bem_status ensure_rigid_body(bem_mesh* mesh, cudaStream_t st, bool dnu);
 bem_status launch_entries(bem_mesh* mesh, int rows, int kernel, const int32_t* req, int64_t n,
                           void* out, int* d_flag, cudaStream_t st);
 bem_status compress(bem_tree* tree, cudaStream_t st, OpData** out);
