@@ -34,9 +34,9 @@ WORKLOAD = dict(workload="sphere-5120-K64", mesh="icosphere level 4, radius 1 m,
                 rows="nodes (Neumann)", operators="V (SL) + C+K (DL)")
 METRIC = "3D-ACA tensor entries/s"
 # k_face DRAM traffic / algorithmic bytes, measured with ncu on the
-# icosphere-3 single layer (all 47 face launches of one compression): the
+# icosphere-3 single layer (all 42 face launches of one compression): the
 # previous faces are read twice per launch (residual and Gram passes)
-FACE_TRAFFIC_RATIO = 1.923
+FACE_TRAFFIC_RATIO = 1.932
 UNIT = "block entries/s"
 
 
@@ -165,6 +165,53 @@ def run_small():
 
 
 # ---------------------------------------------------------------------------
+# multi-mesh workload: one work list over many meshes (not the bench line)
+# ---------------------------------------------------------------------------
+
+def run_batch(count, n_max, n_streams):
+    """Single layer, node rows, MIXED, of the multi-mesh workload (mesh i of
+    synthetic.batch_meshes: N = K, dt = 0.6 h / c1): every operator
+    compressed one after the other, then all from one work list on
+    n_streams streams; block entries/s of both (dense tensor sizes summed)."""
+    import time
+    import torch
+    import paper_2607_15292_b300 as g
+    rho, lam, mu = syn.STEEL
+    c1 = float(np.sqrt((lam + 2.0 * mu) / rho))   # P-wave speed, for dt of the recipe
+
+    def trees():
+        out = []
+        for name, xyz, tri, K in syn.batch_meshes(count, n_max):
+            e = np.concatenate([xyz[tri[:, 1]] - xyz[tri[:, 0]], xyz[tri[:, 2]] - xyz[tri[:, 1]]])
+            h = float(np.linalg.norm(e, axis=1).mean())
+            ctx = g.Context(eps=1e-6, leaf=32, eta=2.0, precision=g.BEM_MIXED)
+            ctx.material(*syn.STEEL)
+            ctx.freqs(g.freqs_bdf2(K, 0.6 * h / c1, K))
+            out.append(ctx.mesh(xyz, tri).tree(g.BEM_ROWS_NODES, g.BEM_SL))
+        return out
+    warm = trees()[:2]
+    g.compress_batch(warm, 2)
+    ts = trees()
+    entries = sum(t.n_rows * t.n_cols * t.mesh.ctx.K for t in ts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ops = [t.compress(stream=0) for t in ts]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    del ops
+    ts = trees()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ops = g.compress_batch(ts, n_streams)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    print(json.dumps({"case": "multi-mesh workload, single layer, node rows, MIXED", "meshes": len(ts),
+                      "n_max": n_max, "triangles": int(sum(t.n_cols for t in ts)), "block_entries": int(entries),
+                      "sequential_s": t_seq, "batch_s": t_batch, "n_streams": n_streams,
+                      "sequential_entries_per_s": entries / t_seq, "batch_entries_per_s": entries / t_batch}))
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -179,11 +226,18 @@ def main():
     ap.add_argument("--small", action="store_true",
                     help="one MIXED compression and batched apply of the icosphere-3 single layer "
                          "(1,280 triangles, K = 64), for profiler captures; prints its statistics")
+    ap.add_argument("--batch", type=int, default=0, metavar="COUNT",
+                    help="multi-mesh workload: compress the first COUNT meshes one by one and from one "
+                         "work list; prints both rates (not the bench line)")
+    ap.add_argument("--batch-nmax", type=int, default=25, help="cap on the grid size n of --batch meshes")
+    ap.add_argument("--batch-streams", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.small:
         return run_small()
+    if args.batch:
+        return run_batch(args.batch, args.batch_nmax, args.batch_streams)
 
     import torch
     import paper_2607_15292_b300 as g

@@ -204,6 +204,23 @@ bem_status bem_tree_export(const bem_tree* tree, int32_t* row_perm, int32_t* col
  * pivot frequencies are larger, are not attempted).  Synchronises the
  * stream on return.  BEM_ERR_STATE if no frequencies or material are set. */
 bem_status bem_op_compress(bem_tree* tree, void* stream, bem_op** out);
+
+/* Compresses n operators (any meshes, kernels and frequency sets on one
+ * device) from one work list: jobs are ordered by decreasing cost
+ * n_rows n_cols K (bem_batch_order) and taken by min(n_streams, n, 32) host
+ * threads, each compressing on its own non-blocking stream, so that the
+ * launches of small meshes overlap on the device.  Lazy per-mesh state (the
+ * rigid-body diagonals) is built first, serially.  out[i] receives the
+ * operator of trees[i], equal to what bem_op_compress returns for it.  On
+ * error every operator of the call is destroyed, out[] is set to NULL and
+ * the first failing job's status is returned (BEM_ERR_ARG: null or repeated
+ * tree, trees on different devices; BEM_ERR_STATE: host-only context or
+ * material/frequencies unset).  Blocks until all jobs end. */
+bem_status bem_op_compress_batch(bem_tree* const* trees, int32_t n, int32_t n_streams, bem_op** out);
+
+/* The work-list order of bem_op_compress_batch: order[0..n) = indices of
+ * cost[] by decreasing cost, ties by index (host only). */
+bem_status bem_batch_order(const int64_t* cost, int32_t n, int32_t* order);
 void bem_op_destroy(bem_op* op);
 
 /* Apply (Eq. (3.15)).  transpose = 0:

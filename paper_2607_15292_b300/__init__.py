@@ -86,6 +86,8 @@ _SIGS = {
     "bem_op_face_ranks": (_i32, [_vp, _P(_i32)]),
     "bem_op_solve": (_i32, [_vp, _vp, _vp, _dbl, _i32, _P(_i32), _P(_dbl), _vp]),
     "bem_op_inner": (_i32, [_vp, _i32, _vp, _vp, _P(_dbl), _vp]),
+    "bem_op_compress_batch": (_i32, [_P(_vp), _i32, _i32, _P(_vp)]),
+    "bem_batch_order": (_i32, [_P(_i64), _i32, _P(_i32)]),
     "bem_face_compress": (_i32, [_vp, _vp, _i64, _i64, _dbl, _P(_i32), _vp, _vp]),
     "bem_kernel_launches": (_i64, []),
     "bem_cq_forward": (_i32, [_i32, _i64, _vp, _vp, _vp]),
@@ -128,6 +130,26 @@ def options_default() -> bem_options:
     o = bem_options()
     _check(_lib.bem_options_default(ctypes.byref(o)))
     return o
+
+
+def batch_order(cost) -> np.ndarray:
+    """Work-list order of compress_batch: indices by decreasing cost."""
+    c = np.ascontiguousarray(cost, dtype=np.int64)
+    o = np.zeros(len(c), dtype=np.int32)
+    _check(_lib.bem_batch_order(c.ctypes.data_as(_P(_i64)), len(c), o.ctypes.data_as(_P(_i32))))
+    return o
+
+
+def compress_batch(trees, n_streams: int = 4) -> list:
+    """Compresses several trees (any meshes, kernels and frequency sets on
+    one device) from one work list (bem_op_compress_batch)."""
+    n = len(trees)
+    arr = (_vp * n)(*[t._p.value for t in trees])
+    out = (_vp * n)()
+    st = _lib.bem_op_compress_batch(arr, n, int(n_streams), out)
+    if st != BEM_OK:
+        _check(st, trees[0].mesh.ctx.ptr)
+    return [Operator._adopt(t, out[i]) for i, t in enumerate(trees)]
 
 
 def kernel_launches() -> int:
@@ -299,12 +321,20 @@ class Stats:
 class Operator:
     """Compressed K-frequency tensor (bem_op)."""
 
-    def __init__(self, tree: Tree, stream=None):
+    def __init__(self, tree: Tree, stream=None, _ptr=None):
         self.tree = tree
         self.ctx = tree.mesh.ctx
         self.K = self.ctx.K
         self._p = ctypes.c_void_p()
+        if _ptr is not None:
+            self._p = ctypes.c_void_p(_ptr)
+            return
         _check(_lib.bem_op_compress(tree._p, _stream_ptr(stream), ctypes.byref(self._p)), self.ctx.ptr)
+
+    @classmethod
+    def _adopt(cls, tree: Tree, ptr) -> "Operator":
+        """Wraps an operator the library already compressed (takes ownership)."""
+        return cls(tree, _ptr=ptr)
 
     def __del__(self):
         try:

@@ -1203,10 +1203,13 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
                                                          d->d_hn2, K);
     GCQ_CUDA(ctx, cudaGetLastError());
     const int tb = std::max(32, ((K + 31) / 32) * 32);
-    const size_t fsm = sizeof(double2) * 9 * (size_t)K;
+    // the function attribute is process-wide state: it is set to the size
+    // of the largest K (256) so that operators with other K compressed
+    // concurrently on other host threads never see a smaller limit
+    const size_t fsm = sizeof(double2) * 9 * (size_t)K, fsm_max = sizeof(double2) * 9 * 256;
     GCQ_DISPATCH(d->kernel, d->rows,
                  (cudaFuncSetAttribute(k_fibre_step<R, S, KK, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)fsm),
+                                       (int)fsm_max),
                   k_fibre_step<R, S, KK, RR><<<(unsigned)active.size(), tb, fsm, st>>>(
                      v, d->d_blk, d_active, (S* const*)d->d_face, (S* const*)d->d_fib, nb, slot, d->d_row_perm,
                      d->d_col_perm, d->d_M, d->d_ks, d->d_used, K, ctx->opt.eps)));

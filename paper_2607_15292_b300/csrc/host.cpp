@@ -3,8 +3,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <numeric>
+#include <thread>
 
 #include "internal.h"
 
@@ -747,6 +749,92 @@ bem_status bem_op_compress(bem_tree* tree, void* stream, bem_op** out) {
   tree->refs++;
   *out = op;
   return BEM_OK;
+}
+
+// Work list over several operators (meshes x kernels x frequency sets): the
+// jobs, ordered by decreasing cost n_rows n_cols K (longest first), are taken
+// by a pool of host threads, each compressing on its own non-blocking stream,
+// so that the small launches of small meshes overlap on the device.
+bem_status bem_batch_order(const int64_t* cost, int32_t n, int32_t* order) {
+  if (!cost || !order || n < 0) return BEM_ERR_ARG;
+  std::vector<int32_t> o(n);
+  std::iota(o.begin(), o.end(), 0);
+  std::stable_sort(o.begin(), o.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  std::copy(o.begin(), o.end(), order);
+  return BEM_OK;
+}
+
+bem_status bem_op_compress_batch(bem_tree* const* trees, int32_t n, int32_t n_streams, bem_op** out) {
+  if (!trees || !out || n < 1 || n_streams < 1) return BEM_ERR_ARG;
+  for (int32_t i = 0; i < n; ++i) {
+    out[i] = nullptr;
+    if (!trees[i]) return BEM_ERR_ARG;
+  }
+  bem_ctx* ctx0 = trees[0]->mesh->ctx;
+  for (int32_t i = 0; i < n; ++i) {
+    bem_ctx* c = trees[i]->mesh->ctx;
+    if (c->device < 0) return set_err(c, BEM_ERR_STATE, "bem_op_compress_batch: host-only context (device -1)");
+    if (c->device != ctx0->device)
+      return set_err(c, BEM_ERR_ARG, "bem_op_compress_batch: all trees must be on one device");
+    if (!c->has_material || c->K < 1)
+      return set_err(c, BEM_ERR_STATE, "bem_op_compress_batch: material or frequencies not set");
+    for (int32_t j = 0; j < i; ++j)
+      if (trees[j] == trees[i]) return set_err(c, BEM_ERR_ARG, "bem_op_compress_batch: a tree is listed twice");
+  }
+  GCQ_CUDA(ctx0, cudaSetDevice(ctx0->device));
+  // per-device and per-mesh state created lazily by the first compression
+  // is created here, once, before the workers start
+  for (int32_t i = 0; i < n; ++i) {
+    bem_tree* t = trees[i];
+    bem_status s = upload_quadrature(t->mesh->ctx);
+    if (s == BEM_OK && !kern_sl(t->kernel) && t->rows == BEM_ROWS_NODES)
+      s = ensure_rigid_body(t->mesh, nullptr, kern_dc(t->kernel) != 0);
+    if (s != BEM_OK) return s;
+  }
+  GCQ_CUDA(ctx0, cudaDeviceSynchronize());
+  std::vector<int64_t> cost(n);
+  for (int32_t i = 0; i < n; ++i) cost[i] = trees[i]->n_rows * trees[i]->n_cols * (int64_t)trees[i]->mesh->ctx->K;
+  std::vector<int32_t> order(n);
+  bem_batch_order(cost.data(), n, order.data());
+  std::vector<bem_status> st(n, BEM_OK);
+  std::atomic<int32_t> next{0};
+  const int32_t nw = std::min<int32_t>(std::min<int32_t>(n_streams, n), 32);
+  // a worker that cannot set up its stream takes no job; the others do
+  auto work = [&](int32_t) {
+    if (cudaSetDevice(ctx0->device) != cudaSuccess) return;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
+    for (int32_t j = next++; j < n; j = next++) {
+      const int32_t i = order[j];
+      st[i] = bem_op_compress(trees[i], s, &out[i]);
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> pool;
+  for (int32_t w = 1; w < nw; ++w) pool.emplace_back(work, w);
+  work(0);
+  for (auto& t : pool) t.join();
+  bem_status res = BEM_OK;
+  int32_t bad = -1;   // first failing job in tree order (its context holds the message)
+  for (int32_t i = 0; i < n && res == BEM_OK; ++i)
+    if ((res = st[i]) != BEM_OK) bad = i;
+  bool untaken = false;
+  for (int32_t i = 0; i < n; ++i) untaken |= st[i] == BEM_OK && !out[i];
+  if (res == BEM_OK && untaken) res = set_err(ctx0, BEM_ERR_CUDA, "bem_op_compress_batch: no worker could set up a stream");
+  if (res != BEM_OK) {
+    for (int32_t i = 0; i < n; ++i) {
+      bem_op_destroy(out[i]);
+      out[i] = nullptr;
+    }
+    if (bad >= 0 && trees[bad]->mesh->ctx != ctx0) {
+      // report the failing job's message through the first tree's context too
+      std::string m = std::string("bem_op_compress_batch: job ") + std::to_string(bad) + ": " +
+                      bem_last_error(trees[bad]->mesh->ctx);
+      set_err(ctx0, res, m);
+    }
+  }
+  return res;
 }
 
 void bem_op_destroy(bem_op* op) {

@@ -174,6 +174,40 @@ def ellipsoid(level: int, axes=(2.0, 1.0, 1.0)) -> tuple[np.ndarray, np.ndarray]
     return xyz * np.asarray(axes, dtype=np.float64), tri
 
 
+def cube_sphere(n: int, radius: float = 1.0) -> tuple[np.ndarray, np.ndarray]:
+    """cube_grid(n) with every node projected radially onto the sphere of the
+    given radius: 12 n^2 triangles."""
+    xyz, tri = cube_grid(n)
+    return radius * xyz / np.linalg.norm(xyz, axis=1, keepdims=True), tri
+
+
+def batch_meshes(count: int = 32, n_max: int = 25):
+    """The multi-mesh workload: mesh i (i = 0..count-1) takes three
+    splitmix64 words of seed 1000 + i: u0 mod 3 picks a cube grid, a
+    cube-sphere or a 2:1:1 ellipsoid (scaled cube-sphere), 7 + u1 mod 19
+    (capped at n_max) the grid size n (12 n^2 triangles, 588 to 7,500), and
+    u2 mod 4 the frequency count K in {16, 32, 64, 128}.  Returns a list of
+    (name, xyz, tri, K)."""
+    out = []
+    for i in range(count):
+        u = splitmix64(1000 + i, 3)
+        kind = int(u[0] % 3)
+        n = min(7 + int(u[1] % 19), n_max)
+        K = (16, 32, 64, 128)[int(u[2] % 4)]
+        if kind == 0:
+            xyz, tri = cube_grid(n)
+            name = f"cube{n}"
+        elif kind == 1:
+            xyz, tri = cube_sphere(n)
+            name = f"cubesphere{n}"
+        else:
+            xyz, tri = cube_sphere(n)
+            xyz = xyz * np.array([2.0, 1.0, 1.0])
+            name = f"ellipsoid{n}"
+        out.append((name, xyz, tri, K))
+    return out
+
+
 # --------------------------------------------------------------------------
 # seeded random numbers: splitmix64 counter stream -> uniforms -> Box-Muller
 # --------------------------------------------------------------------------
