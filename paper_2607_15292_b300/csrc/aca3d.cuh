@@ -296,8 +296,19 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
                                                 const int32_t* __restrict__ row_perm,
                                                 const int32_t* __restrict__ col_perm, double* __restrict__ p_s3,
                                                 int64_t* __restrict__ p_idx, double* __restrict__ p_h2,
-                                                double2* __restrict__ p_M, const double* __restrict__ hn2, int K) {
+                                                double2* __restrict__ p_M, const double* __restrict__ hn2, int K,
+                                                int* __restrict__ err) {
   using W = typename WorkOf<S>::W;
+  // Previous faces stream through shared memory: the tile's 256 entries of a
+  // face are one contiguous range (256 x 9 x 16 B = 36 KB), copied by one
+  // bulk TMA copy into one of two buffers.  Copy n (n = 0 .. 2 slot - 1)
+  // brings face n for the residual pass (n < slot), then faces slot - 1 ..
+  // 0 for the Gram pass; it lands in buffer n & 1, completes phase
+  // (n >> 1) & 1 of that buffer's barrier, and copy n + 2 is issued once
+  // every thread is done with copy n.  The first two copies overlap the
+  // entry evaluation.
+  extern __shared__ __align__(128) unsigned char kf_dyn[];   // 2 x kTile x 9 S
+  __shared__ __align__(8) uint64_t kf_bar[2];
   __shared__ S sf[64 * 9];     // f_p[k_d] for p < slot, in chunks of 64
   __shared__ unsigned char ssmall[64];   // term p below 2^-10 of the first: plain FMA (MIXED)
   __shared__ double shv[32 * 18];
@@ -308,6 +319,25 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   const bool ok = e < B.m * B.n;
   const int kd = B.k_cur;
   constexpr bool FF = sizeof(S) == sizeof(float4) && sizeof(W) == sizeof(float);
+  S* const fbuf0 = reinterpret_cast<S*>(kf_dyn);
+  const int64_t nval = min((int64_t)kTile, B.m * B.n - t.start);
+  const uint32_t tile_bytes = (uint32_t)(nval * 9 * (int64_t)sizeof(S));
+  const int nload = 2 * slot;
+  auto issue = [&](int n) {   // thread 0 only
+    const int pf = n < slot ? n : 2 * slot - 1 - n;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&kf_bar[n & 1], tile_bytes);
+    bulk_copy_g2s(fbuf0 + (n & 1) * (kTile * 9), face_tab[(int64_t)pf * nb + t.blk] + t.start * 9, tile_bytes,
+                  &kf_bar[n & 1]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&kf_bar[0], 1);
+    mbar_init(&kf_bar[1], 1);
+    fence_mbar_init();
+    if (nload > 0) issue(0);
+    if (nload > 1) issue(1);
+  }
+  int waited_ok = 1;   // every barrier wait of this thread completed
   float fh[18], fl[18];           // float-float accumulators (MIXED)
   cx<double> Hd64[9];             // double accumulators (FP64)
   int i = 0, j = 0;
@@ -381,18 +411,14 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
       }
       __syncthreads();
     }
-    if (ok) {
-      S nxt[9];
-      {
-        const S* Hp = face_tab[(int64_t)p0 * nb + t.blk] + e * 9;
-        for (int c = 0; c < 9; ++c) nxt[c] = Hp[c];
-      }
-      for (int p = 0; p < np; ++p) {
+    for (int p = 0; p < np; ++p) {
+      const int n = p0 + p;   // copy n holds face n
+      if (!mbar_wait(&kf_bar[n & 1], (n >> 1) & 1)) waited_ok = 0;
+      if (ok && waited_ok) {
         S cur[9];
-        for (int c = 0; c < 9; ++c) cur[c] = nxt[c];
-        if (p + 1 < np) {   // prefetch the next face while this one is used
-          const S* Hn = face_tab[(int64_t)(p0 + p + 1) * nb + t.blk] + e * 9;
-          for (int c = 0; c < 9; ++c) nxt[c] = Hn[c];
+        {
+          const S* Hp = fbuf0 + (n & 1) * (kTile * 9) + threadIdx.x * 9;
+          for (int c = 0; c < 9; ++c) cur[c] = Hp[c];
         }
         const S* f = sf + 9 * p;
         if constexpr (FF) {
@@ -410,24 +436,24 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
                   si = fmaf(x.y, y.x, si);
                 }
               }
-            continue;
-          }
-          for (int a = 0; a < 3; ++a)
-            for (int c = 0; c < 3; ++c) {
-              const float4 x = reinterpret_cast<const float4*>(cur)[3 * a + c];
-              for (int b = 0; b < 3; ++b) {
-                const float4 y = reinterpret_cast<const float4*>(f)[3 * c + b];
-                float& rh = fh[2 * (3 * a + b)];
-                float& rl = fl[2 * (3 * a + b)];
-                float& ih = fh[2 * (3 * a + b) + 1];
-                float& il = fl[2 * (3 * a + b) + 1];
-                // (re) -= x.re y.re - x.im y.im ; (im) -= x.re y.im + x.im y.re
-                ff_sub_prod(rh, rl, x.x, x.z, y.x, y.z);
-                ff_sub_prod(rh, rl, -x.y, -x.w, y.y, y.w);
-                ff_sub_prod(ih, il, x.x, x.z, y.y, y.w);
-                ff_sub_prod(ih, il, x.y, x.w, y.x, y.z);
+          } else {
+            for (int a = 0; a < 3; ++a)
+              for (int c = 0; c < 3; ++c) {
+                const float4 x = reinterpret_cast<const float4*>(cur)[3 * a + c];
+                for (int b = 0; b < 3; ++b) {
+                  const float4 y = reinterpret_cast<const float4*>(f)[3 * c + b];
+                  float& rh = fh[2 * (3 * a + b)];
+                  float& rl = fl[2 * (3 * a + b)];
+                  float& ih = fh[2 * (3 * a + b) + 1];
+                  float& il = fl[2 * (3 * a + b) + 1];
+                  // (re) -= x.re y.re - x.im y.im ; (im) -= x.re y.im + x.im y.re
+                  ff_sub_prod(rh, rl, x.x, x.z, y.x, y.z);
+                  ff_sub_prod(rh, rl, -x.y, -x.w, y.y, y.w);
+                  ff_sub_prod(ih, il, x.x, x.z, y.y, y.w);
+                  ff_sub_prod(ih, il, x.y, x.w, y.x, y.z);
+                }
               }
-            }
+          }
         } else {
           cx<double> hp[9], ff[9];
           for (int c = 0; c < 9; ++c) {
@@ -442,6 +468,8 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
             }
         }
       }
+      __syncthreads();   // every thread is done with copy n: its buffer takes copy n + 2
+      if (threadIdx.x == 0 && n + 2 < nload) issue(n + 2);
     }
   }
   S* Hd = face_tab[(int64_t)slot * nb + t.blk];
@@ -479,35 +507,35 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
     p_idx[blockIdx.x] = idx;
     p_h2[blockIdx.x] = h2s[0];
   }
-  // Gram blocks M_pd = sum_ij H_p[i,j]^H H_d[i,j], p = 0..slot: per-warp
-  // transpose sums into shared memory, then a fixed-order sum over the warps
+  // Gram blocks M_pd = sum_ij H_p[i,j]^H H_d[i,j], p = slot..0: per-warp
+  // transpose sums into shared memory, then a fixed-order sum over the warps.
+  // p = slot is the face in registers; p < slot arrive as copies
+  // n = 2 slot - 1 - p (the reverse of the residual pass's order).
   __shared__ W gw[kTile / 32][16][18];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  S nxt[9];
-  if (ok) {
-    const S* Hp = face_tab[t.blk] + e * 9;
-    for (int c = 0; c < 9; ++c) nxt[c] = Hp[c];
-  }
   for (int p0 = 0; p0 <= slot; p0 += 16) {
     const int np = min(16, slot + 1 - p0);
     for (int pp = 0; pp < np; ++pp) {
-      const int p = p0 + pp;
+      const int q = p0 + pp;          // p = slot - q
+      const int n = slot + q - 1;     // copy holding face p (q > 0)
+      if (q > 0 && !mbar_wait(&kf_bar[n & 1], (n >> 1) & 1)) waited_ok = 0;
       W g[32];
       for (int c = 0; c < 32; ++c) g[c] = W(0);
-      if (ok) {
+      if (ok && waited_ok) {
         cx<W> hp[9];
-        for (int c = 0; c < 9; ++c) {
-          if constexpr (FF) {
-            const float4 x = reinterpret_cast<const float4*>(nxt)[c];
-            hp[c] = {(W)x.x, (W)x.y};
-          } else {
-            const cx<double> x = St<S>::ld(nxt + c);
-            hp[c] = {(W)x.x, (W)x.y};
+        if (q == 0) {
+          for (int c = 0; c < 9; ++c) hp[c] = H[c];
+        } else {
+          const S* Hp = fbuf0 + (n & 1) * (kTile * 9) + threadIdx.x * 9;
+          for (int c = 0; c < 9; ++c) {
+            if constexpr (FF) {
+              const float4 x = reinterpret_cast<const float4*>(Hp)[c];
+              hp[c] = {(W)x.x, (W)x.y};
+            } else {
+              const cx<double> x = St<S>::ld(Hp + c);
+              hp[c] = {(W)x.x, (W)x.y};
+            }
           }
-        }
-        if (p + 1 <= slot) {
-          const S* Hn = face_tab[(int64_t)(p + 1) * nb + t.blk] + e * 9;
-          for (int c = 0; c < 9; ++c) nxt[c] = Hn[c];
         }
         for (int a = 0; a < 3; ++a)
           for (int b = 0; b < 3; ++b) {
@@ -519,6 +547,10 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
       }
       const W tot = warp_transpose_sum<W>(g);
       if (lane < 18) gw[wid][pp][lane] = tot;
+      if (q > 0) {
+        __syncthreads();   // every thread is done with copy n
+        if (threadIdx.x == 0 && n + 2 < nload) issue(n + 2);
+      }
     }
     __syncthreads();
     double* pm = reinterpret_cast<double*>(p_M);
@@ -526,9 +558,15 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
       const int pp = q / 18, c = q % 18;
       double sum = 0.0;
       for (int w = 0; w < kTile / 32; ++w) sum += (double)gw[w][pp][c];
-      pm[((int64_t)blockIdx.x * K + p0 + pp) * 18 + c] = sum;
+      pm[((int64_t)blockIdx.x * K + slot - (p0 + pp)) * 18 + c] = sum;
     }
     __syncthreads();
+  }
+  // a copy that did not land in time: flag it for the host (which abandons
+  // the compression) and give the copies still in flight a bounded wait
+  if (__syncthreads_or(!waited_ok) && threadIdx.x == 0) {
+    atomicExch(err, 1);
+    for (int n = max(0, nload - 2); n < nload; ++n) mbar_wait(&kf_bar[n & 1], (n >> 1) & 1);
   }
 }
 
@@ -704,8 +742,14 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
   // thread per (face p, entry (a, c2)) reading f_d from shared memory, then
   // tr(M_pd N_dp) accumulated per thread; one block reduction at the end
   extern __shared__ double2 sfd[];   // K x 9 (f_d), from the launch
+  float2* sff = reinterpret_cast<float2*>(sfd);   // MIXED: f_d rounded to FP32 once, for the FP32 Gram
   if (ok)
-    for (int c = 0; c < 9; ++c) sfd[(int64_t)k * 9 + c] = make_double2(f[c].x, f[c].y);
+    for (int c = 0; c < 9; ++c) {
+      if constexpr (FF)
+        sff[(int64_t)k * 9 + c] = make_float2((float)f[c].x, (float)f[c].y);
+      else
+        sfd[(int64_t)k * 9 + c] = make_double2(f[c].x, f[c].y);
+    }
   __syncthreads();
   double part[3] = {0.0, 0.0, 0.0};   // ||f_d||^2, cross, self
   if (ok)
@@ -718,9 +762,9 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
       cx<float> af = {0.f, 0.f};
       for (int kk = 0; kk < K; ++kk)
         for (int c = 0; c < 3; ++c) {
-          const double2 x = sfd[(int64_t)kk * 9 + 3 * a + c];
+          const float2 x = sff[(int64_t)kk * 9 + 3 * a + c];
           const float4 y = reinterpret_cast<const float4*>(fp)[(int64_t)kk * 9 + 3 * c2 + c];
-          af = cfma(cx<float>{(float)x.x, (float)x.y}, cx<float>{y.x, -y.y}, af);
+          af = cfma(cx<float>{x.x, x.y}, cx<float>{y.x, -y.y}, af);
         }
       acc = {(double)af.x, (double)af.y};
     } else {
@@ -1139,6 +1183,10 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   GCQ_CUDA(ctx, dmalloc(&p_h2, sizeof(double) * n_tiles_all, &scratch));
   GCQ_CUDA(ctx, dmalloc(&p_idx, sizeof(int64_t) * n_tiles_all, &scratch));
   GCQ_CUDA(ctx, dmalloc(&p_M, sizeof(double2) * n_tiles_all * K * 9, &scratch));
+  int* d_err = nullptr;   // set by k_face when a staged face copy did not land in time
+  int h_err = 0;
+  GCQ_CUDA(ctx, dmalloc(&d_err, sizeof(int), &scratch));
+  GCQ_CUDA(ctx, cudaMemsetAsync(d_err, 0, sizeof(int), st));
   cudaEvent_t ev0, ev1, evf;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
@@ -1188,10 +1236,15 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
     GCQ_CUDA(ctx, cudaMemcpyAsync(d_active, active.data(), sizeof(int32_t) * active.size(), cudaMemcpyHostToDevice,
                                   st));
     cudaEventRecord(ev0, st);
+    // two face tiles of the TMA double buffer (the same size for every
+    // operator, so the process-wide attribute never changes)
+    const size_t kf_smem = 2 * (size_t)kTile * 9 * sizeof(SC);
     GCQ_DISPATCH(d->kernel, d->rows,
-                 (k_face<R, SC, KK, RR><<<(unsigned)tiles.size(), kTile, 0, st>>>(
+                 (cudaFuncSetAttribute(k_face<R, SC, KK, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kf_smem),
+                  k_face<R, SC, KK, RR><<<(unsigned)tiles.size(), kTile, kf_smem, st>>>(
                      v, d_tiles, d->d_blk, (S* const*)d->d_face, (S* const*)d->d_fib, nb, slot, d->d_row_perm,
-                     d->d_col_perm, p_s3, p_idx, p_h2, p_M, d->d_hn2, K)));
+                     d->d_col_perm, p_s3, p_idx, p_h2, p_M, d->d_hn2, K, d_err)));
     GCQ_CUDA(ctx, cudaGetLastError());
     cudaEventRecord(evf, st);
     d->face_launches++;
@@ -1216,7 +1269,12 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
     GCQ_CUDA(ctx, cudaGetLastError());
     cudaEventRecord(ev1, st);
     GCQ_CUDA(ctx, cudaMemcpyAsync(d->h_blk.data(), d->d_blk, sizeof(BlkDev) * nb, cudaMemcpyDeviceToHost, st));
+    GCQ_CUDA(ctx, cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     GCQ_CUDA(ctx, cudaStreamSynchronize(st));
+    if (h_err) {
+      result = set_err(ctx, BEM_ERR_CUDA, "bem_op_compress: a staged face copy of k_face did not complete in time");
+      break;
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     t_ent += ms;

@@ -375,6 +375,7 @@ extern "C" bem_status bem_entries_noalloc(bem_mesh* mesh, int32_t rows, int32_t 
 
 namespace gcq {}  // aca3d.cuh and apply.cuh reopen the namespace
 
+#include "tma.cuh"
 #include "aca3d.cuh"
 #include "apply.cuh"
 #include "solve.cuh"
