@@ -35,8 +35,9 @@ WORKLOAD = dict(workload="sphere-5120-K64", mesh="icosphere level 4, radius 1 m,
 METRIC = "3D-ACA tensor entries/s"
 # k_face DRAM traffic / algorithmic bytes, measured with ncu on the
 # icosphere-3 single layer (all 42 face launches of one compression): the
-# previous faces are read twice per launch (residual and Gram passes)
-FACE_TRAFFIC_RATIO = 1.932
+# previous faces are read twice per launch (residual and Gram passes), the
+# second time partly from L2
+FACE_TRAFFIC_RATIO = 1.708
 UNIT = "block entries/s"
 
 
