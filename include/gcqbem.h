@@ -295,8 +295,23 @@ typedef struct {
   int64_t n_faces_lowrank;      /* of which stored as U' W'^T (Eq. (3.12))  */
   double face_rank_mean;        /* mean rank k of the low-rank faces       */
   double t_face_aca_ms;         /* device time of the face ACA kernel      */
+  int64_t apply_bk;             /* frequency tile of the batched apply (16, 32, 64) */
+  double apply_tune_ms[3];      /* batched-apply times of tiles 16, 32, 64 from
+                                   bem_op_autotune (0: not timed)           */
 } bem_op_stats;
 bem_status bem_op_stats_get(const bem_op* op, bem_op_stats* st);
+
+/* Frequency tile of the batched apply: each CTA of the face kernels owns 32
+ * rows x BK frequencies of a block (BK = 16, 32 or 64; default the smallest
+ * of them >= K, else 64).  bem_op_set_apply_tile selects one (BEM_ERR_ARG
+ * for another value); bem_op_autotune times one warm-up and three batched
+ * applies of zero vectors with each tile on the operator itself (CUDA
+ * events on the stream), keeps the fastest and returns it in *bk (may be
+ * NULL).  Results do not depend on the tile: every frequency's arithmetic is
+ * the same.  The autotune allocates an input and an output vector and
+ * synchronises the stream. */
+bem_status bem_op_set_apply_tile(bem_op* op, int32_t bk);
+bem_status bem_op_autotune(bem_op* op, void* stream, int32_t* bk);
 
 /* Per-block results (host, n_blocks x 4 int64): kind (0 aca, 1 dense,
  * 2 rank0), rank, first pivot frequency k_1 (-1 if none), number of the

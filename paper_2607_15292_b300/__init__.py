@@ -55,7 +55,8 @@ class bem_op_stats(ctypes.Structure):
                 ("apply_bytes", ctypes.c_int64), ("t_face_ms", ctypes.c_double),
                 ("face_launches", ctypes.c_int64), ("face_alg_bytes", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("n_faces", ctypes.c_int64), ("n_faces_lowrank", ctypes.c_int64),
-                ("face_rank_mean", ctypes.c_double), ("t_face_aca_ms", ctypes.c_double)]
+                ("face_rank_mean", ctypes.c_double), ("t_face_aca_ms", ctypes.c_double),
+                ("apply_bk", ctypes.c_int64), ("apply_tune_ms", ctypes.c_double * 3)]
 
 
 _vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -87,6 +88,8 @@ _SIGS = {
     "bem_op_solve": (_i32, [_vp, _vp, _vp, _dbl, _i32, _P(_i32), _P(_dbl), _vp]),
     "bem_op_inner": (_i32, [_vp, _i32, _vp, _vp, _P(_dbl), _vp]),
     "bem_op_compress_batch": (_i32, [_P(_vp), _i32, _i32, _P(_vp)]),
+    "bem_op_set_apply_tile": (_i32, [_vp, _i32]),
+    "bem_op_autotune": (_i32, [_vp, _vp, _P(_i32)]),
     "bem_batch_order": (_i32, [_P(_i64), _i32, _P(_i32)]),
     "bem_face_compress": (_i32, [_vp, _vp, _i64, _i64, _dbl, _P(_i32), _vp, _vp]),
     "bem_kernel_launches": (_i64, []),
@@ -316,6 +319,8 @@ class Stats:
     n_faces_lowrank: int
     face_rank_mean: float
     t_face_aca_ms: float
+    apply_bk: int
+    apply_tune_ms: tuple
 
 
 class Operator:
@@ -363,6 +368,17 @@ class Operator:
     def apply_adjoint(self, Yin, Xout, mode: int = BEM_APPLY_BATCHED, stream=None):
         self.apply(Yin, Xout, mode, stream, transpose=1)
 
+    def set_apply_tile(self, bk: int):
+        """Frequency tile of the batched apply (16, 32 or 64)."""
+        _check(_lib.bem_op_set_apply_tile(self._p, int(bk)), self.ctx.ptr)
+
+    def autotune(self, stream=None) -> int:
+        """Times the batched apply with each frequency tile on this operator
+        and keeps the fastest; returns it."""
+        bk = _i32(0)
+        _check(_lib.bem_op_autotune(self._p, _stream_ptr(stream), ctypes.byref(bk)), self.ctx.ptr)
+        return int(bk.value)
+
     def inner(self, G, X, mode: int = BEM_APPLY_BATCHED, stream=None) -> complex:
         """<G, C X> (bem_op_inner): sum of conj(G) times the apply of X."""
         out = np.zeros(2, dtype=np.float64)
@@ -376,7 +392,8 @@ class Operator:
     def stats(self) -> Stats:
         s = bem_op_stats()
         _check(_lib.bem_op_stats_get(self._p, ctypes.byref(s)))
-        return Stats(*[getattr(s, f) for f, _ in bem_op_stats._fields_])
+        vals = [getattr(s, f) for f, _ in bem_op_stats._fields_]
+        return Stats(*[tuple(v) if isinstance(v, ctypes.Array) else v for v in vals])
 
     def blocks(self) -> np.ndarray:
         out = np.zeros((self.tree.n_blocks, 4), dtype=np.int64)

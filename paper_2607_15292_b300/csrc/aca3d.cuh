@@ -66,8 +66,11 @@ struct OpData {
   double face_alg_bytes = 0;     // algorithmic bytes of k_face: (slot + 1) faces per entry
   int64_t launches = 0;          // kernels launched by the compression
   // apply work lists
-  int32_t* d_apply_items = nullptr;  // (block, row tile, k tile) for aca blocks
-  int64_t n_apply_items = 0;
+  // batched apply work lists, one per frequency tile BK = 16, 32, 64
+  int32_t* d_apply_items_v[3] = {nullptr, nullptr, nullptr};   // (block, row tile, k tile)
+  int64_t n_apply_items_v[3] = {0, 0, 0};
+  int32_t apply_bk = 64;             // frequency tile in use (default: the smallest >= K, else 64)
+  double apply_tune_ms[3] = {0, 0, 0};   // batched-apply times of the variants (autotune), 0 = not timed
   int32_t* d_dense_list = nullptr;   // dense block ids
   int64_t n_dense = 0;
   int32_t* d_aca_list = nullptr;     // aca block ids (rank > 0)
@@ -90,8 +93,8 @@ struct OpData {
   // apply scratch of the low-rank faces: T_p (k x K) per face
   int64_t* d_toff = nullptr;         // [slot][block] offset into d_t, -1 if none
   void* d_t = nullptr;
-  int32_t* d_lr_items = nullptr;     // (block, slot, pseudo-row tile, k tile) int4
-  int64_t n_lr_items = 0;
+  int32_t* d_lr_items_v[3] = {nullptr, nullptr, nullptr};   // (block, slot, pseudo-row tile, k tile) int4
+  int64_t n_lr_items_v[3] = {0, 0, 0};
   int32_t* d_lr_faces = nullptr;     // (block, slot, aca index, 0) int4 of low-rank faces with k > 0
   // adjoint apply: items (block, column tile, k tile) and (block, slot, rank tile, k tile)
   int32_t* d_adj_items = nullptr;

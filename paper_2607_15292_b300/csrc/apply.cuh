@@ -161,7 +161,7 @@ __global__ void k_contract_apply(const BlkDev* __restrict__ blk, const int32_t* 
 
 // ---- batched apply of 3D-ACA blocks, frequency-contiguous layout ------------
 // Xp: n_cols x K x 3 and Yp: n_rows x K x 3 complex in cluster order.  A CTA
-// owns kBM rows x kBK frequencies of one block and streams every face of the
+// owns kBM rows x BK frequencies of one block and streams every face of the
 // block once through shared memory in chunks of kBN columns:
 //   Z[j][a][k] = sum_b f_p[k][a][b] x_k[j][b]      (fibre transform, per chunk)
 //   Y[i][k][a] += sum_j sum_b H_p[i][j][a][b] Z[j][b][k]
@@ -170,16 +170,20 @@ __global__ void k_contract_apply(const BlkDev* __restrict__ blk, const int32_t* 
 // 3 kBN rank columns take the place of kBN nodes x 3 components, so one inner
 // loop serves both.  Each thread accumulates 8 frequencies x 3 components of
 // one row in registers; the block's result is added to Yp once (atomics).
-constexpr int kBM = 32, kBK = 64, kBN = 16, kTPR = 8;
+// The frequency tile BK (16, 32 or 64) is a template parameter: an operator
+// with few frequencies takes a narrower tile (K = 16 fills a 64-wide tile to
+// a quarter); bem_op_autotune times the variants on the operator itself.
+constexpr int kBM = 32, kBN = 16, kTPR = 8;
+constexpr int kApplyBK[3] = {16, 32, 64};
 constexpr int kSHR = kBN * 9 + 1;   // padded row stride of the face tile (no bank conflicts)
 constexpr int kApplyThreads = kBM * kTPR;   // 256
 
-// Z chunk: sZ[(jj * 3 + a) * kBK + kk] = sum_b f[kk][a][b] x[j0 + jj][b] (zero outside)
-template <typename S, typename A>
+// Z chunk: sZ[(jj * 3 + a) * BK + kk] = sum_b f[kk][a][b] x[j0 + jj][b] (zero outside)
+template <typename S, typename A, int BK>
 __device__ __forceinline__ void load_z_chunk(cx<A>* sZ, const cx<A>* sF, const S* __restrict__ Xp, int64_t c0,
                                              int64_t j0, int64_t n, int K, int k0, int nk) {
-  for (int c = threadIdx.x; c < kBN * kBK; c += blockDim.x) {
-    const int jj = c / kBK, kk = c % kBK;
+  for (int c = threadIdx.x; c < kBN * BK; c += blockDim.x) {
+    const int jj = c / BK, kk = c % BK;
     const int64_t gj = j0 + jj;
     cx<A> x[3] = {{A(0), A(0)}, {A(0), A(0)}, {A(0), A(0)}};
     if (gj < n && kk < nk) {
@@ -189,13 +193,13 @@ __device__ __forceinline__ void load_z_chunk(cx<A>* sZ, const cx<A>* sF, const S
     for (int a = 0; a < 3; ++a) {
       cx<A> z = {A(0), A(0)};
       for (int b = 0; b < 3; ++b) z = cfma(sF[kk * 9 + 3 * a + b], x[b], z);
-      sZ[(jj * 3 + a) * kBK + kk] = z;
+      sZ[(jj * 3 + a) * BK + kk] = z;
     }
   }
 }
-template <typename S, typename A>
+template <typename S, typename A, int BK>
 __device__ __forceinline__ void load_f(cx<A>* sF, const S* __restrict__ f, int k0, int nk) {
-  for (int c = threadIdx.x; c < kBK * 9; c += blockDim.x) {
+  for (int c = threadIdx.x; c < BK * 9; c += blockDim.x) {
     const int kk = c / 9;
     sF[c] = kk < nk ? Ld<S, A>::ld(f + (int64_t)(k0 + kk) * 9 + c % 9) : cx<A>{A(0), A(0)};
   }
@@ -204,12 +208,12 @@ __device__ __forceinline__ void load_f(cx<A>* sF, const S* __restrict__ f, int k
 // Two-level summation: each chunk (3 kBN terms per output) is summed in a
 // fresh register before it joins the block's accumulator, so that FP32
 // rounding grows with sqrt(3 kBN + chunks) instead of sqrt(all terms).
-template <typename A>
-__device__ __forceinline__ void mac_chunk(cx<A> (&acc)[kBK / kTPR][3], const cx<A>* sH, const cx<A>* sZ, int r,
+template <typename A, int BK>
+__device__ __forceinline__ void mac_chunk(cx<A> (&acc)[BK / kTPR][3], const cx<A>* sH, const cx<A>* sZ, int r,
                                           int kq) {
-  cx<A> part[kBK / kTPR][3];
+  cx<A> part[BK / kTPR][3];
 #pragma unroll
-  for (int t = 0; t < kBK / kTPR; ++t)
+  for (int t = 0; t < BK / kTPR; ++t)
 #pragma unroll
     for (int a = 0; a < 3; ++a) part[t][a] = {A(0), A(0)};
 #pragma unroll 4
@@ -220,19 +224,19 @@ __device__ __forceinline__ void mac_chunk(cx<A> (&acc)[kBK / kTPR][3], const cx<
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
-      for (int t = 0; t < kBK / kTPR; ++t) {
-        const cx<A> z = sZ[(jj * 3 + b) * kBK + kq + kTPR * t];
+      for (int t = 0; t < BK / kTPR; ++t) {
+        const cx<A> z = sZ[(jj * 3 + b) * BK + kq + kTPR * t];
 #pragma unroll
         for (int a = 0; a < 3; ++a) part[t][a] = cfma(h[3 * a + b], z, part[t][a]);
       }
   }
 #pragma unroll
-  for (int t = 0; t < kBK / kTPR; ++t)
+  for (int t = 0; t < BK / kTPR; ++t)
 #pragma unroll
     for (int a = 0; a < 3; ++a) acc[t][a] = acc[t][a] + part[t][a];
 }
 
-template <typename S, typename A>
+template <typename S, typename A, int BK>
 __global__ void __launch_bounds__(kApplyThreads, sizeof(A) == 4 ? 2 : 1) k_apply_faces(const BlkDev* __restrict__ blk,
                                                                const int4* __restrict__ items,
                                                                S* const* __restrict__ face_tab,
@@ -244,18 +248,18 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(A) == 4 ? 2 : 1) k_apply
                                                                int K) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<A>* sH = reinterpret_cast<cx<A>*>(smem_raw);       // [kBM][kBN * 9 + 1] (padded rows)
-  cx<A>* sZ = sH + kBM * kSHR;                           // [kBN][3][kBK]
-  cx<A>* sF = sZ + kBN * 3 * kBK;                        // [kBK][9]
+  cx<A>* sZ = sH + kBM * kSHR;                           // [kBN][3][BK]
+  cx<A>* sF = sZ + kBN * 3 * BK;                        // [BK][9]
   const int4 it = items[blockIdx.x];
   const BlkDev& B = blk[it.x];
   const int r = threadIdx.x / kTPR, kq = threadIdx.x % kTPR;
   const int64_t i0 = (int64_t)it.y * kBM;
-  const int k0 = it.z * kBK;
-  const int nk = min(kBK, K - k0);
+  const int k0 = it.z * BK;
+  const int nk = min(BK, K - k0);
   const int64_t M3 = 3 * B.m;
-  cx<A> acc[kBK / kTPR][3];
+  cx<A> acc[BK / kTPR][3];
 #pragma unroll
-  for (int t = 0; t < kBK / kTPR; ++t)
+  for (int t = 0; t < BK / kTPR; ++t)
 #pragma unroll
     for (int a = 0; a < 3; ++a) acc[t][a] = {A(0), A(0)};
   for (int p = 0; p < B.rank; ++p) {
@@ -277,19 +281,19 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(A) == 4 ? 2 : 1) k_apply
           sH[rr * kSHR + jj * 9 + 3 * a + b] =
               (gi < B.m && gq < fr) ? Ld<S, A>::ld(H + (int64_t)gq * M3 + 3 * gi + a) : cx<A>{A(0), A(0)};
         }
-        for (int c = threadIdx.x; c < 3 * kBN * kBK; c += blockDim.x) {
-          const int q = c / kBK, kk = c % kBK;
+        for (int c = threadIdx.x; c < 3 * kBN * BK; c += blockDim.x) {
+          const int q = c / BK, kk = c % BK;
           const int gq = q0 + q;
-          sZ[q * kBK + kk] = (gq < fr && kk < nk) ? Tp[(int64_t)gq * K + k0 + kk] : cx<A>{A(0), A(0)};
+          sZ[q * BK + kk] = (gq < fr && kk < nk) ? Tp[(int64_t)gq * K + k0 + kk] : cx<A>{A(0), A(0)};
         }
         __syncthreads();
-        mac_chunk<A>(acc, sH, sZ, r, kq);
+        mac_chunk<A, BK>(acc, sH, sZ, r, kq);
       }
       continue;
     }
     const S* f = fib_tab[idx];
     __syncthreads();
-    load_f<S, A>(sF, f, k0, nk);
+    load_f<S, A, BK>(sF, f, k0, nk);
     for (int64_t j0 = 0; j0 < B.n; j0 += kBN) {
       __syncthreads();
       for (int c = threadIdx.x; c < kBM * kBN * 9; c += blockDim.x) {
@@ -297,15 +301,15 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(A) == 4 ? 2 : 1) k_apply
         const int64_t gi = i0 + rr, gj = j0 + jj;
         sH[rr * kSHR + rem] = (gi < B.m && gj < B.n) ? Ld<S, A>::ld(H + (gi * B.n + gj) * 9 + rem % 9) : cx<A>{A(0), A(0)};
       }
-      load_z_chunk<S, A>(sZ, sF, Xp, B.c0, j0, B.n, K, k0, nk);
+      load_z_chunk<S, A, BK>(sZ, sF, Xp, B.c0, j0, B.n, K, k0, nk);
       __syncthreads();
-      mac_chunk<A>(acc, sH, sZ, r, kq);
+      mac_chunk<A, BK>(acc, sH, sZ, r, kq);
     }
   }
   const int64_t gi = i0 + r;
   if (gi < B.m)
 #pragma unroll
-    for (int t = 0; t < kBK / kTPR; ++t) {
+    for (int t = 0; t < BK / kTPR; ++t) {
       const int kk = kq + kTPR * t;
       if (kk < nk) {
         double* y = Yp + (((B.r0 + gi) * K + k0 + kk) * 3) * 2;
@@ -317,7 +321,7 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(A) == 4 ? 2 : 1) k_apply
 // T_p = W'^T Z_p for every low-rank face: item (block, slot, tile of kBM
 // rank triples, frequency tile).  Rank column q = 3 r + a of the tile plays
 // the role of row r, component a of k_apply_faces; the result is stored.
-template <typename S, typename A>
+template <typename S, typename A, int BK>
 __global__ void __launch_bounds__(kApplyThreads) k_apply_lr_t(const BlkDev* __restrict__ blk,
                                                               const int4* __restrict__ items,
                                                               S* const* __restrict__ face_tab,
@@ -329,7 +333,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_lr_t(const BlkDev* __re
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<A>* sH = reinterpret_cast<cx<A>*>(smem_raw);
   cx<A>* sZ = sH + kBM * kSHR;
-  cx<A>* sF = sZ + kBN * 3 * kBK;
+  cx<A>* sF = sZ + kBN * 3 * BK;
   const int4 it = items[blockIdx.x];
   const BlkDev& B = blk[it.x];
   const int64_t idx = (int64_t)it.y * nb + it.x;
@@ -338,14 +342,14 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_lr_t(const BlkDev* __re
   const int64_t N3 = 3 * B.n;
   const int r = threadIdx.x / kTPR, kq = threadIdx.x % kTPR;
   const int q0 = it.z * 3 * kBM;
-  const int k0 = it.w * kBK;
-  const int nk = min(kBK, K - k0);
-  cx<A> acc[kBK / kTPR][3];
+  const int k0 = it.w * BK;
+  const int nk = min(BK, K - k0);
+  cx<A> acc[BK / kTPR][3];
 #pragma unroll
-  for (int t = 0; t < kBK / kTPR; ++t)
+  for (int t = 0; t < BK / kTPR; ++t)
 #pragma unroll
     for (int a = 0; a < 3; ++a) acc[t][a] = {A(0), A(0)};
-  load_f<S, A>(sF, fib_tab[idx], k0, nk);
+  load_f<S, A, BK>(sF, fib_tab[idx], k0, nk);
   for (int64_t j0 = 0; j0 < B.n; j0 += kBN) {
     __syncthreads();
     for (int c = threadIdx.x; c < kBM * kBN * 9; c += blockDim.x) {
@@ -357,13 +361,13 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_lr_t(const BlkDev* __re
       sH[rr * kSHR + jj * 9 + 3 * a + b] =
           (gq < fr && gj < B.n) ? Ld<S, A>::ld(Wt + (int64_t)gq * N3 + 3 * gj + b) : cx<A>{A(0), A(0)};
     }
-    load_z_chunk<S, A>(sZ, sF, Xp, B.c0, j0, B.n, K, k0, nk);
+    load_z_chunk<S, A, BK>(sZ, sF, Xp, B.c0, j0, B.n, K, k0, nk);
     __syncthreads();
-    mac_chunk<A>(acc, sH, sZ, r, kq);
+    mac_chunk<A, BK>(acc, sH, sZ, r, kq);
   }
   cx<A>* Tp = T + toff[idx];
 #pragma unroll
-  for (int t = 0; t < kBK / kTPR; ++t) {
+  for (int t = 0; t < BK / kTPR; ++t) {
     const int kk = kq + kTPR * t;
     if (kk < nk)
       for (int a = 0; a < 3; ++a) {
@@ -670,7 +674,7 @@ __global__ void k_apply_dense_p(const BlkDev* __restrict__ blk, const int32_t* _
 }
 
 bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
-  std::vector<int4> items, lr_items, lr_faces, adj_items, adj_lr_items;
+  std::vector<int4> items_v[3], lr_items_v[3], lr_faces, adj_items, adj_lr_items;
   std::vector<int32_t> dense, aca;
   std::vector<int64_t> zoff;
   std::vector<int4> zitems;   // (block, face, 128-column chunk, aca index)
@@ -688,8 +692,9 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
           toff[(size_t)p * nb + b] = tt;
           tt += (int64_t)fr * d->K;
           lr_faces.push_back(make_int4((int)b, p, (int)aca.size(), 0));
-          for (int q = 0; q * 3 * kBM < fr; ++q)
-            for (int kt = 0; kt * kBK < d->K; ++kt) lr_items.push_back(make_int4((int)b, p, q, kt));
+          for (int v = 0; v < 3; ++v)
+            for (int q = 0; q * 3 * kBM < fr; ++q)
+              for (int kt = 0; kt * kApplyBK[v] < d->K; ++kt) lr_items_v[v].push_back(make_int4((int)b, p, q, kt));
           for (int q = 0; q * kAN < fr; ++q)
             for (int kt = 0; kt * kAK < d->K; ++kt) adj_lr_items.push_back(make_int4((int)b, p, q, kt));
         }
@@ -697,18 +702,22 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
       aca.push_back((int32_t)b);
       zoff.push_back(z);
       z += (int64_t)B.rank * B.n * 3;
-      for (int64_t rt = 0; rt * kBM < B.m; ++rt)
-        for (int kt = 0; kt * kBK < d->K; ++kt) items.push_back(make_int4((int)b, (int)rt, kt, 0));
+      for (int v = 0; v < 3; ++v)
+        for (int64_t rt = 0; rt * kBM < B.m; ++rt)
+          for (int kt = 0; kt * kApplyBK[v] < d->K; ++kt) items_v[v].push_back(make_int4((int)b, (int)rt, kt, 0));
       for (int64_t ct = 0; ct * kAN < B.n; ++ct)
         for (int kt = 0; kt * kAK < d->K; ++kt) adj_items.push_back(make_int4((int)b, (int)ct, kt, 0));
     }
   }
   std::vector<void*>* own = &d->allocs;
-  d->n_apply_items = (int64_t)items.size();
+  for (int v = 0; v < 3; ++v) {
+    d->n_apply_items_v[v] = (int64_t)items_v[v].size();
+    d->n_lr_items_v[v] = (int64_t)lr_items_v[v].size();
+  }
+  d->apply_bk = d->K <= 16 ? 16 : (d->K <= 32 ? 32 : 64);
   d->n_dense = (int64_t)dense.size();
   d->n_aca = (int64_t)aca.size();
   d->z_elems = z;
-  d->n_lr_items = (int64_t)lr_items.size();
   d->n_lr_faces = (int64_t)lr_faces.size();
   auto up = [&](auto** dst, const auto& v) -> cudaError_t {
     using T = typename std::decay<decltype(v)>::type::value_type;
@@ -716,12 +725,14 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
     if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
     return e;
   };
-  GCQ_CUDA(ctx, up((int4**)&d->d_apply_items, items));
+  for (int v = 0; v < 3; ++v) {
+    GCQ_CUDA(ctx, up((int4**)&d->d_apply_items_v[v], items_v[v]));
+    GCQ_CUDA(ctx, up((int4**)&d->d_lr_items_v[v], lr_items_v[v]));
+  }
   GCQ_CUDA(ctx, up(&d->d_dense_list, dense));
   GCQ_CUDA(ctx, up(&d->d_aca_list, aca));
   GCQ_CUDA(ctx, up(&d->d_zoff, zoff));
   GCQ_CUDA(ctx, up((int4**)&d->d_zitems, zitems));
-  GCQ_CUDA(ctx, up((int4**)&d->d_lr_items, lr_items));
   GCQ_CUDA(ctx, up((int4**)&d->d_lr_faces, lr_faces));
   GCQ_CUDA(ctx, up(&d->d_toff, toff));
   GCQ_CUDA(ctx, up((int4**)&d->d_adj_items, adj_items));
@@ -741,6 +752,31 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
   return BEM_OK;
 }
 
+// the low-rank T and face launches of the batched apply with frequency tile
+// BK (work lists of variant v)
+template <typename S, typename A, int BK>
+static bem_status apply_faces_bk(bem_ctx* ctx, OpData* d, int v, cudaStream_t st) {
+  // one size per instantiation: the process-wide attribute never changes
+  const size_t smem = sizeof(cx<A>) * (kBM * kSHR + kBN * 3 * BK + BK * 9);
+  if (d->n_lr_items_v[v] > 0) {
+    cudaFuncSetAttribute(k_apply_lr_t<S, A, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_apply_lr_t<S, A, BK><<<(unsigned)d->n_lr_items_v[v], kApplyThreads, smem, st>>>(
+        d->d_blk, (const int4*)d->d_lr_items_v[v], (S* const*)d->d_face, (S* const*)d->d_fib, d->d_frank,
+        d->d_toff, (cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_xp, d->K);
+    GCQ_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
+  }
+  if (d->n_apply_items_v[v] > 0) {
+    cudaFuncSetAttribute(k_apply_faces<S, A, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_apply_faces<S, A, BK><<<(unsigned)d->n_apply_items_v[v], kApplyThreads, smem, st>>>(
+        d->d_blk, (const int4*)d->d_apply_items_v[v], (S* const*)d->d_face, (S* const*)d->d_fib, d->d_frank,
+        d->d_toff, (const cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_xp, (double*)d->d_yp, d->K);
+    GCQ_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
+  }
+  return BEM_OK;
+}
+
 template <typename S, typename A>
 static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaStream_t st) {
   OpData* d = op->d;
@@ -753,23 +789,13 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
     GCQ_CUDA(ctx, cudaMemsetAsync(d->d_yp, 0, sizeof(double2) * 3 * nyp, st));
-    const size_t smem = sizeof(cx<A>) * (kBM * kSHR + kBN * 3 * kBK + kBK * 9);
-    if (d->n_lr_items > 0) {
-      cudaFuncSetAttribute(k_apply_lr_t<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_apply_lr_t<S, A><<<(unsigned)d->n_lr_items, kApplyThreads, smem, st>>>(
-          d->d_blk, (const int4*)d->d_lr_items, (S* const*)d->d_face, (S* const*)d->d_fib, d->d_frank, d->d_toff,
-          (cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_xp, d->K);
-      GCQ_CUDA(ctx, cudaGetLastError());
-      count_launches(1);
+    bem_status rs = BEM_OK;
+    switch (d->apply_bk) {
+      case 16: rs = apply_faces_bk<S, A, 16>(ctx, d, 0, st); break;
+      case 32: rs = apply_faces_bk<S, A, 32>(ctx, d, 1, st); break;
+      default: rs = apply_faces_bk<S, A, 64>(ctx, d, 2, st); break;
     }
-    if (d->n_apply_items > 0) {
-      cudaFuncSetAttribute(k_apply_faces<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_apply_faces<S, A><<<(unsigned)d->n_apply_items, kApplyThreads, smem, st>>>(
-          d->d_blk, (const int4*)d->d_apply_items, (S* const*)d->d_face, (S* const*)d->d_fib, d->d_frank,
-          d->d_toff, (const cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_xp, (double*)d->d_yp, d->K);
-      GCQ_CUDA(ctx, cudaGetLastError());
-      count_launches(1);
-    }
+    if (rs != BEM_OK) return rs;
     if (d->n_dense > 0) {
       dim3 g((unsigned)d->n_dense, (unsigned)d->K);
       k_apply_dense_p<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense,
@@ -875,6 +901,55 @@ bem_status apply(bem_op* op, int mode, int transpose, const void* X, void* Y, cu
                                    : apply_adj_t<float2, float>(op, mode, X, Y, st);
   return op->d->prec == BEM_FP64 ? apply_t<double2, double>(op, mode, X, Y, st)
                                  : apply_t<float2, float>(op, mode, X, Y, st);
+}
+
+// autotune of the batched apply's frequency tile: each variant timed on the
+// operator (one warm-up, three timed applies of zero vectors), fastest kept
+bem_status autotune(bem_op* op, cudaStream_t st, int32_t* bk) {
+  OpData* d = op->d;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  const size_t es = d->prec == BEM_FP64 ? sizeof(double2) : sizeof(float2);
+  void *X = nullptr, *Y = nullptr;
+  GCQ_CUDA(ctx, cudaMalloc(&X, es * 3 * (size_t)d->K * d->n_cols));
+  if (cudaMalloc(&Y, es * 3 * (size_t)d->K * d->n_rows) != cudaSuccess) {
+    cudaFree(X);
+    return set_err(ctx, BEM_ERR_OOM, "bem_op_autotune: out of device memory");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  bem_status res = BEM_OK;
+  cudaError_t ce = cudaMemsetAsync(X, 0, es * 3 * (size_t)d->K * d->n_cols, st);
+  const int32_t keep = d->apply_bk;
+  int best = -1;
+  for (int v = 0; v < 3 && res == BEM_OK && ce == cudaSuccess; ++v) {
+    d->apply_bk = kApplyBK[v];
+    res = apply(op, BEM_APPLY_BATCHED, 0, X, Y, st);
+    if (res == BEM_OK) ce = cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && res == BEM_OK && ce == cudaSuccess; ++r) res = apply(op, BEM_APPLY_BATCHED, 0, X, Y, st);
+    if (res == BEM_OK && ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+    if (res == BEM_OK && ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (res == BEM_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    d->apply_tune_ms[v] = ms / 3.0;
+    if (res == BEM_OK && ce == cudaSuccess && (best < 0 || d->apply_tune_ms[v] < d->apply_tune_ms[best])) best = v;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(X);
+  cudaFree(Y);
+  d->apply_bk = best >= 0 ? kApplyBK[best] : keep;
+  if (res != BEM_OK) return res;
+  if (ce != cudaSuccess) return cuda_err(ctx, ce, "bem_op_autotune");
+  if (bk) *bk = d->apply_bk;
+  return BEM_OK;
+}
+
+bem_status set_apply_tile(bem_op* op, int32_t bk) {
+  if (bk != 16 && bk != 32 && bk != 64)
+    return set_err(op->tree->mesh->ctx, BEM_ERR_ARG, "bem_op_set_apply_tile: the tile must be 16, 32 or 64");
+  op->d->apply_bk = bk;
+  return BEM_OK;
 }
 
 // ---- dense reconstruction: out[(i * n_cols + j) * K + k] -----------------------
@@ -991,6 +1066,8 @@ bem_status op_stats(const bem_op* op, bem_op_stats* s) {
   s->n_faces_lowrank = d->n_faces_lr;
   s->face_rank_mean = d->n_faces_lr ? (double)d->face_rank_sum / d->n_faces_lr : 0.0;
   s->t_face_aca_ms = d->t_face_aca_ms;
+  s->apply_bk = d->apply_bk;
+  for (int v = 0; v < 3; ++v) s->apply_tune_ms[v] = d->apply_tune_ms[v];
   return BEM_OK;
 }
 

@@ -907,6 +907,17 @@ bem_status bem_op_inner(bem_op* op, int32_t mode, const void* G, const void* X, 
   return inner(op, mode, G, X, out, (cudaStream_t)stream);
 }
 
+bem_status bem_op_set_apply_tile(bem_op* op, int32_t bk) {
+  if (!op) return BEM_ERR_ARG;
+  return set_apply_tile(op, bk);
+}
+
+bem_status bem_op_autotune(bem_op* op, void* stream, int32_t* bk) {
+  if (!op) return BEM_ERR_ARG;
+  GCQ_CUDA(op->tree->mesh->ctx, cudaSetDevice(op->tree->mesh->ctx->device));
+  return autotune(op, (cudaStream_t)stream, bk);
+}
+
 bem_status bem_op_face_ranks(const bem_op* op, int32_t* ranks) {
   if (!op || !ranks) return BEM_ERR_ARG;
   return op_face_ranks(op, ranks);

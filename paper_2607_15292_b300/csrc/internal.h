@@ -164,6 +164,8 @@ bem_status op_face_ranks(const bem_op* op, int32_t* ranks);
 bem_status solve(bem_op* op, const void* B, void* X, double tol, int max_iter, int32_t* iters, double* relres,
                  cudaStream_t st);
 bem_status inner(bem_op* op, int mode, const void* G, const void* X, double* out, cudaStream_t st);
+bem_status autotune(bem_op* op, cudaStream_t st, int32_t* bk);
+bem_status set_apply_tile(bem_op* op, int32_t bk);
 bem_status face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, double eps, int32_t* rank, void* out,
                          cudaStream_t st);
 bem_status cq_transform(int N, int64_t nvec, const void* in, void* out, bool inverse, cudaStream_t st);
