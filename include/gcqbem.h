@@ -311,6 +311,23 @@ bem_status bem_op_stats_get(const bem_op* op, bem_op_stats* st);
  * the same.  The autotune allocates an input and an output vector and
  * synchronises the stream. */
 bem_status bem_op_set_apply_tile(bem_op* op, int32_t bk);
+
+/* Checkpoint of a compressed operator.  bem_op_save writes the block table,
+ * face ranks, pivot frequencies, the tree's permutations and every stored
+ * face, factor pair, fibre and dense block (in the operator's storage type)
+ * to the file at path, behind a header with sizes and an FNV-1a 64 checksum
+ * of the payload (copies device -> host; synchronous).  bem_op_load builds
+ * the operator of tree from such a file: the file must come from an
+ * operator of the same kernel, rows and block cluster tree (same mesh, leaf,
+ * eta), and the context must have the same K and precision; the frequencies
+ * and material themselves are not stored (the entries are); a mismatch, a
+ * truncated file or a wrong checksum returns BEM_ERR_ARG and creates
+ * nothing.  The loaded operator applies exactly as the saved one (the apply
+ * work lists are rebuilt); the compression statistics other than counts and
+ * stored bytes read 0.  BEM_ERR_STATE on a host-only context or without
+ * frequencies/material. */
+bem_status bem_op_save(const bem_op* op, const char* path);
+bem_status bem_op_load(bem_tree* tree, const char* path, bem_op** out);
 bem_status bem_op_autotune(bem_op* op, void* stream, int32_t* bk);
 
 /* Per-block results (host, n_blocks x 4 int64): kind (0 aca, 1 dense,

@@ -89,6 +89,8 @@ _SIGS = {
     "bem_op_inner": (_i32, [_vp, _i32, _vp, _vp, _P(_dbl), _vp]),
     "bem_op_compress_batch": (_i32, [_P(_vp), _i32, _i32, _P(_vp)]),
     "bem_op_set_apply_tile": (_i32, [_vp, _i32]),
+    "bem_op_save": (_i32, [_vp, ctypes.c_char_p]),
+    "bem_op_load": (_i32, [_vp, ctypes.c_char_p, _P(_vp)]),
     "bem_op_autotune": (_i32, [_vp, _vp, _P(_i32)]),
     "bem_batch_order": (_i32, [_P(_i64), _i32, _P(_i32)]),
     "bem_face_compress": (_i32, [_vp, _vp, _i64, _i64, _dbl, _P(_i32), _vp, _vp]),
@@ -367,6 +369,17 @@ class Operator:
 
     def apply_adjoint(self, Yin, Xout, mode: int = BEM_APPLY_BATCHED, stream=None):
         self.apply(Yin, Xout, mode, stream, transpose=1)
+
+    def save(self, path: str):
+        """Writes the compressed operator to a file (bem_op_save)."""
+        _check(_lib.bem_op_save(self._p, os.fsencode(path)), self.ctx.ptr)
+
+    @classmethod
+    def load(cls, tree: "Tree", path: str) -> "Operator":
+        """The operator of tree from a file written by save (bem_op_load)."""
+        p = ctypes.c_void_p()
+        _check(_lib.bem_op_load(tree._p, os.fsencode(path), ctypes.byref(p)), tree.mesh.ctx.ptr)
+        return cls._adopt(tree, p.value)
 
     def set_apply_tile(self, bk: int):
         """Frequency tile of the batched apply (16, 32 or 64)."""

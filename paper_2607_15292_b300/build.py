@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgcqbem.so")
 SOURCES = ["host.cpp", "gcqbem.cu"]
-DEPS = ["internal.h", "entry.cuh", "entryf.cuh", "tma.cuh", "aca3d.cuh", "faceaca.cuh", "apply.cuh", "solve.cuh"]
+DEPS = ["internal.h", "entry.cuh", "entryf.cuh", "tma.cuh", "aca3d.cuh", "faceaca.cuh", "apply.cuh", "solve.cuh", "persist.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

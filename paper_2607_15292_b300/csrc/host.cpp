@@ -907,6 +907,35 @@ bem_status bem_op_inner(bem_op* op, int32_t mode, const void* G, const void* X, 
   return inner(op, mode, G, X, out, (cudaStream_t)stream);
 }
 
+bem_status bem_op_save(const bem_op* op, const char* path) {
+  if (!op) return BEM_ERR_ARG;
+  if (!path) return set_err(op->tree->mesh->ctx, BEM_ERR_ARG, "bem_op_save: path is NULL");
+  GCQ_CUDA(op->tree->mesh->ctx, cudaSetDevice(op->tree->mesh->ctx->device));
+  return op_save(op, path);
+}
+
+bem_status bem_op_load(bem_tree* tree, const char* path, bem_op** out) {
+  if (!tree) return BEM_ERR_ARG;
+  bem_ctx* ctx = tree->mesh->ctx;
+  if (!out || !path) return set_err(ctx, BEM_ERR_ARG, "bem_op_load: out or path is NULL");
+  *out = nullptr;
+  if (ctx->device < 0) return set_err(ctx, BEM_ERR_STATE, "bem_op_load: host-only context (device -1)");
+  if (!ctx->has_material) return set_err(ctx, BEM_ERR_STATE, "bem_op_load: material not set");
+  if (ctx->K < 1) return set_err(ctx, BEM_ERR_STATE, "bem_op_load: frequencies not set");
+  GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
+  auto* op = new (std::nothrow) bem_op;
+  if (!op) return set_err(ctx, BEM_ERR_OOM, "bem_op_load: host allocation");
+  op->tree = tree;
+  bem_status s = op_load(tree, path, &op->d);
+  if (s != BEM_OK) {
+    delete op;
+    return s;
+  }
+  tree->refs++;
+  *out = op;
+  return BEM_OK;
+}
+
 bem_status bem_op_set_apply_tile(bem_op* op, int32_t bk) {
   if (!op) return BEM_ERR_ARG;
   return set_apply_tile(op, bk);

@@ -53,3 +53,14 @@ def test_batch_workload_recipe():
     again = syn.batch_meshes(4)
     for (n1, x1, t1, k1), (n2, x2, t2, k2) in zip(b[:4], again):
         assert n1 == n2 and k1 == k2 and np.array_equal(x1, x2) and np.array_equal(t1, t2)
+
+
+def test_op_load_rejects_host_only_context_and_missing_file(tmp_path):
+    ctx = g.Context(device=-1)
+    ctx.material(*syn.STEEL)
+    ctx.freqs([1e3 + 0j])
+    xyz, tri = syn.cube_grid(1)
+    t = ctx.mesh(xyz, tri).tree(g.BEM_ROWS_NODES, g.BEM_SL)
+    with pytest.raises(g.BemError) as e:
+        g.Operator.load(t, str(tmp_path / "absent.op"))
+    assert e.value.status == g.BEM_ERR_STATE
