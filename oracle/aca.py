@@ -288,3 +288,19 @@ def apply_adjoint_dense(C: np.ndarray, Y: np.ndarray) -> np.ndarray:
     frequency k has block (i, j) = C[i, j, k]; its conjugate transpose has
     block (j, i) = C[i, j, k]^H."""
     return np.einsum("ijkab,iak->jbk", C.conj(), Y)
+
+
+def receiver_energy(C: np.ndarray, X: np.ndarray, w: np.ndarray) -> float:
+    """J = sum_k sum_i w_i |(C_k X_k)[i]|^2 (a receiver response): C (M, N,
+    K, 3, 3), X (N, 3, K), w (M,) receiver weights."""
+    Y = apply_dense(C, X)
+    return float((w[:, None, None] * np.abs(Y) ** 2).sum())
+
+
+def receiver_energy_speed_gradient(C: np.ndarray, dC: np.ndarray, X: np.ndarray, w: np.ndarray) -> float:
+    """dJ/dc for one wave speed c, with dC = dC/dc (same layout as C):
+    dJ/dc = 2 Re sum_k sum_i w_i conj(Y_k[i]) . (dC_k X_k)[i], Y = C X (the
+    adjoint field of J is 2 w Y)."""
+    Y = apply_dense(C, X)
+    dY = apply_dense(dC, X)
+    return float(2.0 * np.real((w[:, None, None] * np.conj(Y) * dY).sum()))

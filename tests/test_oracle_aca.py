@@ -133,3 +133,31 @@ def test_adjoint_apply_pins():
     lhs = np.vdot(Y, aca.apply_dense(D, X))               # <y, C x>
     rhs = np.vdot(XA, X)                                  # <C^H y, x>
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("kern,dkern", [(bem.KERNEL_SL, {"p": bem.KERNEL_SL_DCP, "s": bem.KERNEL_SL_DCS}),
+                                        (bem.KERNEL_DL, {"p": bem.KERNEL_DL_DCP, "s": bem.KERNEL_DL_DCS})])
+def test_receiver_energy_speed_gradient_by_fd(kern, dkern):
+    """The wave-speed gradient of a receiver response from the derivative
+    operators against central differences of the response in c_a (rho
+    fixed), single and double layer, node rows."""
+    from oracle import kernels
+    xyz, tri = syn.icosphere(1)
+    s = bem.freqs_bdf2(16, 1e-4, 16)[[0, 5]]
+    rho = syn.STEEL[0]
+    c1, c2 = kernels.wave_speeds(*syn.STEEL)
+    op = bem.Operator(xyz, tri, syn.STEEL, rows=bem.ROWS_NODES, kernel=kern)
+    C = op.dense(s)
+    X = syn.complex_normal(9, (op.n_cols, 3, len(s)))
+    w = (syn.uniform01(9, op.n_rows) < 0.4).astype(np.float64)
+    for wave, c in (("p", c1), ("s", c2)):
+        dC = bem.Operator(xyz, tri, syn.STEEL, rows=bem.ROWS_NODES, kernel=dkern[wave]).dense(s)
+        g = aca.receiver_energy_speed_gradient(C, dC, X, w)
+        h = 1e-4 * c
+
+        def J(dc):
+            cc1, cc2 = (c1 + dc, c2) if wave == "p" else (c1, c2 + dc)
+            mat = (rho,) + kernels.lame_from_speeds(rho, cc1, cc2)
+            return aca.receiver_energy(bem.Operator(xyz, tri, mat, rows=bem.ROWS_NODES, kernel=kern).dense(s), X, w)
+        fd = (-J(2 * h) + 8 * J(h) - 8 * J(-h) + J(-2 * h)) / (12 * h)
+        assert abs(g - fd) <= 1e-7 * abs(fd), (wave, g, fd)
