@@ -859,6 +859,20 @@ static cudaError_t dmalloc(T** p, size_t bytes, std::vector<void*>* owner) {
   return e;
 }
 
+// device buffers and events of one compression call, released on every
+// return path
+struct CallScratch {
+  std::vector<void*> bufs;
+  std::vector<cudaEvent_t> evs;
+  CallScratch() = default;
+  CallScratch(const CallScratch&) = delete;
+  CallScratch& operator=(const CallScratch&) = delete;
+  ~CallScratch() {
+    for (void* p : bufs) cudaFree(p);
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+  }
+};
+
 void free_op(OpData* d) {
   if (!d) return;
   for (void* p : d->allocs) cudaFree(p);
@@ -1173,8 +1187,10 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   d->h_face.assign(nb * K, nullptr);
   d->h_fib.assign(nb * K, nullptr);
   d->h_dense.assign(nb, nullptr);
-  // per-iteration scratch (freed at the end)
-  std::vector<void*> scratch;
+  // per-iteration scratch: freed at the end, or by the guard when an error
+  // returns from the middle of the loop
+  CallScratch scratch_guard, chunk_guard;
+  std::vector<void*>& scratch = scratch_guard.bufs;
   Tile* d_tiles = nullptr;
   int32_t* d_active = nullptr;
   double *p_s3 = nullptr, *p_h2 = nullptr;
@@ -1194,10 +1210,11 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
   cudaEventCreate(&evf);
+  scratch_guard.evs = {ev0, ev1, evf};
   float t_ent = 0.f;
   std::vector<Tile> tiles;
   std::vector<int32_t> active;
-  std::vector<void*> slot_chunks;   // compression-time storage of faces and fibres
+  std::vector<void*>& slot_chunks = chunk_guard.bufs;   // compression-time storage of faces and fibres
   bem_status result = BEM_OK;
   for (int slot = 0; slot < K && result == BEM_OK; ++slot) {
     active.clear();
@@ -1328,10 +1345,9 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   // face ACA of far blocks and final storage of the accepted pairs
   if (result == BEM_OK) result = finalize_storage<R, SC, SF>(ctx, d, st);
   for (void* p : slot_chunks) cudaFree(p);
-  cudaEventDestroy(ev0);
-  cudaEventDestroy(ev1);
-  cudaEventDestroy(evf);
+  slot_chunks.clear();
   for (void* p : scratch) cudaFree(p);
+  scratch.clear();
   if (result != BEM_OK) return result;
   GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_blk, d->h_blk.data(), sizeof(BlkDev) * nb, cudaMemcpyHostToDevice, st));
   bem_status s = build_apply_lists(ctx, d);
