@@ -110,3 +110,25 @@ def test_invalid_input_is_rejected():
     assert g.freqs_bdf2.__doc__
     with pytest.raises(g.BemError):
         g.freqs_bdf2(4, 1e-3, 9)        # K > N + 1
+
+
+def test_derivative_kernel_trees_match_their_layer():
+    """The wave-speed derivative operators share the columns and the block
+    cluster tree of their layer (host-only context); unknown kernel ids are
+    rejected."""
+    ctx = g.Context(device=-1)
+    xyz, tri = syn.icosphere(2)
+    m = ctx.mesh(xyz, tri)
+    for base, derived in ((g.BEM_SL, (g.BEM_SL_DCP, g.BEM_SL_DCS)), (g.BEM_DL, (g.BEM_DL_DCP, g.BEM_DL_DCS))):
+        for rows in (g.BEM_ROWS_NODES, g.BEM_ROWS_CENTROIDS):
+            tb = m.tree(rows, base)
+            rb, cb, bb = tb.export()
+            for k in derived:
+                t = m.tree(rows, k)
+                assert (t.n_rows, t.n_cols, t.n_blocks, t.n_far) == (tb.n_rows, tb.n_cols, tb.n_blocks, tb.n_far)
+                r, c, b = t.export()
+                assert np.array_equal(r, rb) and np.array_equal(c, cb) and np.array_equal(b, bb)
+    for bad in (-1, 6, 99):
+        with pytest.raises(g.BemError) as e:
+            m.tree(g.BEM_ROWS_NODES, bad)
+        assert e.value.status == g.BEM_ERR_ARG
