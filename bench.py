@@ -109,6 +109,7 @@ def cpu_oracle_sample(budget_s: float = 15.0):
     rows = rng.permutation(op.n_rows)
     cols = np.arange(op.n_cols)
     t0 = time.perf_counter()
+    c0 = time.process_time()
     n = 0
     used = 0
     while time.perf_counter() - t0 < budget_s and used < len(rows):
@@ -116,9 +117,21 @@ def cpu_oracle_sample(budget_s: float = 15.0):
         n += op.n_cols * 4
         used += 1
     dt = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
-    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    cpu = time.process_time() - c0
+    return {"value": n / dt, "unit": UNIT, "cores": round(cpu / dt, 2), "kind": "oracle",
+            "cores_how": "process CPU time / wall time over the sample (threads actually busy)",
+            "host_cpus": os.cpu_count(), "cpu_model": _cpu_model(),
             "sample": f"{used} node rows x 5120 elements x 4 frequencies of V ({n} block entries, {dt:.1f} s)"}
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 def run_reference(args):
@@ -398,16 +411,30 @@ def main():
         XV64, XK64 = XV.to(torch.complex128), XK.to(torch.complex128)
         YV64 = torch.empty((K, len(xyz), 3), dtype=torch.complex128, device=dev)
         YK64 = torch.empty_like(YV64)
+        # warm-up: every FP64 kernel launched once (module load, attributes)
+        # on the icosphere-2 mesh, then two timed steps of the workload
+        xw, tw = syn.icosphere(2)
+        cw = g.Context(eps=WORKLOAD["eps"], leaf=WORKLOAD["leaf"], eta=WORKLOAD["eta"], precision=g.BEM_FP64,
+                       device=local)
+        cw.material(*syn.STEEL)
+        cw.freqs(s)
+        mw = cw.mesh(xw, tw)
+        for kern, ncol in ((g.BEM_SL, len(tw)), (g.BEM_DL, len(xw))):
+            ow = mw.tree(g.BEM_ROWS_NODES, kern).compress(stream)
+            ow.apply(torch.zeros((K, ncol, 3), dtype=torch.complex128, device=dev),
+                     torch.empty((K, len(xw), 3), dtype=torch.complex128, device=dev), g.BEM_APPLY_BATCHED, stream)
         torch.cuda.synchronize()
+        fp64_steps = 2
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         b0.record(stream)
-        oV64 = tV64.compress(stream)
-        oK64 = tK64.compress(stream)
-        oV64.apply(XV64, YV64, g.BEM_APPLY_BATCHED, stream)
-        oK64.apply(XK64, YK64, g.BEM_APPLY_BATCHED, stream)
+        for _ in range(fp64_steps):
+            oV64 = tV64.compress(stream)
+            oK64 = tK64.compress(stream)
+            oV64.apply(XV64, YV64, g.BEM_APPLY_BATCHED, stream)
+            oK64.apply(XK64, YK64, g.BEM_APPLY_BATCHED, stream)
         b1.record(stream)
         torch.cuda.synchronize()
-        ms64 = b0.elapsed_time(b1)
+        ms64 = b0.elapsed_time(b1) / fp64_steps
         e64 = oV64.stats().entries_evaluated + oK64.stats().entries_evaluated
         oV.apply(XV, YV, g.BEM_APPLY_BATCHED, stream)
         oK.apply(XK, YK, g.BEM_APPLY_BATCHED, stream)
@@ -415,6 +442,7 @@ def main():
         errV = (torch.linalg.norm(YV.to(torch.complex128) - YV64) / torch.linalg.norm(YV64)).item()
         errK = (torch.linalg.norm(YK.to(torch.complex128) - YK64) / torch.linalg.norm(YK64)).item()
         extra.update({"fp64_entries_per_s": e64 / (ms64 / 1e3), "fp64_ms_per_step": ms64,
+                      "fp64_timing": f"{fp64_steps} steps after an FP64 warm-up on icosphere level 2",
                       "mixed_vs_fp64_speedup": (ms64 / 1e3) / (ms / args.steps / 1e3),
                       "mixed_vs_fp64_rel_err_V": errV, "mixed_vs_fp64_rel_err_K": errK,
                       "fp64_vs_exact_rel_err_V": rel(YV64[:, rs], YV_ex),

@@ -156,8 +156,10 @@ bem_status bem_entries(bem_mesh* mesh, int32_t rows, int32_t kernel,
 
 /* bem_entries without any device allocation.  The paper has no
  * counterpart; this is a service to callers that cannot call cudaMalloc
- * during the call: code running while a CUDA graph is captured, inside
- * another framework's memory pool or real-time loop, or under a fixed,
+ * during the call: code that runs inside another framework's memory pool
+ * (which owns the device memory and must not see allocations beside it),
+ * real-time loops where an allocation's latency and implicit
+ * synchronisation are not allowed, and programs held to a fixed,
  * pre-reserved memory budget.  Same requests, output and precision as
  * bem_entries; the range-check scratch that bem_entries allocates per call
  * is a static device array of 256 words (1 KiB) instead, which every device
@@ -165,18 +167,22 @@ bem_status bem_entries(bem_mesh* mesh, int32_t rows, int32_t kernel,
  *  - At most 16,777,216 requests per call (256 words x 65,536 requests);
  *    larger n returns BEM_ERR_ARG before any device work.
  *  - The first call on a device looks the array's device address up
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.  Later calls only memset, launch and copy
- *    1 KiB back.
+ *    (cudaGetSymbolAddress, with that device current) and keeps it for the
+ *    life of the process (a cudaDeviceReset of that device invalidates it,
+ *    as it does every other device object of the library); make that first
+ *    call before any stream capture.  Later calls only clear the words they
+ *    use, launch and copy at most 1 KiB back.
  *  - All calls share the array: calls whose device work overlaps (other
  *    streams, other host threads) race on it and must be serialised by the
- *    caller.  The words used are reset at the start of every call.
+ *    caller.  The words a call uses are cleared at its start.
  *  - BEM_DL (BEM_DL_DCP, BEM_DL_DCS) with BEM_ROWS_NODES needs the mesh's
- *    rigid-body diagonal (its nu-derivative), which is computed (and
- *    allocated) by the first bem_entries or bem_op_compress of that kind on
- *    the mesh; without it this call returns BEM_ERR_STATE.
- *  - Synchronises the stream; an out-of-range request yields a NaN block and
- *    BEM_ERR_ARG naming the first offending request. */
+ *    rigid-body diagonal (its nu-derivative) for the context's current
+ *    material, which is computed (and allocated) by the first bem_entries or
+ *    bem_op_compress of that kind on the mesh after bem_material_set;
+ *    without it this call returns BEM_ERR_STATE.
+ *  - Synchronises the stream before it returns (it reads the range-check
+ *    words back); an out-of-range request yields a NaN block and BEM_ERR_ARG
+ *    naming the first offending request. */
 bem_status bem_entries_noalloc(bem_mesh* mesh, int32_t rows, int32_t kernel,
                                const int32_t* req, int64_t n, void* out, void* stream);
 
@@ -251,7 +257,8 @@ bem_status bem_op_apply(bem_op* op, int32_t mode, int32_t transpose,
  * and final relative residual per frequency.  Allocates 6 K n 3 complex of
  * device scratch per call and synchronises the stream every iteration.
  * BEM_ERR_NOT_CONVERGED when a frequency ends above tol (breakdown or
- * max_iter); X then holds the last iterate. */
+ * max_iter); X then holds the last iterate.  BEM_ERR_ARG when some b_k holds
+ * a NaN or an infinity (its relres reads NaN, X holds zeros). */
 bem_status bem_op_solve(bem_op* op, const void* B, void* X, double tol, int32_t max_iter,
                         int32_t* iters, double* relres, void* stream);
 
@@ -357,6 +364,21 @@ bem_status bem_op_face_ranks(const bem_op* op, int32_t* ranks);
  * k (m + n) >= 3 m n), out untouched.  Synchronises the stream. */
 bem_status bem_face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, double eps_face,
                              int32_t* rank, void* out, void* stream);
+
+/* Fault injection for tests (the paper has no counterpart), process-wide,
+ * off by default:
+ *  BEM_DEBUG_FACE_WAIT_FAIL (value != 0): the 3D-ACA face kernel treats every
+ *    staged copy of a previous face as not landed once it has landed, so the
+ *    compression takes its timeout path (no further copy issued, the copies
+ *    in flight drained, an error flag read by the host) and returns
+ *    BEM_ERR_CUDA with no copy left in flight; the context stays usable.
+ *  BEM_DEBUG_ALLOC_CAP (value >= 0 bytes, 0 = off): every device allocation
+ *    of the compression larger than value fails as if the device were out of
+ *    memory, so bem_op_compress returns BEM_ERR_OOM after releasing what it
+ *    holds.
+ * BEM_ERR_ARG for another `what` or a negative cap. */
+typedef enum { BEM_DEBUG_FACE_WAIT_FAIL = 1, BEM_DEBUG_ALLOC_CAP = 2 } bem_debug;
+bem_status bem_debug_set(int32_t what, int64_t value);
 
 /* Number of CUDA kernels this library has launched in the process so far
  * (all contexts); used to count the device work of a timed region. */

@@ -34,6 +34,8 @@ BEM_SL_DCP, BEM_SL_DCS = 2, 3
 # and of the double layer C + K, d(C + K)/dc_p and d(C + K)/dc_s
 BEM_DL_DCP, BEM_DL_DCS = 4, 5
 BEM_APPLY_BATCHED, BEM_APPLY_CONTRACTED = 0, 1
+# fault injection for tests (bem_debug_set)
+BEM_DEBUG_FACE_WAIT_FAIL, BEM_DEBUG_ALLOC_CAP = 1, 2
 
 _STATUS = {0: "BEM_OK", 1: "BEM_ERR_ARG", 2: "BEM_ERR_CUDA", 3: "BEM_ERR_OOM", 4: "BEM_ERR_MESH",
            5: "BEM_ERR_NOT_CONVERGED", 6: "BEM_ERR_STATE"}
@@ -95,6 +97,7 @@ _SIGS = {
     "bem_batch_order": (_i32, [_P(_i64), _i32, _P(_i32)]),
     "bem_face_compress": (_i32, [_vp, _vp, _i64, _i64, _dbl, _P(_i32), _vp, _vp]),
     "bem_kernel_launches": (_i64, []),
+    "bem_debug_set": (_i32, [_i32, _i64]),
     "bem_cq_forward": (_i32, [_i32, _i64, _vp, _vp, _vp]),
     "bem_cq_inverse": (_i32, [_i32, _i64, _vp, _vp, _vp]),
 }
@@ -131,6 +134,32 @@ def _dptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _device_tensor(name, t, dtype, shape, device):
+    """Refuses (ValueError, before any library call) a buffer the C ABI
+    would misread: not a CUDA tensor on the context's device, another dtype,
+    another shape, or not contiguous (the library writes by pointer and
+    size, so any of these would read or write outside the buffer)."""
+    if not hasattr(t, "data_ptr") or not hasattr(t, "is_cuda"):
+        raise ValueError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor (it is on {t.device})")
+    if device is not None and device >= 0 and t.device.index != device:
+        raise ValueError(f"{name}: on cuda:{t.device.index}, the context is on cuda:{device}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if t.numel() and t.data_ptr() % 16:
+        raise ValueError(f"{name}: must be 16-byte aligned")
+
+
+def _cdtype(precision):
+    import torch
+    return torch.complex128 if precision == BEM_FP64 else torch.complex64
+
+
 def options_default() -> bem_options:
     o = bem_options()
     _check(_lib.bem_options_default(ctypes.byref(o)))
@@ -157,6 +186,12 @@ def compress_batch(trees, n_streams: int = 4) -> list:
     return [Operator._adopt(t, out[i]) for i, t in enumerate(trees)]
 
 
+def debug_set(what: int, value: int):
+    """Process-wide fault injection for tests (bem_debug_set): a failed
+    staged-copy wait in the face kernel, or a cap on device allocations."""
+    _check(_lib.bem_debug_set(int(what), int(value)))
+
+
 def kernel_launches() -> int:
     """Kernels launched by the library in this process so far."""
     return int(_lib.bem_kernel_launches())
@@ -169,11 +204,23 @@ def freqs_bdf2(N: int, dt: float, K: int) -> np.ndarray:
     return out[0::2] + 1j * out[1::2]
 
 
+def _cq_args(N, nvec, x, out):
+    import torch
+    for name, t in (("x", x), ("out", out)):
+        _device_tensor(name, t, torch.complex128, (N + 1, nvec), None)
+    if x.data_ptr() == out.data_ptr():
+        raise ValueError("cq: in and out must not overlap")
+
+
 def cq_forward(N: int, nvec: int, x, out, stream=None):
+    """Scaled DFT of N + 1 levels of nvec complex128 values (L x nvec)."""
+    _cq_args(N, nvec, x, out)
     _check(_lib.bem_cq_forward(N, nvec, _dptr(x), _dptr(out), _stream_ptr(stream)))
 
 
 def cq_inverse(N: int, nvec: int, x, out, stream=None):
+    """Inverse of cq_forward (L x nvec complex128)."""
+    _cq_args(N, nvec, x, out)
     _check(_lib.bem_cq_inverse(N, nvec, _dptr(x), _dptr(out), _stream_ptr(stream)))
 
 
@@ -189,6 +236,7 @@ class Context:
         self._p = ctypes.c_void_p()
         _check(_lib.bem_ctx_create(ctypes.byref(o), ctypes.byref(self._p)), None)
         self.precision = precision
+        self.device = device
         self.K = 0
 
     @property
@@ -226,7 +274,12 @@ class Context:
         m x n x 3 x 3); out (device, >= 9 m n complex of the context's
         precision) receives U' (3m x k) then W' (3n x k) column-major.
         Returns k, or -1 when the face stays dense."""
+        import torch
         m, n = int(H.shape[0]), int(H.shape[1])
+        _device_tensor("H", H, torch.complex128, (m, n, 3, 3), self.device)
+        if out.numel() < 9 * m * n:
+            raise ValueError(f"out: needs at least {9 * m * n} complex values")
+        _device_tensor("out", out, _cdtype(self.precision), tuple(out.shape), self.device)
         rk = ctypes.c_int32(-2)
         _check(_lib.bem_face_compress(self.ptr, _dptr(H), m, n, float(eps_face), ctypes.byref(rk), _dptr(out),
                                       _stream_ptr(stream)), self.ptr)
@@ -250,17 +303,27 @@ class Mesh:
         except Exception:
             pass
 
+    def _entry_args(self, req, out):
+        import torch
+        n = int(req.shape[0]) if hasattr(req, "shape") and len(req.shape) == 2 else -1
+        if n < 0:
+            raise ValueError("req: expected an (n, 3) int32 CUDA tensor")
+        _device_tensor("req", req, torch.int32, (n, 3), self.ctx.device)
+        _device_tensor("out", out, _cdtype(self.ctx.precision), (n, 3, 3), self.ctx.device)
+        return n
+
     def entries(self, rows: int, kernel: int, req, out, stream=None):
         """req: int32 CUDA tensor (n, 3) of (row, col, k); out: complex CUDA
-        tensor (n, 3, 3) (complex128 in FP64, complex64 in MIXED)."""
-        n = req.shape[0]
+        tensor (n, 3, 3) (complex128 in FP64, complex64 in MIXED), both
+        contiguous on the context's device (checked before the call)."""
+        n = self._entry_args(req, out)
         _check(_lib.bem_entries(self._p, rows, kernel, _dptr(req), n, _dptr(out), _stream_ptr(stream)),
                self.ctx.ptr)
 
     def entries_noalloc(self, rows: int, kernel: int, req, out, stream=None):
         """As entries(), through bem_entries_noalloc: no device allocation in
         the call (static 1 KiB scratch, at most 16,777,216 requests)."""
-        n = req.shape[0]
+        n = self._entry_args(req, out)
         _check(_lib.bem_entries_noalloc(self._p, rows, kernel, _dptr(req), n, _dptr(out), _stream_ptr(stream)),
                self.ctx.ptr)
 
@@ -350,15 +413,34 @@ class Operator:
         except Exception:
             pass
 
+    def _shapes(self, mode, transpose):
+        """(input shape, output shape) of the apply in this mode."""
+        K, nr, nc = self.K, self.tree.n_rows, self.tree.n_cols
+        if mode not in (BEM_APPLY_BATCHED, BEM_APPLY_CONTRACTED):
+            raise ValueError(f"mode: {mode} is neither BEM_APPLY_BATCHED nor BEM_APPLY_CONTRACTED")
+        if not transpose:
+            return (K, nc, 3), ((K, nr, 3) if mode == BEM_APPLY_BATCHED else (nr, 3))
+        return ((K, nr, 3) if mode == BEM_APPLY_BATCHED else (nr, 3)), (K, nc, 3)
+
     def apply(self, X, Y, mode: int = BEM_APPLY_BATCHED, stream=None, transpose: int = 0):
         """transpose = 0: Y = C X; transpose = 1: Y = C^H X (X is then the
-        row-side input, Y the column-side output)."""
+        row-side input, Y the column-side output).  Shapes, dtype (complex128
+        in FP64, complex64 in MIXED), device and contiguity are checked first."""
+        sin, sout = self._shapes(mode, transpose)
+        cdt = _cdtype(self.ctx.precision)
+        _device_tensor("input", X, cdt, sin, self.ctx.device)
+        _device_tensor("output", Y, cdt, sout, self.ctx.device)
         _check(_lib.bem_op_apply(self._p, mode, transpose, _dptr(X), _dptr(Y), _stream_ptr(stream)), self.ctx.ptr)
 
     def solve(self, B, X, tol: float = 1e-8, max_iter: int = 200, stream=None, check: bool = True):
         """X_k = C(s_k)^{-1} B_k for all k (BiCGstab); returns (iterations,
         relative residuals) per frequency.  With check=False a frequency that
         did not converge is not an error (the residuals tell)."""
+        if self.tree.n_rows != self.tree.n_cols:
+            raise ValueError("solve: the operator is not square")
+        cdt = _cdtype(self.ctx.precision)
+        _device_tensor("B", B, cdt, (self.K, self.tree.n_rows, 3), self.ctx.device)
+        _device_tensor("X", X, cdt, (self.K, self.tree.n_rows, 3), self.ctx.device)
         it = np.zeros(self.K, dtype=np.int32)
         rr = np.zeros(self.K, dtype=np.float64)
         st = _lib.bem_op_solve(self._p, _dptr(B), _dptr(X), float(tol), int(max_iter),
@@ -394,12 +476,19 @@ class Operator:
 
     def inner(self, G, X, mode: int = BEM_APPLY_BATCHED, stream=None) -> complex:
         """<G, C X> (bem_op_inner): sum of conj(G) times the apply of X."""
+        sin, sout = self._shapes(mode, 0)
+        cdt = _cdtype(self.ctx.precision)
+        _device_tensor("G", G, cdt, sout, self.ctx.device)
+        _device_tensor("X", X, cdt, sin, self.ctx.device)
         out = np.zeros(2, dtype=np.float64)
         _check(_lib.bem_op_inner(self._p, mode, _dptr(G), _dptr(X), out.ctypes.data_as(_P(_dbl)),
                                  _stream_ptr(stream)), self.ctx.ptr)
         return complex(out[0], out[1])
 
     def dense(self, out, stream=None):
+        """Dense reconstruction into out (n_rows, n_cols, K, 3, 3)."""
+        _device_tensor("out", out, _cdtype(self.ctx.precision),
+                       (self.tree.n_rows, self.tree.n_cols, self.K, 3, 3), self.ctx.device)
         _check(_lib.bem_op_dense(self._p, _dptr(out), _stream_ptr(stream)), self.ctx.ptr)
 
     def stats(self) -> Stats:

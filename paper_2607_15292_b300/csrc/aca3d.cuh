@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
                                                 const int32_t* __restrict__ col_perm, double* __restrict__ p_s3,
                                                 int64_t* __restrict__ p_idx, double* __restrict__ p_h2,
                                                 double2* __restrict__ p_M, const double* __restrict__ hn2, int K,
-                                                int* __restrict__ err) {
+                                                int* __restrict__ err, int dbg_fail) {
   using W = typename WorkOf<S>::W;
   // Previous faces stream through shared memory: the tile's 256 entries of a
   // face are one contiguous range (256 x 9 x 16 B = 36 KB), copied by one
@@ -326,21 +326,37 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   const int64_t nval = min((int64_t)kTile, B.m * B.n - t.start);
   const uint32_t tile_bytes = (uint32_t)(nval * 9 * (int64_t)sizeof(S));
   const int nload = 2 * slot;
+  // A wait that gives up (or, with dbg_fail, a wait that completed: fault
+  // injection for tests) sets kf_fail; from the next CTA barrier on, no thread
+  // waits and thread 0 issues no further copy, so that at most the last two
+  // issued copies can still be in flight, and thread 0 drains them at the end.
+  __shared__ volatile int kf_fail;
+  int n_issued = 0;   // thread 0: copies issued
   auto issue = [&](int n) {   // thread 0 only
     const int pf = n < slot ? n : 2 * slot - 1 - n;
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&kf_bar[n & 1], tile_bytes);
     bulk_copy_g2s(fbuf0 + (n & 1) * (kTile * 9), face_tab[(int64_t)pf * nb + t.blk] + t.start * 9, tile_bytes,
                   &kf_bar[n & 1]);
+    n_issued = n + 1;
   };
   if (threadIdx.x == 0) {
+    kf_fail = 0;
     mbar_init(&kf_bar[0], 1);
     mbar_init(&kf_bar[1], 1);
     fence_mbar_init();
     if (nload > 0) issue(0);
     if (nload > 1) issue(1);
   }
-  int waited_ok = 1;   // every barrier wait of this thread completed
+  // copy n is usable: it was issued (no failure before the barrier that
+  // preceded its issue) and it landed
+  auto wait_copy = [&](int n) -> bool {
+    if (kf_fail) return false;
+    const bool landed = mbar_wait(&kf_bar[n & 1], (n >> 1) & 1);
+    if (!landed || dbg_fail) kf_fail = 1;
+    return landed && !dbg_fail;
+  };
+  int waited_ok = 1;   // every copy this thread used had landed
   float fh[18], fl[18];           // float-float accumulators (MIXED)
   cx<double> Hd64[9];             // double accumulators (FP64)
   int i = 0, j = 0;
@@ -416,7 +432,7 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
     }
     for (int p = 0; p < np; ++p) {
       const int n = p0 + p;   // copy n holds face n
-      if (!mbar_wait(&kf_bar[n & 1], (n >> 1) & 1)) waited_ok = 0;
+      if (!wait_copy(n)) waited_ok = 0;
       if (ok && waited_ok) {
         S cur[9];
         {
@@ -472,7 +488,7 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
         }
       }
       __syncthreads();   // every thread is done with copy n: its buffer takes copy n + 2
-      if (threadIdx.x == 0 && n + 2 < nload) issue(n + 2);
+      if (threadIdx.x == 0 && n + 2 < nload && !kf_fail) issue(n + 2);
     }
   }
   S* Hd = face_tab[(int64_t)slot * nb + t.blk];
@@ -521,7 +537,7 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
     for (int pp = 0; pp < np; ++pp) {
       const int q = p0 + pp;          // p = slot - q
       const int n = slot + q - 1;     // copy holding face p (q > 0)
-      if (q > 0 && !mbar_wait(&kf_bar[n & 1], (n >> 1) & 1)) waited_ok = 0;
+      if (q > 0 && !wait_copy(n)) waited_ok = 0;
       W g[32];
       for (int c = 0; c < 32; ++c) g[c] = W(0);
       if (ok && waited_ok) {
@@ -552,7 +568,7 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
       if (lane < 18) gw[wid][pp][lane] = tot;
       if (q > 0) {
         __syncthreads();   // every thread is done with copy n
-        if (threadIdx.x == 0 && n + 2 < nload) issue(n + 2);
+        if (threadIdx.x == 0 && n + 2 < nload && !kf_fail) issue(n + 2);
       }
     }
     __syncthreads();
@@ -566,10 +582,11 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
     __syncthreads();
   }
   // a copy that did not land in time: flag it for the host (which abandons
-  // the compression) and give the copies still in flight a bounded wait
-  if (__syncthreads_or(!waited_ok) && threadIdx.x == 0) {
+  // the compression) and give the last two issued copies, the only ones that
+  // can still be in flight, a bounded wait before the CTA exits
+  if (__syncthreads_or(!waited_ok || kf_fail) && threadIdx.x == 0) {
     atomicExch(err, 1);
-    for (int n = max(0, nload - 2); n < nload; ++n) mbar_wait(&kf_bar[n & 1], (n >> 1) & 1);
+    for (int n = max(0, n_issued - 2); n < n_issued; ++n) mbar_wait(&kf_bar[n & 1], (n >> 1) & 1);
   }
 }
 
@@ -854,6 +871,8 @@ __global__ void __launch_bounds__(kTile) k_dense_fill(EntryView v, const Tile* _
 // ---- host driver ---------------------------------------------------------------
 template <typename T>
 static cudaError_t dmalloc(T** p, size_t bytes, std::vector<void*>* owner) {
+  const int64_t cap = debug_alloc_cap();   // fault injection for tests (bem_debug_set)
+  if (cap > 0 && bytes > (size_t)cap) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMalloc((void**)p, bytes > 0 ? bytes : 16);
   if (e == cudaSuccess && owner) owner->push_back((void*)*p);
   return e;
@@ -1264,7 +1283,7 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
                                        (int)kf_smem),
                   k_face<R, SC, KK, RR><<<(unsigned)tiles.size(), kTile, kf_smem, st>>>(
                      v, d_tiles, d->d_blk, (S* const*)d->d_face, (S* const*)d->d_fib, nb, slot, d->d_row_perm,
-                     d->d_col_perm, p_s3, p_idx, p_h2, p_M, d->d_hn2, K, d_err)));
+                     d->d_col_perm, p_s3, p_idx, p_h2, p_M, d->d_hn2, K, d_err, debug_face_wait_fail())));
     GCQ_CUDA(ctx, cudaGetLastError());
     cudaEventRecord(evf, st);
     d->face_launches++;

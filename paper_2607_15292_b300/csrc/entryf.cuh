@@ -169,9 +169,13 @@ __device__ __forceinline__ void vert_f(const FrameF& f, int a, float* P) {
 
 // exp(-s r0 / c_a), a = 1, 2, at a reference distance r0 (an FP32 number):
 // the phase (Im s / c_a) r0 is formed as a float-float product and reduced
-// modulo 2 pi with a two-part 2 pi; the magnitude exp(-(Re s / c_a) r0) gets
-// the low part of its exponent as a first-order factor.  Removes the FP32
-// error proportional to |s| r / c of exp(-s r / c) evaluated at full r.
+// modulo 2 pi by Cody and Waite's additive reduction (W. J. Cody and
+// W. Waite, Software Manual for the Elementary Functions, 1980): 2 pi split
+// into a leading part C1 = fl(2 pi) and a correction C2 = 2 pi - C1, the
+// product nt C1 subtracted exactly by FMA, then nt C2 added; the magnitude
+// exp(-(Re s / c_a) r0) gets the low part of its exponent as a first-order
+// factor.  Removes the FP32 error proportional to |s| r / c of
+// exp(-s r / c) evaluated at full r.
 __device__ __forceinline__ void ref_exp(const EntryView& v, int k, float r0, cx<float>* E0, cx<float>* w) {
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
@@ -181,7 +185,7 @@ __device__ __forceinline__ void ref_exp(const EntryView& v, int k, float r0, cx<
     float pe = fmaf(q.z, r0, -ph);
     pe = fmaf(q.w, r0, pe);
     const float nt = rintf(ph * 0.159154943091895336f);
-    float t = fmaf(-nt, 6.28318548202514648f, ph);   // 2 pi = 6.2831854820 - 1.7484556e-7
+    float t = fmaf(-nt, 6.28318548202514648f, ph);   // Cody-Waite: C1 = fl(2 pi), C2 = 2 pi - C1 = -1.7484556e-7
     t = fmaf(nt, 1.74845553e-07f, t) + pe;
     const float mg = q.x * r0;
     float me = fmaf(q.x, r0, -mg);

@@ -24,6 +24,11 @@ namespace gcq {
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches += n; }
 
+static std::atomic<int> g_dbg_face_wait_fail{0};
+static std::atomic<int64_t> g_dbg_alloc_cap{0};
+int debug_face_wait_fail() { return g_dbg_face_wait_fail.load(); }
+int64_t debug_alloc_cap() { return g_dbg_alloc_cap.load(); }
+
 // ---------------------------------------------------------------------------
 // quadrature tables (host-built, uploaded once per device)
 // ---------------------------------------------------------------------------
@@ -225,11 +230,22 @@ __global__ void k_rigid_body(EntryView v, double* __restrict__ rb) {
   if (threadIdx.x < 9) rb[9 * (int64_t)i + threadIdx.x] = -red[threadIdx.x][0];
 }
 
+// the diagonal depends on Poisson's ratio: built for the context's current
+// material, and rebuilt when bem_material_set has changed it since
+bool rigid_body_current(const bem_mesh* m, bool dnu) {
+  return (dnu ? m->d_rb_dnu : m->d_rb) != nullptr && (dnu ? m->rb_dnu_gen : m->rb_gen) == m->ctx->mat_gen;
+}
+
 bem_status ensure_rigid_body(bem_mesh* m, cudaStream_t st, bool dnu) {
+  if (rigid_body_current(m, dnu)) return BEM_OK;
   double*& rb = dnu ? m->d_rb_dnu : m->d_rb;
-  if (rb) return BEM_OK;
   bem_ctx* ctx = m->ctx;
+  if (rb) {   // stale (older material): cudaFree waits for the kernels still reading it
+    GCQ_CUDA(ctx, cudaFree(rb));
+    rb = nullptr;
+  }
   GCQ_CUDA(ctx, cudaMalloc(&rb, sizeof(double) * 9 * m->n_nodes));
+  (dnu ? m->rb_dnu_gen : m->rb_gen) = ctx->mat_gen;
   EntryView v = make_view(m);
   if (dnu)
     k_rigid_body<true><<<(unsigned)m->n_nodes, 256, 0, st>>>(v, rb);
@@ -264,16 +280,17 @@ bem_status launch_entries(bem_mesh* m, int rows, int kernel, const int32_t* req,
 // ---------------------------------------------------------------------------
 // no-allocation variant of the raw-request entry kernel
 //
-// For callers that must not allocate device memory during a call: code that
-// runs while a CUDA graph is being captured, inside another framework's
-// memory pool or real-time loop, or under a pre-reserved memory budget.  The
-// range-check scratch that bem_entries allocates per call lives here in a
-// file-scope device array instead: kNoAllocSlots words, word w holding the
-// smallest offending request index of requests [w * kNoAllocChunk, (w + 1) *
-// kNoAllocChunk), so one call handles at most kNoAllocSlots * kNoAllocChunk
-// requests.  Every device that loads the library holds the array (1 KiB)
-// until the process exits; all calls share it, so calls that overlap on the
-// GPU race on it.
+// For callers that must not allocate device memory during a call: code
+// inside another framework's memory pool, real-time loops that cannot take
+// an allocation's latency or implicit synchronisation, programs under a
+// pre-reserved memory budget.  The range-check scratch that bem_entries
+// allocates per call lives here in a file-scope device array instead:
+// kNoAllocSlots words, word w holding the smallest offending request index
+// of requests [w * kNoAllocChunk, (w + 1) * kNoAllocChunk), so one call
+// handles at most kNoAllocSlots * kNoAllocChunk requests.  Every device that
+// loads the library holds the array (1 KiB) until the process exits; all
+// calls share it, so calls that overlap on the GPU race on it.  The call
+// reads the words back and synchronises the stream.
 // ---------------------------------------------------------------------------
 constexpr int kNoAllocSlots = 256;
 constexpr int64_t kNoAllocChunk = 65536;
@@ -304,7 +321,9 @@ __global__ void k_entries_req_noalloc(EntryView v, const int32_t* __restrict__ r
 }
 
 // device address of the scratch for the context's (current) device, resolved
-// once per device with cudaGetSymbolAddress
+// once per device with cudaGetSymbolAddress and kept for the life of the
+// process (a cudaDeviceReset of the device would invalidate it together with
+// every other device object of the library)
 static bem_status noalloc_scratch(bem_ctx* ctx, unsigned int** out) {
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
@@ -335,10 +354,10 @@ extern "C" bem_status bem_entries_noalloc(bem_mesh* mesh, int32_t rows, int32_t 
   if (ctx->device < 0) return set_err_c(ctx, BEM_ERR_STATE, "bem_entries_noalloc: host-only context (device -1)");
   if (!ctx->has_material) return set_err_c(ctx, BEM_ERR_STATE, "bem_entries_noalloc: material not set");
   if (ctx->K < 1) return set_err_c(ctx, BEM_ERR_STATE, "bem_entries_noalloc: frequencies not set");
-  if (!kern_sl(kernel) && rows == BEM_ROWS_NODES && !(kern_dc(kernel) ? mesh->d_rb_dnu : mesh->d_rb))
+  if (!kern_sl(kernel) && rows == BEM_ROWS_NODES && !rigid_body_current(mesh, kern_dc(kernel) != 0))
     return set_err_c(ctx, BEM_ERR_STATE,
-                     "bem_entries_noalloc: rigid-body diagonal not prepared; call bem_entries or bem_op_compress "
-                     "once for this mesh with this kernel and BEM_ROWS_NODES first");
+                     "bem_entries_noalloc: rigid-body diagonal not prepared for the current material; call "
+                     "bem_entries or bem_op_compress once for this mesh with this kernel and BEM_ROWS_NODES first");
   if (n == 0) return BEM_OK;
   GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
   unsigned int* slots = nullptr;
@@ -382,3 +401,14 @@ namespace gcq {}  // aca3d.cuh and apply.cuh reopen the namespace
 #include "persist.cuh"
 
 extern "C" int64_t bem_kernel_launches(void) { return gcq::g_launches.load(); }
+
+extern "C" bem_status bem_debug_set(int32_t what, int64_t value) {
+  switch (what) {
+    case BEM_DEBUG_FACE_WAIT_FAIL: gcq::g_dbg_face_wait_fail = value != 0; return BEM_OK;
+    case BEM_DEBUG_ALLOC_CAP:
+      if (value < 0) return BEM_ERR_ARG;
+      gcq::g_dbg_alloc_cap = value;
+      return BEM_OK;
+    default: return BEM_ERR_ARG;
+  }
+}

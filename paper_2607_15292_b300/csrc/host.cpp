@@ -448,6 +448,7 @@ bem_status bem_material_set(bem_ctx* ctx, double rho, double lambda, double mu, 
   m.nu = lambda / (2.0 * (lambda + mu));
   series_tables(m.c1, m.c2, m.ta, m.tb);
   ctx->has_material = true;
+  ctx->mat_gen++;   // cached per-mesh quantities of the old material (rigid-body diagonals) are stale
   if (c1) *c1 = m.c1;
   if (c2) *c2 = m.c2;
   return update_wave_table(ctx);
@@ -649,6 +650,7 @@ void bem_mesh_destroy(bem_mesh* m) {
 
 bem_status bem_entries(bem_mesh* mesh, int32_t rows, int32_t kernel, const int32_t* req, int64_t n, void* out,
                        void* stream) {
+  gcq::NvtxRange nvtx("bem_entries");
   if (!mesh) return BEM_ERR_ARG;
   bem_ctx* ctx = mesh->ctx;
   if ((rows != BEM_ROWS_CENTROIDS && rows != BEM_ROWS_NODES) || !gcq::kern_valid(kernel) || n < 0 ||
@@ -730,6 +732,7 @@ bem_status bem_tree_export(const bem_tree* t, int32_t* rp, int32_t* cp, int64_t*
 }
 
 bem_status bem_op_compress(bem_tree* tree, void* stream, bem_op** out) {
+  gcq::NvtxRange nvtx("bem_op_compress");
   if (!tree) return BEM_ERR_ARG;
   bem_ctx* ctx = tree->mesh->ctx;
   if (!out) return set_err(ctx, BEM_ERR_ARG, "bem_op_compress: out is NULL");
@@ -765,6 +768,7 @@ bem_status bem_batch_order(const int64_t* cost, int32_t n, int32_t* order) {
 }
 
 bem_status bem_op_compress_batch(bem_tree* const* trees, int32_t n, int32_t n_streams, bem_op** out) {
+  gcq::NvtxRange nvtx("bem_op_compress_batch");
   if (!trees || !out || n < 1 || n_streams < 1) return BEM_ERR_ARG;
   for (int32_t i = 0; i < n; ++i) {
     out[i] = nullptr;
@@ -846,6 +850,7 @@ void bem_op_destroy(bem_op* op) {
 }
 
 bem_status bem_op_apply(bem_op* op, int32_t mode, int32_t transpose, const void* X, void* Y, void* stream) {
+  gcq::NvtxRange nvtx("bem_op_apply");
   if (!op) return BEM_ERR_ARG;
   bem_ctx* ctx = op->tree->mesh->ctx;
   if ((mode != BEM_APPLY_BATCHED && mode != BEM_APPLY_CONTRACTED) || (transpose != 0 && transpose != 1) || !X || !Y)
@@ -884,6 +889,7 @@ bem_status bem_face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, 
 
 bem_status bem_op_solve(bem_op* op, const void* B, void* X, double tol, int32_t max_iter, int32_t* iters,
                         double* relres, void* stream) {
+  gcq::NvtxRange nvtx("bem_op_solve");
   if (!op) return BEM_ERR_ARG;
   bem_ctx* ctx = op->tree->mesh->ctx;
   if (!B || !X || !iters || !relres || !(tol > 0 && tol < 1) || max_iter < 1 || B == X)
@@ -897,6 +903,7 @@ bem_status bem_op_solve(bem_op* op, const void* B, void* X, double tol, int32_t 
 }
 
 bem_status bem_op_inner(bem_op* op, int32_t mode, const void* G, const void* X, double* out, void* stream) {
+  gcq::NvtxRange nvtx("bem_op_inner");
   if (!op) return BEM_ERR_ARG;
   bem_ctx* ctx = op->tree->mesh->ctx;
   if ((mode != BEM_APPLY_BATCHED && mode != BEM_APPLY_CONTRACTED) || !G || !X || !out)

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cstdint>
@@ -73,6 +74,7 @@ struct bem_ctx {
   std::string err;
   bool has_material = false;
   gcq::Material mat{};
+  uint64_t mat_gen = 0;           // incremented by every bem_material_set
   int32_t K = 0;
   std::vector<double> s;          // 2K
   double2* d_s = nullptr;         // s_k
@@ -99,6 +101,8 @@ struct bem_mesh {
   int32_t* d_ne_loc = nullptr;
   double* d_rb = nullptr;         // rigid-body static diagonal (node rows), n_nodes x 9, lazily
   double* d_rb_dnu = nullptr;     // its derivative in nu (wave-speed derivative operators), lazily
+  uint64_t rb_gen = 0;            // ctx->mat_gen when d_rb was built (the diagonal depends on nu)
+  uint64_t rb_dnu_gen = 0;        // ctx->mat_gen when d_rb_dnu was built
   float4* d_ef = nullptr;         // FP32 element frames: [p0 - c, 2 area], [e1, 0], [e2, 0], [n, 0]
   float4* d_cff = nullptr;        // centroids as float pairs: [c_hi, h], [c_lo, 0] per element
   float4* d_nff = nullptr;        // nodes as float pairs: [x_hi, 0], [x_lo, 0] per node
@@ -130,12 +134,24 @@ struct bem_op {
 
 namespace gcq {
 
+// NVTX range over a library call (header-only NVTX v3: no cost unless a
+// profiler is attached); names the calls on an nsys/ncu timeline
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // error helpers -------------------------------------------------------------
 bem_status set_err(bem_ctx* ctx, bem_status st, const std::string& msg);
 // as set_err, copying into the context's preallocated message buffer (no
 // host allocation for messages shorter than its reserved capacity)
 bem_status set_err_c(bem_ctx* ctx, bem_status st, const char* msg);
 void count_launches(int64_t n);
+// fault injection for tests (bem_debug_set), process-wide
+int debug_face_wait_fail();
+int64_t debug_alloc_cap();
 bem_status cuda_err(bem_ctx* ctx, cudaError_t e, const char* what);
 
 #define GCQ_CUDA(ctx, call)                                         \
@@ -152,6 +168,7 @@ bem_status build_trees(bem_tree* t);
 // device-side entry points (entry.cu, aca3d.cu, apply.cu, cq.cu) ---------------
 bem_status upload_quadrature(bem_ctx* ctx);
 bem_status ensure_rigid_body(bem_mesh* mesh, cudaStream_t st, bool dnu);
+bool rigid_body_current(const bem_mesh* mesh, bool dnu);
 bem_status launch_entries(bem_mesh* mesh, int rows, int kernel, const int32_t* req, int64_t n,
                           void* out, int* d_flag, cudaStream_t st);
 bem_status compress(bem_tree* tree, cudaStream_t st, OpData** out);

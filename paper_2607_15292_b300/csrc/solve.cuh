@@ -115,10 +115,14 @@ static bem_status solve_t(bem_op* op, const void* Bv, void* Xv, double tol, int 
   if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, 2 * vb, st);
   if (e == cudaSuccess) e = dot(b, b);
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
-    bn[k] = std::sqrt(std::max(hd[k].x, 0.0));
-    done[k] = !(bn[k] > 0.0);
     iters[k] = 0;
     relres[k] = 0.0;
+    if (!std::isfinite(hd[k].x)) {   // NaN or Inf in b_k: refused, not taken for a zero right-hand side
+      relres[k] = NAN;
+      res = set_err(ctx, BEM_ERR_ARG, "bem_op_solve: non-finite right-hand side");
+    }
+    bn[k] = std::sqrt(std::max(hd[k].x, 0.0));
+    done[k] = !(bn[k] > 0.0);
   }
   int it = 0;
   while (e == cudaSuccess && res == BEM_OK) {

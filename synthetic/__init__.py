@@ -16,7 +16,8 @@ import numpy as np
 
 __all__ = [
     "STEEL", "PAPER_CUBE_MATERIAL", "lame_from_young",
-    "cube_grid", "paper_cube", "refine", "icosphere", "ellipsoid",
+    "cube_grid", "paper_cube", "refine", "icosphere", "ellipsoid", "cube_sphere", "slotted_cylinder",
+    "SLOTTED_CYLINDER", "batch_meshes",
     "splitmix64", "uniform01", "normal", "complex_normal",
 ]
 
@@ -179,6 +180,127 @@ def cube_sphere(n: int, radius: float = 1.0) -> tuple[np.ndarray, np.ndarray]:
     given radius: 12 n^2 triangles."""
     xyz, tri = cube_grid(n)
     return radius * xyz / np.linalg.norm(xyz, axis=1, keepdims=True), tri
+
+
+def _orient_outward(xyz: np.ndarray, tri: np.ndarray) -> np.ndarray:
+    """Makes the orientation of a closed triangulated surface consistent
+    (breadth-first walk over shared edges: a neighbour must traverse the
+    shared edge in the opposite direction), then outward (positive enclosed
+    volume by the divergence theorem)."""
+    tri = tri.copy()
+    edge_tris = {}
+    for t, (a, b, c) in enumerate(tri):
+        for u, v in ((a, b), (b, c), (c, a)):
+            edge_tris.setdefault((min(u, v), max(u, v)), []).append(t)
+    seen = np.zeros(len(tri), dtype=bool)
+    for start in range(len(tri)):
+        if seen[start]:
+            continue
+        seen[start] = True
+        stack = [start]
+        while stack:
+            t = stack.pop()
+            a, b, c = tri[t]
+            for u, v in ((a, b), (b, c), (c, a)):
+                for o in edge_tris[(min(u, v), max(u, v))]:
+                    if o == t or seen[o]:
+                        continue
+                    oa, ob, oc = tri[o]
+                    same = (u, v) in ((oa, ob), (ob, oc), (oc, oa))
+                    if same:          # traverses the shared edge the same way: flip
+                        tri[o] = tri[o][[0, 2, 1]]
+                    seen[o] = True
+                    stack.append(o)
+    P = xyz[tri]
+    vol = np.einsum("ij,ij->i", P[:, 0], np.cross(P[:, 1], P[:, 2])).sum() / 6.0
+    return tri if vol > 0 else tri[:, [0, 2, 1]]
+
+
+#: slotted hollow cylinder of the large configuration: outer radius 0.3 m,
+#: inner radius 0.2 m, length 0.5 m, 36 axial slots cut into the bore,
+#: 0.02 m deep, 4 degrees wide, full length
+SLOTTED_CYLINDER = dict(r_out=0.3, r_in=0.2, length=0.5, slots=36, depth=0.02, slot_deg=4.0)
+
+
+def slotted_cylinder(n_half_land: int = 2, n_wall: int = 2, n_bottom: int = 3, n_z: int = 40, n_r: int = 7,
+                     r_out: float = 0.3, r_in: float = 0.2, length: float = 0.5, slots: int = 36,
+                     depth: float = 0.02, slot_deg: float = 4.0) -> tuple[np.ndarray, np.ndarray]:
+    """Closed surface of a hollow cylinder (axis z, 0 <= z <= length) whose
+    bore carries `slots` axial slots of the given depth and angular width.
+
+    Every node lies on one polar grid (repeated at the axial levels): per
+    slot pitch U = 2 n_half_land + n_bottom angles (half land, slot, half
+    land, from the middle of one land to the middle of the next) and the
+    radii r_in + depth k / n_wall (k = 0..n_wall, the slot walls) then
+    r_in + depth + (r_out - r_in - depth) l / n_r (l = 1..n_r).  The bore
+    profile of a pitch has S = 2 n_half_land + 2 n_wall + n_bottom segments
+    (land at r_in, wall out, slot bottom at r_in + depth, wall back, land);
+    the outer circle has U segments per pitch; the lateral surfaces have
+    n_z axial segments; the end caps are the polar cells of the material
+    (all angles beyond the slot bottoms, the land angles below them).  Every
+    quadrilateral is split into two triangles along the diagonal whose
+    smaller triangle is the larger: 2 slots [n_z (S + U) + 2 (U n_r +
+    2 n_half_land n_wall)] triangles of a genus-one surface (V - E + F = 0).
+    The defaults give 60,048 triangles, the size of the large configuration."""
+    land = 2.0 * np.pi / slots - np.deg2rad(slot_deg)
+    hl = 0.5 * land
+    wslot = np.deg2rad(slot_deg)
+    pitch = 2.0 * np.pi / slots
+    U = 2 * n_half_land + n_bottom
+    a_loc = np.concatenate([hl * np.arange(n_half_land) / n_half_land,
+                            hl + wslot * np.arange(n_bottom) / n_bottom,
+                            hl + wslot + hl * np.arange(n_half_land) / n_half_land])
+    ang = (np.arange(slots)[:, None] * pitch + a_loc[None, :]).ravel()            # slots * U angles
+    NA = len(ang)
+    radii = np.concatenate([r_in + depth * np.arange(n_wall + 1) / n_wall,
+                            r_in + depth + (r_out - r_in - depth) * np.arange(1, n_r + 1) / n_r])
+    top = len(radii) - 1
+    # bore profile of one pitch as (radius level, local angle index)
+    prof = [(0, u) for u in range(n_half_land)]
+    prof += [(k, n_half_land) for k in range(n_wall)]
+    prof += [(n_wall, n_half_land + u) for u in range(n_bottom)]
+    prof += [(n_wall - k, n_half_land + n_bottom) for k in range(n_wall)]
+    prof += [(0, n_half_land + n_bottom + u) for u in range(n_half_land)]
+    S = len(prof)
+    bore = [(k, p * U + u) for p in range(slots) for k, u in prof]
+    zs = np.linspace(0.0, length, n_z + 1)
+    node = {}
+    pts = []
+
+    def nd(j, k, u):
+        key = (j, k, u % NA)
+        if key not in node:
+            node[key] = len(pts)
+            a = ang[u % NA]
+            pts.append((radii[k] * np.cos(a), radii[k] * np.sin(a), zs[j]))
+        return node[key]
+    quads = []
+    for j in range(n_z):
+        for i in range(len(bore)):
+            (k0, u0), (k1, u1) = bore[i], bore[(i + 1) % len(bore)]
+            if u1 < u0:
+                u1 += NA
+            quads.append((nd(j, k0, u0), nd(j, k1, u1), nd(j + 1, k1, u1), nd(j + 1, k0, u0)))
+        for u in range(NA):
+            quads.append((nd(j, top, u), nd(j, top, u + 1), nd(j + 1, top, u + 1), nd(j + 1, top, u)))
+    land_seg = [u for u in range(U) if u < n_half_land or u >= n_half_land + n_bottom]
+    for j in (0, n_z):
+        for k in range(top):
+            segs = range(NA) if k >= n_wall else [p * U + u for p in range(slots) for u in land_seg]
+            for u in segs:
+                quads.append((nd(j, k, u), nd(j, k, u + 1), nd(j, k + 1, u + 1), nd(j, k + 1, u)))
+    xyz = np.array(pts, dtype=np.float64)
+    q = np.array(quads, dtype=np.int64)
+
+    def area2(a, b, c):
+        return np.linalg.norm(np.cross(xyz[b] - xyz[a], xyz[c] - xyz[a]), axis=1)
+    d02 = np.minimum(area2(q[:, 0], q[:, 1], q[:, 2]), area2(q[:, 0], q[:, 2], q[:, 3]))
+    d13 = np.minimum(area2(q[:, 0], q[:, 1], q[:, 3]), area2(q[:, 1], q[:, 2], q[:, 3]))
+    use13 = d13 > d02
+    t1 = np.where(use13[:, None], q[:, [0, 1, 3]], q[:, [0, 1, 2]])
+    t2 = np.where(use13[:, None], q[:, [1, 2, 3]], q[:, [0, 2, 3]])
+    tri = np.concatenate([t1, t2])
+    return xyz, _orient_outward(xyz, tri).astype(np.int32)
 
 
 def batch_meshes(count: int = 32, n_max: int = 25):

@@ -8,6 +8,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+@pytest.fixture()
+def record(request):
+    """record(name, value): appends a measured error or timing to the JSON
+    lines file named by GCQ_RECORD (when set), tagged with the test id, so
+    that the tolerances in the tests can be compared with measured values."""
+    import json
+    path = os.environ.get("GCQ_RECORD")
+
+    def _rec(name, value):
+        if path:
+            with open(path, "a") as f:
+                f.write(json.dumps({"test": request.node.nodeid, "name": name, "value": float(value)}) + "\n")
+    return _rec
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
     config.addinivalue_line("markers", "slow: longer CPU test")

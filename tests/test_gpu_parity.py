@@ -20,6 +20,12 @@ from oracle import aca, bem  # noqa: E402
 ROWS = {"nodes": 1, "centroids": 0}
 KERN = {"sl": 0, "dl": 1}
 N_C1, DT_C1, K_C1 = 16, 1e-4, 16
+# per-block relative error bound of the MIXED (FP32) entries: u = 2^-24 times
+# the cancellation of the kernel formulas (series below |s| r / c2 = 2,
+# closed form above: at most e^2 < 2^3), of the quadrature sum over an
+# element whose phase varies by |s| h / c2 (at most 2^2 on these meshes), and
+# 2^3 for the 3 x 3 products and the float-float phase reduction
+MIXED_BLOCK_TOL = 2.0 ** -16
 
 
 def _ctx(s, precision=0, eps=1e-6, leaf=32, eta=2.0, material=syn.STEEL):
@@ -84,7 +90,7 @@ def test_entries_static_kernel(rows, kern):
 
 
 @pytest.mark.parametrize("name,rows,kern", CASES[:4])
-def test_entries_mixed(name, rows, kern):
+def test_entries_mixed(name, rows, kern, record):
     xyz, tri = _mesh(name)
     s = bem.freqs_bdf2(N_C1, DT_C1, K_C1)
     ctx = _ctx(s, precision=1)
@@ -96,8 +102,12 @@ def test_entries_mixed(name, rows, kern):
     req = [(i, j, k) for i in range(m) for j in range(n) for k in ks]
     got = _gpu_entries(mesh, rows, kern, req, 1)
     want = np.stack([D[i, j, ks.index(k)] for i, j, k in req])
-    assert np.linalg.norm(got - want) <= 1e-6 * np.linalg.norm(want)
-    assert _block_err(got, want, 1e-6 * np.abs(want).max()) < 2e-5
+    eg = np.linalg.norm(got - want) / np.linalg.norm(want)
+    eb = _block_err(got, want, 1e-6 * np.abs(want).max())
+    record("mixed_entries_global", eg)
+    record("mixed_entries_block_max", eb)
+    assert eg <= 1e-6, eg
+    assert eb < MIXED_BLOCK_TOL, eb
 
 
 def test_entries_out_of_range_request_reports_error():
@@ -136,7 +146,7 @@ def _meshx(name):
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name,rows,kern,leaf", [("cube2", "centroids", "sl", 8), ("cube2", "centroids", "dl", 8),
                                                  ("ico2", "nodes", "sl", 16), ("ico2", "nodes", "dl", 16)])
-def test_aca3d_tensor_and_apply(name, rows, kern, leaf, precision):
+def test_aca3d_tensor_and_apply(name, rows, kern, leaf, precision, record):
     eps = 1e-6
     s = bem.freqs_bdf2(N_C1, DT_C1, K_C1)
     xyz, tri = _meshx(name)
@@ -151,7 +161,8 @@ def test_aca3d_tensor_and_apply(name, rows, kern, leaf, precision):
     op.dense(out)
     C = out.cpu().numpy().astype(np.complex128)
     err = np.linalg.norm(C - D) / np.linalg.norm(D)
-    assert err < 10 * eps, err
+    record("tensor_vs_dense", err)
+    assert err < eps, err
     # batched apply Y_k = C_k X_k
     K = len(s)
     X = syn.complex_normal(1, (K, D.shape[1], 3))
@@ -160,17 +171,21 @@ def test_aca3d_tensor_and_apply(name, rows, kern, leaf, precision):
     op.apply(Xt, Yt, g.BEM_APPLY_BATCHED)
     Y = Yt.cpu().numpy()
     Yd = np.einsum("ijkab,kjb->kia", D, X)
-    assert np.linalg.norm(Y - Yd) / np.linalg.norm(Yd) < 10 * eps
+    ea = np.linalg.norm(Y - Yd) / np.linalg.norm(Yd)
+    record("apply_vs_dense", ea)
+    assert ea < eps, ea
     # contracted apply y = sum_k C_k X_k
     yt = torch.empty((D.shape[0], 3), dtype=cdt, device="cuda")
     op.apply(Xt, yt, g.BEM_APPLY_CONTRACTED)
     y = yt.cpu().numpy()
-    assert np.linalg.norm(y - Yd.sum(0)) / np.linalg.norm(Yd.sum(0)) < 10 * eps
+    ec = np.linalg.norm(y - Yd.sum(0)) / np.linalg.norm(Yd.sum(0))
+    record("contracted_vs_dense", ec)
+    assert ec < eps, ec
     if precision == 0 and name == "ico2":
         assert st.n_far > 0
 
 
-def test_aca3d_against_oracle_compression_config1():
+def test_aca3d_against_oracle_compression_config1(record):
     """Cube 4x4 squares per face (192 triangles), centroid rows, K = 16:
     GPU and oracle compressed tensors both within eps of the dense tensor."""
     eps = 1e-6
@@ -189,9 +204,11 @@ def test_aca3d_against_oracle_compression_config1():
     for b in blocks:
         Co[np.ix_(b.rows, b.cols)] = aca.block_tensor(b, len(s))
     nD = np.linalg.norm(D)
-    assert np.linalg.norm(C - D) / nD < 10 * eps
-    assert np.linalg.norm(Co - D) / nD < 10 * eps
-    assert np.linalg.norm(C - Co) / nD < 20 * eps
+    eg, eo = np.linalg.norm(C - D) / nD, np.linalg.norm(Co - D) / nD
+    record("config1_gpu_vs_dense", eg)
+    record("config1_oracle_vs_dense", eo)
+    assert eg < eps and eo < eps, (eg, eo)
+    assert np.linalg.norm(C - Co) / nD < 2 * eps
 
 
 # --------------------------------------------------------------------------
@@ -221,7 +238,7 @@ def test_cq_transforms_match_oracle(N, nvec):
 # accuracy of the compressed operator against exact rows, both precisions
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("kern", ["sl", "dl"])
-def test_compressed_apply_within_eps_of_exact_rows(kern):
+def test_compressed_apply_within_eps_of_exact_rows(kern, record):
     """Icosphere level 3 (1,280 triangles, 642 nodes), node rows, K = 64
     frequencies of N = 64, dt = 2e-5 (the sphere workload's frequency set),
     eps = 1e-6: the batched apply of the compressed operator, FP64 and MIXED,
@@ -248,4 +265,30 @@ def test_compressed_apply_within_eps_of_exact_rows(kern):
         op.apply(torch.tensor(X, dtype=cdt, device="cuda"), Yt, g.BEM_APPLY_BATCHED)
         Y = Yt.cpu().numpy().astype(np.complex128)[:, rows]
         err = np.linalg.norm(Y - Yex) / np.linalg.norm(Yex)
+        record(f"exact_rows_p{precision}", err)
         assert err < eps, (precision, err)
+
+
+def test_material_change_rebuilds_rigid_body_diagonal():
+    """The rigid-body diagonal of node rows depends on Poisson's ratio: after
+    bem_material_set changes the material, double-layer entries and the
+    compressed operator follow the new material (against the oracle)."""
+    xyz, tri = syn.cube_grid(2)
+    s = bem.freqs_bdf2(N_C1, DT_C1, 4)
+    ctx = _ctx(s)
+    mesh = ctx.mesh(xyz, tri)
+    ks = [0, 3]
+    req = [(i, j, k) for i in range(len(xyz)) for j in range(len(xyz)) for k in ks]
+    _gpu_entries(mesh, "nodes", "dl", req, 0)            # builds the diagonal for steel
+    alu = (2700.0,) + syn.lame_from_young(7.0e10, 0.33)
+    ctx.material(*alu)
+    got = _gpu_entries(mesh, "nodes", "dl", req, 0)
+    D = bem.Operator(xyz, tri, alu, rows="nodes", kernel="dl").dense(s[ks])
+    want = np.stack([D[i, j, ks.index(k)] for i, j, k in req])
+    assert _block_err(got, want, 1e-12 * np.abs(want).max()) < 1e-10
+    t = mesh.tree(ROWS["nodes"], KERN["dl"])
+    op = t.compress()
+    out = torch.empty((len(xyz), len(xyz), len(s), 3, 3), dtype=torch.complex128, device="cuda")
+    op.dense(out)
+    Dall = bem.Operator(xyz, tri, alu, rows="nodes", kernel="dl").dense(s)
+    assert np.linalg.norm(out.cpu().numpy() - Dall) / np.linalg.norm(Dall) < 1e-6
