@@ -305,6 +305,14 @@ typedef struct {
   int64_t apply_bk;             /* frequency tile of the batched apply (16, 32, 64) */
   double apply_tune_ms[3];      /* batched-apply times of tiles 16, 32, 64 from
                                    bem_op_autotune (0: not timed)           */
+  int64_t apply_kernel;         /* batched apply: 0 SIMT, 1 tensor cores    */
+  int64_t apply_errors;         /* nonzero if a tensor-core apply gave up a
+                                   bounded wait (its output is then invalid);
+                                   reading it synchronises the device       */
+  double apply_tensor_flops;    /* TF32 flops of one tensor-core batched apply:
+                                   per face and frequency 24 x rows x columns
+                                   (8 flops per complex multiply-add, three
+                                   split products per real product)         */
 } bem_op_stats;
 bem_status bem_op_stats_get(const bem_op* op, bem_op_stats* st);
 
@@ -318,6 +326,35 @@ bem_status bem_op_stats_get(const bem_op* op, bem_op_stats* st);
  * the same.  The autotune allocates an input and an output vector and
  * synchronises the stream. */
 bem_status bem_op_set_apply_tile(bem_op* op, int32_t bk);
+
+/* Kernel of the batched apply (Eq. (3.15)) of a MIXED operator: 1 (the
+ * default) the tensor-core kernel, 0 the SIMT kernel.  The tensor-core
+ * kernel forms each face's complex product on the fifth-generation tensor
+ * cores (tcgen05, kind::tf32): every FP32 operand split into two TF32
+ * parts, three products per real product (hi hi + hi lo + lo hi), FP32
+ * accumulation in tensor memory read out per face, FP64 accumulation across
+ * blocks.  FP64 operators always use the SIMT kernel (kind 1 on them:
+ * BEM_ERR_ARG).  The contracted and adjoint applies are SIMT in both. */
+bem_status bem_op_set_apply_kernel(bem_op* op, int32_t kind);
+
+/* Self-test of the tensor-core operand layout: D = A B^T computed by one
+ * CTA through the shared-memory layout, descriptors, MMA issue and
+ * tensor-memory read-out of the tensor-core apply (the paper has no
+ * counterpart).  A: host 128 x 32 floats, B: host 64 x 32 floats (row-major,
+ * values meant to be exact in TF32), D: host 128 x 64 floats.  Allocates
+ * and synchronises; BEM_ERR_CUDA if the device work failed or a bounded
+ * wait gave up. */
+bem_status bem_tc_selftest(int32_t device, const float* A, const float* B, float* D);
+
+/* Measured throughput of the execution units that bound this library's
+ * kernels, the roofline denominators of their measurements (the paper has
+ * no counterpart): out (host, 7 doubles) receives FP32 FMA TFLOP/s, FP64 FMA
+ * TFLOP/s, ex2 (special-function unit) Tops/s, tcgen05 kind::tf32 TFLOP/s at
+ * M = 128, N = 128 and at M = 128, N = 256 (operands in shared memory), the
+ * SM clock in MHz measured during the runs, and the SM count.  Every rate
+ * is work / CUDA-event time of one launch over all SMs after a warm-up
+ * launch.  Allocates, synchronises the device, takes about a second. */
+bem_status bem_measure_peaks(int32_t device, double* out);
 
 /* Checkpoint of a compressed operator.  bem_op_save writes the block table,
  * face ranks, pivot frequencies, the tree's permutations and every stored

@@ -58,7 +58,9 @@ class bem_op_stats(ctypes.Structure):
                 ("face_launches", ctypes.c_int64), ("face_alg_bytes", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("n_faces", ctypes.c_int64), ("n_faces_lowrank", ctypes.c_int64),
                 ("face_rank_mean", ctypes.c_double), ("t_face_aca_ms", ctypes.c_double),
-                ("apply_bk", ctypes.c_int64), ("apply_tune_ms", ctypes.c_double * 3)]
+                ("apply_bk", ctypes.c_int64), ("apply_tune_ms", ctypes.c_double * 3),
+                ("apply_kernel", ctypes.c_int64), ("apply_errors", ctypes.c_int64),
+                ("apply_tensor_flops", ctypes.c_double)]
 
 
 _vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -91,6 +93,9 @@ _SIGS = {
     "bem_op_inner": (_i32, [_vp, _i32, _vp, _vp, _P(_dbl), _vp]),
     "bem_op_compress_batch": (_i32, [_P(_vp), _i32, _i32, _P(_vp)]),
     "bem_op_set_apply_tile": (_i32, [_vp, _i32]),
+    "bem_op_set_apply_kernel": (_i32, [_vp, _i32]),
+    "bem_tc_selftest": (_i32, [_i32, _P(ctypes.c_float), _P(ctypes.c_float), _P(ctypes.c_float)]),
+    "bem_measure_peaks": (_i32, [_i32, _P(_dbl)]),
     "bem_op_save": (_i32, [_vp, ctypes.c_char_p]),
     "bem_op_load": (_i32, [_vp, ctypes.c_char_p, _P(_vp)]),
     "bem_op_autotune": (_i32, [_vp, _vp, _P(_i32)]),
@@ -190,6 +195,27 @@ def debug_set(what: int, value: int):
     """Process-wide fault injection for tests (bem_debug_set): a failed
     staged-copy wait in the face kernel, or a cap on device allocations."""
     _check(_lib.bem_debug_set(int(what), int(value)))
+
+
+def measure_peaks(device: int = 0) -> dict:
+    """Measured unit throughputs on the device (bem_measure_peaks)."""
+    out = np.zeros(7, dtype=np.float64)
+    _check(_lib.bem_measure_peaks(int(device), out.ctypes.data_as(_P(_dbl))))
+    keys = ("fp32_tflops", "fp64_tflops", "mufu_ex2_tops", "tf32_tflops_n128", "tf32_tflops_n256", "sm_mhz", "sms")
+    return dict(zip(keys, out.tolist()))
+
+
+def tc_selftest(A, B, device: int = 0):
+    """D = A B^T (A 128 x 32, B 64 x 32 float32) through the tensor-core
+    operand layout of the apply (bem_tc_selftest); returns D (128 x 64)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    if A.shape != (128, 32) or B.shape != (64, 32):
+        raise ValueError("tc_selftest: A must be 128 x 32 and B 64 x 32")
+    D = np.zeros((128, 64), dtype=np.float32)
+    fp = _P(ctypes.c_float)
+    _check(_lib.bem_tc_selftest(int(device), A.ctypes.data_as(fp), B.ctypes.data_as(fp), D.ctypes.data_as(fp)))
+    return D
 
 
 def kernel_launches() -> int:
@@ -386,6 +412,9 @@ class Stats:
     t_face_aca_ms: float
     apply_bk: int
     apply_tune_ms: tuple
+    apply_kernel: int
+    apply_errors: int
+    apply_tensor_flops: float
 
 
 class Operator:
@@ -462,6 +491,11 @@ class Operator:
         p = ctypes.c_void_p()
         _check(_lib.bem_op_load(tree._p, os.fsencode(path), ctypes.byref(p)), tree.mesh.ctx.ptr)
         return cls._adopt(tree, p.value)
+
+    def set_apply_kernel(self, kind: int):
+        """Batched-apply kernel of a MIXED operator: 1 tensor cores (default),
+        0 SIMT (bem_op_set_apply_kernel)."""
+        _check(_lib.bem_op_set_apply_kernel(self._p, int(kind)), self.ctx.ptr)
 
     def set_apply_tile(self, bk: int):
         """Frequency tile of the batched apply (16, 32 or 64)."""

@@ -16,8 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgcqbem.so")
-SOURCES = ["host.cpp", "gcqbem.cu"]
-DEPS = ["internal.h", "entry.cuh", "entryf.cuh", "tma.cuh", "aca3d.cuh", "faceaca.cuh", "apply.cuh", "solve.cuh", "persist.cuh"]
+SOURCES = ["host.cpp", "gcqbem.cu", "apply_tc.cu", "peaks.cu"]
+DEPS = ["internal.h", "opdata.h", "entry.cuh", "entryf.cuh", "tma.cuh", "tc.cuh", "aca3d.cuh", "faceaca.cuh",
+        "apply.cuh", "solve.cuh", "persist.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,14 +38,25 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, ptxas_verbose: bool = False) -> str:
+    """Compiles every source to an object in parallel (one nvcc per
+    translation unit), then links the shared library."""
     if not force and not _stale():
         return LIB
-    cmd = [nvcc(), "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-O3", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "--expt-relaxed-constexpr",
-           *(os.path.join(CSRC, f) for f in SOURCES), "-o", LIB + ".tmp", "-lcudart"]
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    common = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-O3", "-I", os.path.join(ROOT, "include"),
+              "-I", CSRC, "--expt-relaxed-constexpr"]
     if ptxas_verbose:
-        cmd[1:1] = ["-Xptxas", "-v"]
-    subprocess.run(cmd, check=True)
+        common = ["-Xptxas", "-v"] + common
+    procs, objs = [], []
+    for f in SOURCES:
+        obj = os.path.join(objdir, os.path.splitext(f)[0] + ".o")
+        objs.append(obj)
+        procs.append(subprocess.Popen([nvcc(), *common, "-c", os.path.join(CSRC, f), "-o", obj]))
+    bad = [f for f, p in zip(SOURCES, procs) if p.wait() != 0]
+    if bad:
+        raise RuntimeError(f"nvcc failed on {bad}")
+    subprocess.run([nvcc(), *ARCH, "-shared", *objs, "-o", LIB + ".tmp", "-lcudart"], check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

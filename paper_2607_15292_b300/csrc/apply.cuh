@@ -729,6 +729,17 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
     GCQ_CUDA(ctx, up((int4**)&d->d_apply_items_v[v], items_v[v]));
     GCQ_CUDA(ctx, up((int4**)&d->d_lr_items_v[v], lr_items_v[v]));
   }
+  if (d->prec != BEM_FP64) {
+    // the tensor-core batched apply (c64 storage only) is the default in MIXED
+    for (int v = 0; v < 3; ++v) {
+      const std::vector<int4> tci = tc_apply_items(d, kApplyBK[v]);
+      d->n_tc_items_v[v] = (int64_t)tci.size();
+      GCQ_CUDA(ctx, up((int4**)&d->d_tc_items_v[v], tci));
+    }
+    d->apply_kernel = 1;
+  }
+  GCQ_CUDA(ctx, dmalloc(&d->d_apply_err, sizeof(int), own));
+  GCQ_CUDA(ctx, cudaMemset(d->d_apply_err, 0, sizeof(int)));
   GCQ_CUDA(ctx, up(&d->d_dense_list, dense));
   GCQ_CUDA(ctx, up(&d->d_aca_list, aca));
   GCQ_CUDA(ctx, up(&d->d_zoff, zoff));
@@ -749,6 +760,20 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
   GCQ_CUDA(ctx, dmalloc(&d->d_xacc, sizeof(double2) * 3 * (size_t)d->K * d->n_cols, own));
   // algorithmic bytes of one batched apply: stored operator + X + Y
   d->apply_bytes = (int64_t)d->stored_bytes + (int64_t)d->K * (d->n_rows + d->n_cols) * 3 * (int64_t)es;
+  // tensor work of one tensor-core batched apply: per face and frequency,
+  // the complex product of its 3m rows with 3n columns (rank columns for a
+  // low-rank face), 8 real flops per complex multiply-add, three TF32
+  // products per real product
+  double tf = 0.0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const BlkDev& B = d->h_blk[b];
+    if (B.status != ST_DONE) continue;
+    for (int p = 0; p < B.rank; ++p) {
+      const int fr = d->h_frank[(size_t)p * nb + b];
+      tf += 24.0 * 3.0 * (double)B.m * (fr < 0 ? 3.0 * (double)B.n : (double)fr) * d->K;
+    }
+  }
+  d->apply_tensor_flops = tf;
   return BEM_OK;
 }
 
@@ -765,6 +790,13 @@ static bem_status apply_faces_bk(bem_ctx* ctx, OpData* d, int v, cudaStream_t st
         d->d_toff, (cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_xp, d->K);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
+  }
+  if constexpr (std::is_same<S, float2>::value) {
+    if (d->apply_kernel == 1) {   // tensor cores (MIXED)
+      if (d->n_tc_items_v[v] > 0)
+        GCQ_CUDA(ctx, apply_faces_tc(d, BK, (const int4*)d->d_tc_items_v[v], d->n_tc_items_v[v], d->d_apply_err, st));
+      return BEM_OK;
+    }
   }
   if (d->n_apply_items_v[v] > 0) {
     cudaFuncSetAttribute(k_apply_faces<S, A, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -945,6 +977,16 @@ bem_status autotune(bem_op* op, cudaStream_t st, int32_t* bk) {
   return BEM_OK;
 }
 
+bem_status set_apply_kernel(bem_op* op, int32_t kind) {
+  if (kind != 0 && kind != 1)
+    return set_err(op->tree->mesh->ctx, BEM_ERR_ARG, "bem_op_set_apply_kernel: kind must be 0 (SIMT) or 1 (tensor cores)");
+  if (kind == 1 && op->d->prec == BEM_FP64)
+    return set_err(op->tree->mesh->ctx, BEM_ERR_ARG,
+                   "bem_op_set_apply_kernel: the tensor-core apply serves MIXED operators (c64 storage)");
+  op->d->apply_kernel = kind;
+  return BEM_OK;
+}
+
 bem_status set_apply_tile(bem_op* op, int32_t bk) {
   if (bk != 16 && bk != 32 && bk != 64)
     return set_err(op->tree->mesh->ctx, BEM_ERR_ARG, "bem_op_set_apply_tile: the tile must be 16, 32 or 64");
@@ -1068,6 +1110,12 @@ bem_status op_stats(const bem_op* op, bem_op_stats* s) {
   s->t_face_aca_ms = d->t_face_aca_ms;
   s->apply_bk = d->apply_bk;
   for (int v = 0; v < 3; ++v) s->apply_tune_ms[v] = d->apply_tune_ms[v];
+  s->apply_kernel = d->apply_kernel;
+  s->apply_tensor_flops = d->apply_tensor_flops;
+  int herr = 0;
+  if (d->d_apply_err && cudaMemcpy(&herr, d->d_apply_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_err(op->tree->mesh->ctx, cudaGetLastError(), "bem_op_stats_get: apply error word");
+  s->apply_errors = herr;
   return BEM_OK;
 }
 

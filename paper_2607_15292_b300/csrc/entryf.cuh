@@ -256,6 +256,17 @@ __device__ __forceinline__ void ref_point(const RefF& R, const float4& a0, const
   dr = num / (r + R.r0);
 }
 
+// exp(-w (r0 + dr)) from the reference exponential E0 = exp(-w r0).  When
+// E0 underflowed to zero (Re(w) r0 beyond the FP32 range, elements far
+// larger than the decay length exp(-Re(w) r)), the factor exp(-w dr) of a
+// point nearer than r0 can overflow and the product would be 0 x inf: the
+// value is then evaluated directly at r (where it is at most a few orders
+// above the underflow threshold, and its phase error immaterial).
+__device__ __forceinline__ cx<float> exp_from_ref(cx<float> E0, cx<float> w, float r, float dr) {
+  if (E0.x == 0.f && E0.y == 0.f) return cexp_neg(cx<float>{w.x * r, w.y * r});
+  return E0 * cexp_neg(cx<float>{w.x * dr, w.y * dr});
+}
+
 // kernel coefficients at a regular point: series for |s| r / c2 < 2, else the
 // closed form with exp(-s r / c_a) = E0_a exp(-s dr / c_a) when the reference
 // is in use (large |s| r0 / c2), or evaluated directly
@@ -271,8 +282,8 @@ __device__ __forceinline__ void coeffs_ref(const KC<float>& k, float r, float dr
   const cx<float> kr1 = {w[0].x * r, w[0].y * r}, kr2 = {w[1].x * r, w[1].y * r};
   cx<float> e1, e2;
   if (use) {
-    e1 = E0[0] * cexp_neg(cx<float>{w[0].x * dr, w[0].y * dr});
-    e2 = E0[1] * cexp_neg(cx<float>{w[1].x * dr, w[1].y * dr});
+    e1 = exp_from_ref(E0[0], w[0], r, dr);
+    e2 = exp_from_ref(E0[1], w[1], r, dr);
   } else {
     e1 = cexp_neg(kr1);
     e2 = cexp_neg(kr2);
@@ -287,7 +298,7 @@ __device__ __forceinline__ void dcoeffs_ref(const KC<float>& k, float r, float d
                                             const cx<float>* w, cx<float>& A, cx<float>& B) {
   const cx<float> wa = w[DC - 1];
   const cx<float> kr = {wa.x * r, wa.y * r};
-  const cx<float> e = use ? E0[DC - 1] * cexp_neg(cx<float>{wa.x * dr, wa.y * dr}) : cexp_neg(kr);
+  const cx<float> e = use ? exp_from_ref(E0[DC - 1], wa, r, dr) : cexp_neg(kr);
   dcoeffs_from<float, DC>(k, r, kr, e, A, B);
 }
 
@@ -423,7 +434,7 @@ __device__ void entry_dl_f(const EntryView& v, int i, int j, cx<float> s, cx<flo
         } else {
           const cx<float> wa = w[DC - 1];
           const cx<float> xr = {wa.x * r, wa.y * r};
-          const cx<float> ea = use ? E0[DC - 1] * cexp_neg(cx<float>{wa.x * dr, wa.y * dr}) : cexp_neg(xr);
+          const cx<float> ea = use ? exp_from_ref(E0[DC - 1], wa, r, dr) : cexp_neg(xr);
           cx<float> DA, DB, DAp, DBp, DS3;
           dcoeffs2_from<float, DC>(v.kf, r, xr, ea, ea, DA, DB, DAp, DBp, DS3);
           acc_dTT_from<float, DC>(v.kf, wq, r, hh, nf, Bc, dA, dB, S3, DB, DAp, DBp, DS3, A9);

@@ -948,6 +948,11 @@ bem_status bem_op_set_apply_tile(bem_op* op, int32_t bk) {
   return set_apply_tile(op, bk);
 }
 
+bem_status bem_op_set_apply_kernel(bem_op* op, int32_t kind) {
+  if (!op) return BEM_ERR_ARG;
+  return set_apply_kernel(op, kind);
+}
+
 bem_status bem_op_autotune(bem_op* op, void* stream, int32_t* bk) {
   if (!op) return BEM_ERR_ARG;
   GCQ_CUDA(op->tree->mesh->ctx, cudaSetDevice(op->tree->mesh->ctx->device));

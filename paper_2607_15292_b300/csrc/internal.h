@@ -185,6 +185,7 @@ bem_status autotune(bem_op* op, cudaStream_t st, int32_t* bk);
 bem_status op_save(const bem_op* op, const char* path);
 bem_status op_load(bem_tree* tree, const char* path, OpData** out);
 bem_status set_apply_tile(bem_op* op, int32_t bk);
+bem_status set_apply_kernel(bem_op* op, int32_t kind);
 bem_status face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, double eps, int32_t* rank, void* out,
                          cudaStream_t st);
 bem_status cq_transform(int N, int64_t nvec, const void* in, void* out, bool inverse, cudaStream_t st);
