@@ -388,6 +388,13 @@ bem_status bem_op_blocks(const bem_op* op, int64_t* info);
  * has no face in that slot. */
 bem_status bem_op_face_ranks(const bem_op* op, int32_t* ranks);
 
+/* Per-iteration record of the last compression (Algorithm 1's iterations
+ * d = 0, 1, ...): face_ms[d] the device time of iteration d's face kernel
+ * (CUDA events on the stream), entries[d] the entries (i, j) of the blocks
+ * still active in it.  *n receives the number of iterations; at most cap of
+ * them are written (host arrays).  0 iterations for a loaded operator. */
+bem_status bem_op_slot_stats(const bem_op* op, int32_t cap, double* face_ms, int64_t* entries, int32_t* n);
+
 /* The face compression of Sec. 3.1 (Eq. (3.12)) on one face, the step
  * bem_op_compress applies to the faces of far blocks: matrix-valued
  * partial-pivot ACA of the 3m x 3n matrix H[(i,a),(j,b)] to tolerance

@@ -96,6 +96,7 @@ _SIGS = {
     "bem_op_set_apply_kernel": (_i32, [_vp, _i32]),
     "bem_tc_selftest": (_i32, [_i32, _P(ctypes.c_float), _P(ctypes.c_float), _P(ctypes.c_float)]),
     "bem_measure_peaks": (_i32, [_i32, _P(_dbl)]),
+    "bem_op_slot_stats": (_i32, [_vp, _i32, _P(_dbl), _P(_i64), _P(_i32)]),
     "bem_op_save": (_i32, [_vp, ctypes.c_char_p]),
     "bem_op_load": (_i32, [_vp, ctypes.c_char_p, _P(_vp)]),
     "bem_op_autotune": (_i32, [_vp, _vp, _P(_i32)]),
@@ -535,6 +536,16 @@ class Operator:
         out = np.zeros((self.tree.n_blocks, 4), dtype=np.int64)
         _check(_lib.bem_op_blocks(self._p, out.ctypes.data_as(_P(_i64))))
         return out
+
+    def slot_stats(self):
+        """Per 3D-ACA iteration: (face-kernel ms, active entries) arrays."""
+        n = _i32(0)
+        _check(_lib.bem_op_slot_stats(self._p, 0, None, None, ctypes.byref(n)))
+        ms = np.zeros(n.value, dtype=np.float64)
+        en = np.zeros(n.value, dtype=np.int64)
+        _check(_lib.bem_op_slot_stats(self._p, n.value, ms.ctypes.data_as(_P(_dbl)), en.ctypes.data_as(_P(_i64)),
+                                      ctypes.byref(n)))
+        return ms, en
 
     def face_ranks(self) -> np.ndarray:
         """(K, n_blocks) int32: rank of each low-rank face, -1 dense face, -2 no face."""

@@ -9,6 +9,7 @@
 #include <thread>
 
 #include "internal.h"
+#include "opdata.h"
 
 namespace gcq {
 
@@ -962,6 +963,17 @@ bem_status bem_op_autotune(bem_op* op, void* stream, int32_t* bk) {
 bem_status bem_op_face_ranks(const bem_op* op, int32_t* ranks) {
   if (!op || !ranks) return BEM_ERR_ARG;
   return op_face_ranks(op, ranks);
+}
+
+bem_status bem_op_slot_stats(const bem_op* op, int32_t cap, double* face_ms, int64_t* entries, int32_t* n) {
+  if (!op || !n || cap < 0 || (cap > 0 && (!face_ms || !entries))) return BEM_ERR_ARG;
+  const gcq::OpData* d = op->d;
+  *n = (int32_t)d->slot_face_ms.size();
+  for (int32_t s = 0; s < *n && s < cap; ++s) {
+    face_ms[s] = d->slot_face_ms[s];
+    entries[s] = d->slot_entries[s];
+  }
+  return BEM_OK;
 }
 
 bem_status bem_cq_forward(int32_t N, int64_t nvec, const void* in, void* out, void* stream) {

@@ -26,6 +26,8 @@ struct BlkDev {
   double s3max;
   double f2;
   int32_t t0, t1;       // tile range of the current iteration
+  double gscale;        // power of two ~ 1 / rms entry of the first face: the
+                        // FP32 Gram products are formed from scaled values
 };
 
 struct Tile {
@@ -48,12 +50,15 @@ struct OpData {
   std::vector<void*> allocs;   // device chunks owned by the operator
   int32_t* d_ks = nullptr;     // [n_blocks][K] pivot frequencies
   uint8_t* d_used = nullptr;   // [n_blocks][K]
-  double2* d_M = nullptr;      // [n_blocks][K][9] Gram of the current face
+  double2* d_M = nullptr;      // [n_blocks][K][9] Gram blocks M_{p,d-1} of the previous face
+  double2* d_N = nullptr;      // [n_blocks][K][9] fibre Gram blocks N_{d,p} of the latest fibre
   double* d_hn2 = nullptr;     // [n_blocks][K] ||H_p||_F^2 of every accepted face
   int64_t entries = 0;
   double t_entries_ms = 0, t_compress_ms = 0;
   int64_t apply_bytes = 0;
   double t_face_ms = 0;          // k_face device time (events on the stream)
+  std::vector<double> slot_face_ms;      // per 3D-ACA iteration: k_face device time
+  std::vector<int64_t> slot_entries;     // and the entries of its active blocks
   int64_t face_launches = 0;
   double face_alg_bytes = 0;     // algorithmic bytes of k_face: (slot + 1) faces per entry
   int64_t launches = 0;          // kernels launched by the compression
