@@ -34,10 +34,10 @@ WORKLOAD = dict(workload="sphere-5120-K64", mesh="icosphere level 4, radius 1 m,
                 rows="nodes (Neumann)", operators="V (SL) + C+K (DL)")
 METRIC = "3D-ACA tensor entries/s"
 # k_face DRAM traffic / algorithmic bytes, measured with ncu on the
-# icosphere-3 single layer (all 42 face launches of one compression): the
-# previous faces are read twice per launch (residual and Gram passes), the
-# second time partly from L2
-FACE_TRAFFIC_RATIO = 1.708
+# icosphere-3 single layer (all face launches of one compression); None
+# until the counters are taken on the current kernel (one pass over the
+# previous faces per iteration)
+FACE_TRAFFIC_RATIO = None
 UNIT = "block entries/s"
 
 
@@ -265,6 +265,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    # roofline denominators of this GPU's units (FP32, FP64, ex2, TF32 MMA)
+    unit_peaks = g.measure_peaks(local)
 
     xyz, tri = syn.icosphere(4)
     s = g.freqs_bdf2(WORKLOAD["N"], WORKLOAD["dt"], WORKLOAD["K"])
@@ -329,23 +331,39 @@ def main():
         entries = int(e.item())
     value = entries / (ms / 1e3)
 
-    # apply throughput (algorithmic bytes / time) on the compressed operators
+    # apply throughput (algorithmic bytes / time) on the compressed operators:
+    # the tensor-core kernel (the MIXED default) and, for comparison, the
+    # SIMT kernel on the same operators
     oV, oK = step()
     torch.cuda.synchronize()
     reps = 20
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    for _ in range(reps):
-        oV.apply(XV, YV, g.BEM_APPLY_BATCHED, stream)
-        oK.apply(XK, YK, g.BEM_APPLY_BATCHED, stream)
-    a1.record(stream)
-    torch.cuda.synchronize()
-    apply_ms = a0.elapsed_time(a1) / reps
+
+    def time_apply():
+        for _ in range(2):
+            oV.apply(XV, YV, g.BEM_APPLY_BATCHED, stream)
+            oK.apply(XK, YK, g.BEM_APPLY_BATCHED, stream)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            oV.apply(XV, YV, g.BEM_APPLY_BATCHED, stream)
+            oK.apply(XK, YK, g.BEM_APPLY_BATCHED, stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / reps
+    for o in (oV, oK):
+        o.set_apply_kernel(0)
+    apply_ms_simt = time_apply()
+    for o in (oV, oK):
+        o.set_apply_kernel(1)
+    apply_ms = time_apply()
     sv, sk = oV.stats(), oK.stats()
     apply_bytes = sv.apply_bytes + sk.apply_bytes
     apply_gbs = apply_bytes / (apply_ms / 1e3) / 1e9
+    apply_tflops = (sv.apply_tensor_flops + sk.apply_tensor_flops) / (apply_ms / 1e3) / 1e12
 
-    extra = {"apply_gbs": apply_gbs, "apply_ms": apply_ms, "compression_rate_V": sv.compression_rate,
+    extra = {"apply_gbs": apply_gbs, "apply_ms": apply_ms, "apply_kernel": "tcgen05 kind::tf32 (split operands)",
+             "apply_ms_simt": apply_ms_simt, "apply_gbs_simt": apply_bytes / (apply_ms_simt / 1e3) / 1e9,
+             "apply_tensor_tflops": apply_tflops, "compression_rate_V": sv.compression_rate,
              "compression_rate_K": sk.compression_rate, "rank_mean_V": sv.rank_mean, "rank_mean_K": sk.rank_mean,
              "blocks_V": [sv.n_aca, sv.n_dense, sv.n_rank0], "blocks_K": [sk.n_aca, sk.n_dense, sk.n_rank0],
              "faces_lowrank_V": [sv.n_faces_lowrank, sv.n_faces], "faces_lowrank_K": [sk.n_faces_lowrank, sk.n_faces],
@@ -479,19 +497,30 @@ def main():
     hbm = peaks.get("hbm_gbs") or 6400.0
     face_gbs = face["bytes"] / (face["ms"] / 1e3) / 1e9 if face["ms"] > 0 else None
     alg_per_launch = face["bytes"] / max(1, face["launches"])
-    roofline = {"kernel": "k_face (3D-ACA face: entries + residual + Gram), MIXED",
+    roofline = {"kernel": "k_face (3D-ACA face: entries + residual + Gram in one pass), MIXED",
                 "bound": "hbm", "achieved": face_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": (face_gbs / hbm) if face_gbs else None,
                 # DRAM read + write per launch: the ratio to the algorithmic bytes
-                # measured by ncu on all 47 face launches of the icosphere-3 case
+                # measured by ncu on all face launches of the icosphere-3 case
                 # (`python bench.py --small`), times this workload's bytes per launch
-                "traffic": FACE_TRAFFIC_RATIO * alg_per_launch,
-                "traffic_source": "ncu dram__bytes_read+write, icosphere-3 (bench.py --small), ratio "
-                                  f"{FACE_TRAFFIC_RATIO} to algorithmic bytes, scaled",
+                "traffic": FACE_TRAFFIC_RATIO * alg_per_launch if FACE_TRAFFIC_RATIO else None,
+                "traffic_source": ("ncu dram__bytes_read+write, icosphere-3 (bench.py --small), ratio "
+                                   f"{FACE_TRAFFIC_RATIO} to algorithmic bytes, scaled") if FACE_TRAFFIC_RATIO
+                else "not yet captured for this kernel version",
                 "launches": face["launches"],
                 "avg_launch_ms": face["ms"] / max(1, face["launches"]),
                 "algorithmic_bytes_per_launch": face["bytes"] / max(1, face["launches"]),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.4 TB/s"}
+    # the batched apply on the tensor cores: TF32 work against the measured
+    # kind::tf32 rate (bem_measure_peaks on this GPU), bytes against HBM
+    tf32_peak = unit_peaks.get("tf32_tflops_n128")
+    apply_roof = {"kernel": "k_apply_faces_tc (batched apply, tcgen05 kind::tf32, split operands), MIXED",
+                  "bound": "tensor", "achieved": extra["apply_tensor_tflops"], "peak": tf32_peak, "unit": "TFLOP/s",
+                  "frac": extra["apply_tensor_tflops"] / tf32_peak if tf32_peak else None,
+                  "peak_source": "bem_measure_peaks tcgen05 kind::tf32 M=128 N=128 (of measured)",
+                  "hbm_achieved_gbs": apply_gbs, "hbm_frac": apply_gbs / hbm,
+                  "work": "24 x rows x columns x K TF32 flops per face (8 per complex multiply-add, 3 split "
+                          "products), stored operator + X + Y bytes"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64",
@@ -502,7 +531,8 @@ def main():
             "clocks": clk.summary(),
             "e2e": {"value": e_entries / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": launches, "roofline": roofline, **extra}
+            "gpu_launches": launches, "roofline": roofline, "roofline_apply": apply_roof,
+            "unit_peaks": unit_peaks, **extra}
     line["entry_kernels_ms_per_step"] = entry_ms / args.steps
     line["peaks_source"] = "MEASURED_PEAKS.json" if peaks else "fallback"
     if rank == 0 and not args.no_cpu_baseline:

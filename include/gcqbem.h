@@ -337,14 +337,15 @@ bem_status bem_op_set_apply_tile(bem_op* op, int32_t bk);
  * BEM_ERR_ARG).  The contracted and adjoint applies are SIMT in both. */
 bem_status bem_op_set_apply_kernel(bem_op* op, int32_t kind);
 
-/* Self-test of the tensor-core operand layout: D = A B^T computed by one
- * CTA through the shared-memory layout, descriptors, MMA issue and
- * tensor-memory read-out of the tensor-core apply (the paper has no
- * counterpart).  A: host 128 x 32 floats, B: host 64 x 32 floats (row-major,
- * values meant to be exact in TF32), D: host 128 x 64 floats.  Allocates
- * and synchronises; BEM_ERR_CUDA if the device work failed or a bounded
- * wait gave up. */
-bem_status bem_tc_selftest(int32_t device, const float* A, const float* B, float* D);
+/* Self-test of the tensor-core operand layout: D = A B^T (negate = 0) or
+ * D = -A B^T (negate = 1, the instruction descriptor's negate-A bit that the
+ * apply uses for Hi Zi) computed by one CTA through the shared-memory
+ * layout, descriptors, MMA issue and tensor-memory read-out of the
+ * tensor-core apply (the paper has no counterpart).  A: host 128 x 32
+ * floats, B: host 64 x 32 floats (row-major, values meant to be exact in
+ * TF32), D: host 128 x 64 floats.  Allocates and synchronises; BEM_ERR_CUDA
+ * if the device work failed or a bounded wait gave up. */
+bem_status bem_tc_selftest(int32_t device, int32_t negate, const float* A, const float* B, float* D);
 
 /* Measured throughput of the execution units that bound this library's
  * kernels, the roofline denominators of their measurements (the paper has
@@ -409,8 +410,8 @@ bem_status bem_op_slot_stats(const bem_op* op, int32_t cap, double* face_ms, int
 bem_status bem_face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, double eps_face,
                              int32_t* rank, void* out, void* stream);
 
-/* Fault injection for tests (the paper has no counterpart), process-wide,
- * off by default:
+/* Fault injection and measurement switches for tests (the paper has no
+ * counterpart), process-wide, off by default:
  *  BEM_DEBUG_FACE_WAIT_FAIL (value != 0): the 3D-ACA face kernel treats every
  *    staged copy of a previous face as not landed once it has landed, so the
  *    compression takes its timeout path (no further copy issued, the copies
@@ -420,8 +421,12 @@ bem_status bem_face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, 
  *    of the compression larger than value fails as if the device were out of
  *    memory, so bem_op_compress returns BEM_ERR_OOM after releasing what it
  *    holds.
+ *  BEM_DEBUG_FACE_ACA_FULL (value != 0): the face compression of Sec. 3.1
+ *    attempts every face of every far block (no slot-order pruning) and runs
+ *    each face ACA to its step cap (no early exit on a predicted slow
+ *    decay): the measurement of what those two shortcuts leave dense.
  * BEM_ERR_ARG for another `what` or a negative cap. */
-typedef enum { BEM_DEBUG_FACE_WAIT_FAIL = 1, BEM_DEBUG_ALLOC_CAP = 2 } bem_debug;
+typedef enum { BEM_DEBUG_FACE_WAIT_FAIL = 1, BEM_DEBUG_ALLOC_CAP = 2, BEM_DEBUG_FACE_ACA_FULL = 3 } bem_debug;
 bem_status bem_debug_set(int32_t what, int64_t value);
 
 /* Number of CUDA kernels this library has launched in the process so far

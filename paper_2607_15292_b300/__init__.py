@@ -35,7 +35,7 @@ BEM_SL_DCP, BEM_SL_DCS = 2, 3
 BEM_DL_DCP, BEM_DL_DCS = 4, 5
 BEM_APPLY_BATCHED, BEM_APPLY_CONTRACTED = 0, 1
 # fault injection for tests (bem_debug_set)
-BEM_DEBUG_FACE_WAIT_FAIL, BEM_DEBUG_ALLOC_CAP = 1, 2
+BEM_DEBUG_FACE_WAIT_FAIL, BEM_DEBUG_ALLOC_CAP, BEM_DEBUG_FACE_ACA_FULL = 1, 2, 3
 
 _STATUS = {0: "BEM_OK", 1: "BEM_ERR_ARG", 2: "BEM_ERR_CUDA", 3: "BEM_ERR_OOM", 4: "BEM_ERR_MESH",
            5: "BEM_ERR_NOT_CONVERGED", 6: "BEM_ERR_STATE"}
@@ -94,7 +94,7 @@ _SIGS = {
     "bem_op_compress_batch": (_i32, [_P(_vp), _i32, _i32, _P(_vp)]),
     "bem_op_set_apply_tile": (_i32, [_vp, _i32]),
     "bem_op_set_apply_kernel": (_i32, [_vp, _i32]),
-    "bem_tc_selftest": (_i32, [_i32, _P(ctypes.c_float), _P(ctypes.c_float), _P(ctypes.c_float)]),
+    "bem_tc_selftest": (_i32, [_i32, _i32, _P(ctypes.c_float), _P(ctypes.c_float), _P(ctypes.c_float)]),
     "bem_measure_peaks": (_i32, [_i32, _P(_dbl)]),
     "bem_op_slot_stats": (_i32, [_vp, _i32, _P(_dbl), _P(_i64), _P(_i32)]),
     "bem_op_save": (_i32, [_vp, ctypes.c_char_p]),
@@ -206,16 +206,18 @@ def measure_peaks(device: int = 0) -> dict:
     return dict(zip(keys, out.tolist()))
 
 
-def tc_selftest(A, B, device: int = 0):
-    """D = A B^T (A 128 x 32, B 64 x 32 float32) through the tensor-core
-    operand layout of the apply (bem_tc_selftest); returns D (128 x 64)."""
+def tc_selftest(A, B, device: int = 0, negate: bool = False):
+    """D = A B^T, or -A B^T with negate (A 128 x 32, B 64 x 32 float32)
+    through the tensor-core operand layout of the apply (bem_tc_selftest);
+    returns D (128 x 64)."""
     A = np.ascontiguousarray(A, dtype=np.float32)
     B = np.ascontiguousarray(B, dtype=np.float32)
     if A.shape != (128, 32) or B.shape != (64, 32):
         raise ValueError("tc_selftest: A must be 128 x 32 and B 64 x 32")
     D = np.zeros((128, 64), dtype=np.float32)
     fp = _P(ctypes.c_float)
-    _check(_lib.bem_tc_selftest(int(device), A.ctypes.data_as(fp), B.ctypes.data_as(fp), D.ctypes.data_as(fp)))
+    _check(_lib.bem_tc_selftest(int(device), int(bool(negate)), A.ctypes.data_as(fp), B.ctypes.data_as(fp),
+                                D.ctypes.data_as(fp)))
     return D
 
 

@@ -3,24 +3,16 @@
 // One iteration d advances all active blocks by one face-fibre pair:
 //   k_face        H_d[i,j] = ENTRY(i,j,k_d) - sum_{p<d} H_p[i,j] f_p[k_d]
 //                 (all entries of all active blocks, one thread per entry),
-//                 per-tile partials of max sigma_3, ||H_d||^2 and, from the
-//                 same single pass over the previous faces, the Gram blocks
-//                 of the previous face M_{p,d-1} = sum_ij H_p[i,j]^H H_{d-1}[i,j]
-//                 (p <= d - 1);
+//                 per-tile partials of max sigma_3, ||H_d||^2 and the Gram
+//                 blocks M_pd = sum_ij H_p[i,j]^H H_d[i,j] (p <= d);
 //   k_block_red   per block: pivot (i_d, j_d) = argmax sigma_3 (smallest
-//                 flat index on ties), ||H_d||_F, M_{p,d-1};
-//   k_fibre_step  per block, one thread per frequency: first the stop test
-//                 of iteration d - 1, ||H_{d-1}|| ||f_{d-1}|| <= eps ||C^(d-1)||
-//                 with ||C^(d-1)||_F^2 by the recursion of Eq. (3.3) (matrix
-//                 form; the pair d - 1 and the face d are discarded on
-//                 stopping), then for a block that goes on
+//                 flat index on ties), ||H_d||_F, M_pd;
+//   k_fibre_step  per block, one thread per frequency:
 //                 f_d[k] = H_d[i_d,j_d]^{-1} (ENTRY(i_d,j_d,k) - sum_p H_p[i_d,j_d] f_p[k]),
-//                 the fibre Gram blocks N_{d,p} for the next stop test,
+//                 ||C^(d)||_F^2 by the recursion of Eq. (3.3) (matrix form),
+//                 the stop test ||H_d|| ||f_d|| <= eps ||C^(d)|| (pair discarded),
 //                 k_{d+1} = argmax over unused k of sigma_3(f_d[k]) (Eq. (3.8)),
 //                 dense fallback when no regular pivot exists.
-// The stop test runs one iteration late so that the Gram blocks of face d - 1
-// come from the residual pass of iteration d: the previous faces are read
-// once per iteration instead of twice.
 // Faces are stored densely per block ([i][j][3][3], cluster order), fibres
 // [k][3][3]; slot tables are [slot][block].
 #pragma once
@@ -228,9 +220,9 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   using W = typename WorkOf<S>::W;
   // Previous faces stream through shared memory: the tile's 256 entries of a
   // face are one contiguous range (256 x 9 x 16 B = 36 KB), copied by one
-  // bulk TMA copy into one of two buffers.  Copy n (n = 0 .. slot - 1)
-  // brings face slot - 1 (n = 0) or face n - 1 (n >= 1) for the one pass of
-  // residual and Gram; it lands in buffer n & 1, completes phase
+  // bulk TMA copy into one of two buffers.  Copy n (n = 0 .. 2 slot - 1)
+  // brings face n for the residual pass (n < slot), then faces slot - 1 ..
+  // 0 for the Gram pass; it lands in buffer n & 1, completes phase
   // (n >> 1) & 1 of that buffer's barrier, and copy n + 2 is issued once
   // every thread is done with copy n.  The first two copies overlap the
   // entry evaluation.
@@ -249,7 +241,7 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   S* const fbuf0 = reinterpret_cast<S*>(kf_dyn);
   const int64_t nval = min((int64_t)kTile, B.m * B.n - t.start);
   const uint32_t tile_bytes = (uint32_t)(nval * 9 * (int64_t)sizeof(S));
-  const int nload = slot;
+  const int nload = 2 * slot;
   // A wait that gives up (or, with dbg_fail, a wait that completed: fault
   // injection for tests) sets kf_fail; from the next CTA barrier on, no thread
   // waits and thread 0 issues no further copy, so that at most the last two
@@ -257,7 +249,7 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   __shared__ volatile int kf_fail;
   int n_issued = 0;   // thread 0: copies issued
   auto issue = [&](int n) {   // thread 0 only
-    const int pf = n == 0 ? slot - 1 : n - 1;
+    const int pf = n < slot ? n : 2 * slot - 1 - n;
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&kf_bar[n & 1], tile_bytes);
     bulk_copy_g2s(fbuf0 + (n & 1) * (kTile * 9), face_tab[(int64_t)pf * nb + t.blk] + t.start * 9, tile_bytes,
@@ -316,17 +308,10 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
     for (int c = 0; c < 9; ++c) Hd64[c] = {0, 0};
     if (ok) entry<R, KERN, ROWS>(v, i, j, kd, s, is2, Hd64);
   }
-  // residual: H = E - sum_p H_p[i,j] f_p[k_d] over the previous faces
-  // (MIXED: the terms whose ||H_p|| ||f_p[k_d]|| is below 2^-10 of the first
-  // term's take plain FMA, their FP32 rounding staying below 2^-34 of the
-  // face; the others error-free products in float-float), and in the same
-  // pass the Gram blocks of the previous face, M_{p,d-1} = sum_ij
-  // H_p[i,j]^H H_{d-1}[i,j] for p <= d - 1, which the stop test of iteration
-  // d - 1 needs (it runs one iteration late, after this kernel).  Copy 0
-  // brings face d - 1 (kept in registers for the Gram), copy n >= 1 face
-  // n - 1.  The Gram products are formed from the high parts scaled by the
-  // block's power of two gscale (products of small entries would underflow
-  // FP32) and unscaled exactly in double.
+  // residual: H = E - sum_p H_p[i,j] f_p[k_d].  MIXED: the terms whose
+  // ||H_p|| ||f_p[k_d]|| is below 2^-10 of the first term's take plain FMA
+  // (their FP32 rounding stays below 2^-34 of the face), the others
+  // error-free products in float-float
   float fs[18];                   // sum of the small terms (MIXED)
   for (int c = 0; c < 18; ++c) fs[c] = 0.f;
   __shared__ double sref;          // ||H_0|| ||f_0[k_d]|| squared (MIXED), read after the first barrier
@@ -341,24 +326,17 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
       sref = hn2[(int64_t)t.blk * K] * q;
     }
   }
-  __shared__ W gw[kTile / 32][16][18];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const W gsc = (W)B.gscale;
-  const double gsc2inv = 1.0 / (B.gscale * B.gscale);
-  cx<W> Hq[9];                    // face d - 1, scaled high parts
-  for (int c = 0; c < 9; ++c) Hq[c] = {W(0), W(0)};
-  double* pm = reinterpret_cast<double*>(p_M);
-  for (int n0 = 0; n0 < slot; n0 += 16) {
-    const int np = min(16, slot - n0);
+  for (int p0 = 0; p0 < slot; p0 += 64) {
+    const int np = min(64, slot - p0);
     __syncthreads();
     for (int c = threadIdx.x; c < np * 9; c += blockDim.x) {
-      const int n = n0 + c / 9, p = n == 0 ? slot - 1 : n - 1;
+      const int p = p0 + c / 9;
       sf[c] = fib_tab[(int64_t)p * nb + t.blk][(int64_t)kd * 9 + c % 9];
     }
     __syncthreads();
     if constexpr (FF) {
       if (threadIdx.x < np) {
-        const int n = n0 + threadIdx.x, p = n == 0 ? slot - 1 : n - 1;
+        const int p = p0 + threadIdx.x;
         double q = 0.0;
         for (int c = 0; c < 9; ++c) {
           const float4 y = reinterpret_cast<const float4*>(sf)[9 * threadIdx.x + c];
@@ -368,20 +346,18 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
       }
       __syncthreads();
     }
-    for (int pp = 0; pp < np; ++pp) {
-      const int n = n0 + pp;
+    for (int p = 0; p < np; ++p) {
+      const int n = p0 + p;   // copy n holds face n
       if (!wait_copy(n)) waited_ok = 0;
-      W g[32];
-      for (int c = 0; c < 32; ++c) g[c] = W(0);
       if (ok && waited_ok) {
         S cur[9];
         {
           const S* Hp = fbuf0 + (n & 1) * (kTile * 9) + threadIdx.x * 9;
           for (int c = 0; c < 9; ++c) cur[c] = Hp[c];
         }
-        const S* f = sf + 9 * pp;
+        const S* f = sf + 9 * p;
         if constexpr (FF) {
-          if (ssmall[pp]) {
+          if (ssmall[p]) {
             for (int a = 0; a < 3; ++a)
               for (int c = 0; c < 3; ++c) {
                 const float4 x = reinterpret_cast<const float4*>(cur)[3 * a + c];
@@ -426,41 +402,13 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
               Hd64[3 * a + b] = acc;
             }
         }
-              // Gram block of face p with face d - 1
-        cx<W> hp[9];
-        for (int c = 0; c < 9; ++c) {
-          if constexpr (FF) {
-            const float4 x = reinterpret_cast<const float4*>(cur)[c];
-            hp[c] = {gsc * (W)x.x, gsc * (W)x.y};
-          } else {
-            const cx<double> x = St<S>::ld(cur + c);
-            hp[c] = {gsc * (W)x.x, gsc * (W)x.y};
-          }
-        }
-        if (n == 0)
-          for (int c = 0; c < 9; ++c) Hq[c] = hp[c];
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) {
-            cx<W> acc = {W(0), W(0)};
-            for (int c = 0; c < 3; ++c) acc = cfma(conj(hp[3 * c + a]), Hq[3 * c + b], acc);
-            g[2 * (3 * a + b)] = acc.x;
-            g[2 * (3 * a + b) + 1] = acc.y;
-          }
       }
-      const W tot = warp_transpose_sum<W>(g);
-      if (lane < 18) gw[wid][pp][lane] = tot;
       __syncthreads();   // every thread is done with copy n: its buffer takes copy n + 2
       if (threadIdx.x == 0 && n + 2 < nload && !kf_fail) issue(n + 2);
     }
-    for (int q = threadIdx.x; q < np * 18; q += blockDim.x) {
-      const int pp = q / 18, c = q % 18, n = n0 + pp, p = n == 0 ? slot - 1 : n - 1;
-      double sum = 0.0;
-      for (int w = 0; w < kTile / 32; ++w) sum += (double)gw[w][pp][c];
-      pm[((int64_t)blockIdx.x * K + p) * 18 + c] = sum * gsc2inv;
-    }
   }
   S* Hd = face_tab[(int64_t)slot * nb + t.blk];
-  cx<W> H[9];   // working copy for the pivot criterion
+  cx<W> H[9];   // working copy for the pivot criterion and the Gram
   if (ok) {
     for (int c = 0; c < 9; ++c) {
       if constexpr (FF) {
@@ -484,15 +432,81 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   double s3 = ok ? (double)sigma3<W>(H) : -1.0;
   int64_t idx = ok ? e : INT64_MAX;
   block_argmax(s3, idx, shv, shi);
-  // ||H_d||^2 in double (squares of small FP32 entries would underflow)
+  // ||H_d||^2 of the tile in double (squares of small FP32 entries, e.g. of
+  // the wave-speed derivative operators, would underflow), and a power of
+  // two ~ 1 / rms entry of the tile that scales the FP32 Gram products below
   double h2[1] = {0.0};
   if (ok)
     for (int c = 0; c < 9; ++c) h2[0] += (double)H[c].x * H[c].x + (double)H[c].y * H[c].y;
   block_sum<1>(h2, shv);
+  __shared__ double s_gsc;
   if (threadIdx.x == 0) {
     p_s3[blockIdx.x] = s3;
     p_idx[blockIdx.x] = idx;
     p_h2[blockIdx.x] = h2[0];
+    const double rms = sqrt(h2[0] / (9.0 * (double)nval));
+    s_gsc = rms > 0.0 ? exp2(-rint(log2(rms))) : 1.0;
+  }
+  __syncthreads();
+  const W gsc = (W)s_gsc;
+  const double gsc2inv = 1.0 / (s_gsc * s_gsc);
+  for (int c = 0; c < 9; ++c) H[c] = {gsc * H[c].x, gsc * H[c].y};
+  // Gram blocks M_pd = sum_ij H_p[i,j]^H H_d[i,j], p = slot..0, from the
+  // scaled high parts (the products of small entries would underflow FP32;
+  // the scale is undone exactly in double): per-warp transpose sums into
+  // shared memory, then a fixed-order sum over the warps.
+  // p = slot is the face in registers; p < slot arrive as copies
+  // n = 2 slot - 1 - p (the reverse of the residual pass's order).
+  __shared__ W gw[kTile / 32][16][18];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int p0 = 0; p0 <= slot; p0 += 16) {
+    const int np = min(16, slot + 1 - p0);
+    for (int pp = 0; pp < np; ++pp) {
+      const int q = p0 + pp;          // p = slot - q
+      const int n = slot + q - 1;     // copy holding face p (q > 0)
+      if (q > 0 && !wait_copy(n)) waited_ok = 0;
+      W g[32];
+      for (int c = 0; c < 32; ++c) g[c] = W(0);
+      if (ok && waited_ok) {
+        cx<W> hp[9];
+        if (q == 0) {
+          for (int c = 0; c < 9; ++c) hp[c] = H[c];
+        } else {
+          const S* Hp = fbuf0 + (n & 1) * (kTile * 9) + threadIdx.x * 9;
+          for (int c = 0; c < 9; ++c) {
+            if constexpr (FF) {
+              const float4 x = reinterpret_cast<const float4*>(Hp)[c];
+              hp[c] = {gsc * (W)x.x, gsc * (W)x.y};
+            } else {
+              const cx<double> x = St<S>::ld(Hp + c);
+              hp[c] = {gsc * (W)x.x, gsc * (W)x.y};
+            }
+          }
+        }
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            cx<W> acc = {W(0), W(0)};
+            for (int c = 0; c < 3; ++c) acc = cfma(conj(hp[3 * c + a]), H[3 * c + b], acc);
+            g[2 * (3 * a + b)] = acc.x;
+            g[2 * (3 * a + b) + 1] = acc.y;
+          }
+      }
+      const W tot = warp_transpose_sum<W>(g);
+      if (lane < 18) gw[wid][pp][lane] = tot;
+      if (q > 0) {
+        __syncthreads();   // every thread is done with copy n
+        if (threadIdx.x == 0 && n + 2 < nload && !kf_fail) issue(n + 2);
+      }
+    }
+    __syncthreads();
+    double* pm = reinterpret_cast<double*>(p_M);
+    for (int q = threadIdx.x; q < np * 18; q += blockDim.x) {
+      const int pp = q / 18, c = q % 18;
+      double sum = 0.0;
+      for (int w = 0; w < kTile / 32; ++w) sum += (double)gw[w][pp][c];
+      pm[((int64_t)blockIdx.x * K + slot - (p0 + pp)) * 18 + c] = sum * gsc2inv;
+    }
+    __syncthreads();
   }
   // a copy that did not land in time: flag it for the host (which abandons
   // the compression) and give the last two issued copies, the only ones that
@@ -538,8 +552,7 @@ __global__ void k_block_red(BlkDev* __restrict__ blk, const int32_t* __restrict_
   // Gram blocks: thread per (face p, real component), fixed tile order
   const double* pm = reinterpret_cast<const double*>(p_M);
   double* mo = reinterpret_cast<double*>(M);
-  // (of face slot - 1 with the faces p <= slot - 1)
-  for (int q = threadIdx.x; q < slot * 18; q += blockDim.x) {
+  for (int q = threadIdx.x; q < (slot + 1) * 18; q += blockDim.x) {
     const int p = q / 18, c = q % 18;
     double sum = 0.0;
     for (int t = B.t0; t < B.t1; ++t) sum += pm[((int64_t)t * K + p) * 18 + c];
@@ -547,15 +560,14 @@ __global__ void k_block_red(BlkDev* __restrict__ blk, const int32_t* __restrict_
   }
 }
 
-// ---- stop test + fibre + next frequency (one CTA per block) --------------------
+// ---- fibre + norm + stop test + next frequency (one CTA per block) -----------
 template <typename R, typename S, int KERN, int ROWS>
 __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
                              const int32_t* __restrict__ active, S* const* __restrict__ face_tab,
                              S* const* __restrict__ fib_tab, int64_t nb, int slot,
                              const int32_t* __restrict__ row_perm, const int32_t* __restrict__ col_perm,
-                             const double2* __restrict__ M, double2* __restrict__ Nf,
-                             const double* __restrict__ hn2, int32_t* __restrict__ ks,
-                             uint8_t* __restrict__ used, int K, double eps) {
+                             const double2* __restrict__ M, int32_t* __restrict__ ks, uint8_t* __restrict__ used,
+                             int K, double eps) {
   __shared__ double shv[32 * 18];
   __shared__ int64_t shi[32];
   __shared__ int decision;
@@ -567,37 +579,6 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
   constexpr bool FF = std::is_same<S, float4>::value;
   const int b = active[blockIdx.x];
   BlkDev& B = blk[b];
-  // the stop test of iteration slot - 1 (Eq. (3.3)), one iteration late:
-  // ||C^(slot-1)||^2 = ||C^(slot-2)||^2 + 2 sum_{p < slot-1} Re tr(M_{p,slot-1} N_{slot-1,p})
-  //                    + Re tr(M_{slot-1,slot-1} N_{slot-1,slot-1});
-  // on stopping the pair slot - 1 is discarded (r = slot - 1) with the face
-  // slot just computed
-  if (slot > 0) {
-    double part[2] = {0.0, 0.0};   // cross, self
-    for (int q = threadIdx.x; q < slot * 9; q += blockDim.x) {
-      const int p = q / 9, a = (q % 9) / 3, c2 = q % 3;
-      const double2 nn = Nf[((int64_t)b * K + p) * 9 + 3 * a + c2];   // N_{slot-1,p}[a][c2]
-      const double2 m = M[((int64_t)b * K + p) * 9 + 3 * c2 + a];     // M_{p,slot-1}[c2][a]
-      part[p < slot - 1 ? 0 : 1] += m.x * nn.x - m.y * nn.y;
-    }
-    block_sum<2>(part, shv);
-    if (threadIdx.x == 0) {
-      const double norm2 = B.norm2 + 2.0 * part[0] + part[1];
-      const double hprev = sqrt(hn2[(int64_t)b * K + slot - 1]);
-      int dec = 0;
-      if (hprev * sqrt(B.f2) <= eps * sqrt(fmax(norm2, 0.0))) {
-        dec = ST_DONE;
-      } else {
-        B.norm2 = norm2;
-        B.rank = slot;
-      }
-      decision = dec;
-      if (dec) B.status = dec;
-    }
-    __syncthreads();
-    if (decision) return;
-  }
-  // face slot: all zero (rank 0), vanishing residual, no regular pivot
   if (threadIdx.x == 0) {
     const double hn = sqrt(B.h2);
     int dec = 0;
@@ -609,12 +590,6 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
       dec = ST_DENSE;
     decision = dec;
     if (dec) B.status = dec;
-    if (slot == 0 && !dec) {
-      // power of two ~ 1 / rms entry of the first face: scale of the FP32
-      // Gram products of the later iterations
-      const double rms = sqrt(B.h2 / (9.0 * (double)(B.m * B.n)));
-      B.gscale = rms > 0.0 ? exp2(-rint(log2(rms))) : 1.0;
-    }
   }
   __syncthreads();
   if (decision) return;
@@ -710,9 +685,9 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
     for (int c = 0; c < 9; ++c) St<S>::st(fd + (int64_t)k * 9 + c, f[c]);
     for (int c = 0; c < 9; ++c) f[c] = St<S>::ld(fd + (int64_t)k * 9 + c);
   }
-  // ||f_d||^2 and the fibre Gram blocks N_{d,p} = sum_k f_d[k] f_p[k]^H
-  // (p <= d) for the stop test of this pair, one iteration later: one
-  // thread per (face p, entry (a, c2)) reading f_d from shared memory
+  // ||f_d||^2 and the norm recursion: N_dp = sum_k f_d[k] f_p[k]^H with one
+  // thread per (face p, entry (a, c2)) reading f_d from shared memory, then
+  // tr(M_pd N_dp) accumulated per thread; one block reduction at the end
   extern __shared__ double2 sfd[];   // K x 9 (f_d), from the launch
   float2* sff = reinterpret_cast<float2*>(sfd);   // MIXED: f_d rounded to FP32 once, for the FP32 Gram
   if (ok)
@@ -723,7 +698,7 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
         sfd[(int64_t)k * 9 + c] = make_double2(f[c].x, f[c].y);
     }
   __syncthreads();
-  double part[1] = {0.0};   // ||f_d||^2
+  double part[3] = {0.0, 0.0, 0.0};   // ||f_d||^2, cross, self
   if (ok)
     for (int c = 0; c < 9; ++c) part[0] += f[c].x * f[c].x + f[c].y * f[c].y;
   for (int q = threadIdx.x; q < (slot + 1) * 9; q += blockDim.x) {
@@ -746,20 +721,32 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
           acc = cfma(cx<double>{x.x, x.y}, conj(St<S>::ld(fp + (int64_t)kk * 9 + 3 * c2 + c)), acc);
         }
     }
-    Nf[((int64_t)b * K + p) * 9 + 3 * a + c2] = make_double2(acc.x, acc.y);
+    // contribution of N_dp[a][c2] to tr(M_pd N_dp) = sum M_pd[c2][a] N_dp[a][c2]
+    const double2 m = M[((int64_t)b * K + p) * 9 + 3 * c2 + a];
+    const double tr = m.x * acc.x - m.y * acc.y;
+    if (p < slot)
+      part[1] += tr;
+    else
+      part[2] += tr;
   }
-  block_sum<1>(part, shv);
+  block_sum<3>(part, shv);
   double f2[1] = {part[0]};
+  const double cross = part[1], self = part[2];
   __shared__ int stop;
   if (threadIdx.x == 0) {
+    double norm2 = B.norm2 + 2.0 * cross + self;
     B.f2 = f2[0];
     int st = ST_ACTIVE;
     if (!inv_ok) {
       st = ST_DENSE;
+    } else if (sqrt(B.h2) * sqrt(f2[0]) <= eps * sqrt(fmax(norm2, 0.0))) {
+      st = ST_DONE;  // r = d - 1: the pair just computed is discarded
     } else {
-      // k_slot is taken (the pair is accepted or discarded by the next test)
+      B.norm2 = norm2;
       ks[(int64_t)b * K + slot] = B.k_cur;
       used[(int64_t)b * K + B.k_cur] = 1;
+      B.rank = slot + 1;
+      if (B.rank == K) st = ST_DENSE;
     }
     B.status = st;
     stop = st != ST_ACTIVE;
@@ -937,11 +924,12 @@ static bem_status finalize_storage(bem_ctx* ctx, OpData* d, cudaStream_t st) {
       for (int64_t b = 0; b < nb; ++b) {
         const BlkDev& B = d->h_blk[b];
         if (B.status != ST_DONE || !B.far || slot >= B.rank) continue;
-        if (slot > 0 && d->h_frank[(size_t)(slot - 1) * nb + b] < 0) continue;
+        if (slot > 0 && d->h_frank[(size_t)(slot - 1) * nb + b] < 0 && !debug_face_full()) continue;
         FaceJob j{};
         j.m = (int32_t)B.m;
         j.n = (int32_t)B.n;
         j.tcap = face_tcap(B.m, B.n, face_tcap_max<W>());
+        j.pad = debug_face_full() ? 1 : 0;
         j.H = d->h_face[(size_t)slot * nb + b];
         jobs.push_back(j);
         jidx.push_back((int64_t)slot * nb + b);
@@ -1120,7 +1108,6 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
     B.far = bd.far;
     B.status = ST_ACTIVE;
     B.k_cur = 0;  // k_1 = 0
-    B.gscale = 1.0;
     n_tiles_all += (bd.m * bd.n + kTile - 1) / kTile;
   }
   std::vector<void*>* own = &d->allocs;
@@ -1133,7 +1120,6 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   GCQ_CUDA(ctx, dmalloc(&d->d_ks, sizeof(int32_t) * nb * K, own));
   GCQ_CUDA(ctx, dmalloc(&d->d_used, nb * K, own));
   GCQ_CUDA(ctx, dmalloc(&d->d_M, sizeof(double2) * nb * K * 9, own));
-  GCQ_CUDA(ctx, dmalloc(&d->d_N, sizeof(double2) * nb * K * 9, own));
   GCQ_CUDA(ctx, dmalloc(&d->d_hn2, sizeof(double) * nb * K, own));
   GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_blk, d->h_blk.data(), sizeof(BlkDev) * nb, cudaMemcpyHostToDevice, st));
   GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_row_perm, tree->row_perm.data(), sizeof(int32_t) * tree->n_rows,
@@ -1246,7 +1232,7 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
                                        (int)fsm_max),
                   k_fibre_step<R, S, KK, RR><<<(unsigned)active.size(), tb, fsm, st>>>(
                      v, d->d_blk, d_active, (S* const*)d->d_face, (S* const*)d->d_fib, nb, slot, d->d_row_perm,
-                     d->d_col_perm, d->d_M, d->d_N, d->d_hn2, d->d_ks, d->d_used, K, ctx->opt.eps)));
+                     d->d_col_perm, d->d_M, d->d_ks, d->d_used, K, ctx->opt.eps)));
     GCQ_CUDA(ctx, cudaGetLastError());
     cudaEventRecord(ev1, st);
     GCQ_CUDA(ctx, cudaMemcpyAsync(d->h_blk.data(), d->d_blk, sizeof(BlkDev) * nb, cudaMemcpyDeviceToHost, st));
@@ -1273,9 +1259,7 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
     tiles.clear();
     for (int64_t b = 0; b < nb; ++b) {
       BlkDev& B = d->h_blk[b];
-      // a block still active here took every frequency (its last pair untested):
-      // no form smaller than the dense block remains
-      if (B.status == ST_ACTIVE) B.status = ST_DENSE;
+      if (B.status == ST_ACTIVE) B.status = ST_DENSE;   // cannot happen (rank == K -> dense)
       if (B.status != ST_DENSE) continue;
       B.rank = 0;
       void* p = nullptr;

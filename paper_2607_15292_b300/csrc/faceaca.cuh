@@ -529,7 +529,8 @@ __device__ int face_one(const FaceJob& jb, FaceSm<W>& sm, W eps_face) {
         bool hopeless = !(rn < ro);
         if (!hopeless && rn > W(0))
           hopeless = (W)(t + 1) + (W)w * FaceSt<W>::lg(eps_face / rn) / FaceSt<W>::lg(rn / ro) > W(1.5) * (W)tlim;
-        if (rn > W(16) * eps_face && hopeless) s_state = 2;
+        // (jb.pad = 1: no early exit, to measure what it drops)
+        if (rn > W(16) * eps_face && hopeless && jb.pad == 0) s_state = 2;
       }
     }
     __syncthreads();

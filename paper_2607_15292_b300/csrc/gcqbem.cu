@@ -26,8 +26,10 @@ void count_launches(int64_t n) { g_launches += n; }
 
 static std::atomic<int> g_dbg_face_wait_fail{0};
 static std::atomic<int64_t> g_dbg_alloc_cap{0};
+static std::atomic<int> g_dbg_face_full{0};
 int debug_face_wait_fail() { return g_dbg_face_wait_fail.load(); }
 int64_t debug_alloc_cap() { return g_dbg_alloc_cap.load(); }
+int debug_face_full() { return g_dbg_face_full.load(); }
 
 // ---------------------------------------------------------------------------
 // quadrature tables (host-built, uploaded once per device)
@@ -409,6 +411,7 @@ extern "C" bem_status bem_debug_set(int32_t what, int64_t value) {
       if (value < 0) return BEM_ERR_ARG;
       gcq::g_dbg_alloc_cap = value;
       return BEM_OK;
+    case BEM_DEBUG_FACE_ACA_FULL: gcq::g_dbg_face_full = value != 0; return BEM_OK;
     default: return BEM_ERR_ARG;
   }
 }

@@ -152,6 +152,7 @@ void count_launches(int64_t n);
 // fault injection for tests (bem_debug_set), process-wide
 int debug_face_wait_fail();
 int64_t debug_alloc_cap();
+int debug_face_full();
 bem_status cuda_err(bem_ctx* ctx, cudaError_t e, const char* what);
 
 #define GCQ_CUDA(ctx, call)                                         \

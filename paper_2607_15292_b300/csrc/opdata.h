@@ -26,8 +26,6 @@ struct BlkDev {
   double s3max;
   double f2;
   int32_t t0, t1;       // tile range of the current iteration
-  double gscale;        // power of two ~ 1 / rms entry of the first face: the
-                        // FP32 Gram products are formed from scaled values
 };
 
 struct Tile {
@@ -50,8 +48,7 @@ struct OpData {
   std::vector<void*> allocs;   // device chunks owned by the operator
   int32_t* d_ks = nullptr;     // [n_blocks][K] pivot frequencies
   uint8_t* d_used = nullptr;   // [n_blocks][K]
-  double2* d_M = nullptr;      // [n_blocks][K][9] Gram blocks M_{p,d-1} of the previous face
-  double2* d_N = nullptr;      // [n_blocks][K][9] fibre Gram blocks N_{d,p} of the latest fibre
+  double2* d_M = nullptr;      // [n_blocks][K][9] Gram of the current face
   double* d_hn2 = nullptr;     // [n_blocks][K] ||H_p||_F^2 of every accepted face
   int64_t entries = 0;
   double t_entries_ms = 0, t_compress_ms = 0;

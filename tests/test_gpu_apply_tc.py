@@ -46,12 +46,13 @@ def _hw_read(plane_vals, R, KD, swapped):
     return out
 
 
-def test_tc_selftest_matches_fp64_product(record):
+@pytest.mark.parametrize("negate", [False, True])
+def test_tc_selftest_matches_fp64_product(negate, record):
     rng = np.random.default_rng(5)
     A = _tf32(rng.standard_normal((128, 32)))
     B = _tf32(rng.standard_normal((64, 32)))
-    D = g.tc_selftest(A, B)
-    want = A.astype(np.float64) @ B.astype(np.float64).T
+    D = g.tc_selftest(A, B, negate=negate)
+    want = (-1.0 if negate else 1.0) * (A.astype(np.float64) @ B.astype(np.float64).T)
     err = np.abs(D - want).max() / np.abs(want).max()
     record("tc_selftest_err", err)
     if not err < 1e-6:
