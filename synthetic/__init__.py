@@ -17,7 +17,7 @@ import numpy as np
 __all__ = [
     "STEEL", "PAPER_CUBE_MATERIAL", "lame_from_young",
     "cube_grid", "paper_cube", "refine", "icosphere", "ellipsoid", "cube_sphere", "slotted_cylinder",
-    "SLOTTED_CYLINDER", "batch_meshes",
+    "SLOTTED_CYLINDER", "batch_meshes", "box", "BOX_ADJOINT", "box_receivers", "box_traction",
     "splitmix64", "uniform01", "normal", "complex_normal",
 ]
 
@@ -301,6 +301,75 @@ def slotted_cylinder(n_half_land: int = 2, n_wall: int = 2, n_bottom: int = 3, n
     t2 = np.where(use13[:, None], q[:, [1, 2, 3]], q[:, [0, 2, 3]])
     tri = np.concatenate([t1, t2])
     return xyz, _orient_outward(xyz, tri).astype(np.int32)
+
+
+def box(lx: float, ly: float, lz: float, h: float) -> tuple[np.ndarray, np.ndarray]:
+    """Surface of the box [0, lx] x [0, ly] x [0, lz], each face a grid of
+    squares of side h (the extents must be multiples of h), each square cut
+    along one diagonal into two triangles, oriented outward.  With
+    nx, ny, nz = lx/h, ly/h, lz/h: 4 (nx ny + nx nz + ny nz) triangles and
+    half as many nodes plus two (closed genus-0 surface)."""
+    n = [int(round(e / h)) for e in (lx, ly, lz)]
+    if any(abs(k * h - e) > 1e-9 * max(1.0, e) or k < 1 for k, e in zip(n, (lx, ly, lz))):
+        raise ValueError("box: extents must be positive multiples of h")
+    ext = np.array([lx, ly, lz], dtype=np.float64)
+    nodes = _NodeTable(scale=1)
+    tris = []
+    # (fixed axis, value 0 or 1, u axis, v axis): two faces per axis
+    for ax in range(3):
+        u_ax, v_ax = [a for a in range(3) if a != ax]
+        for side in (0, 1):
+            for i in range(n[u_ax]):
+                for j in range(n[v_ax]):
+                    def key(di, dj):
+                        g = [0, 0, 0]
+                        g[ax] = side * n[ax]
+                        g[u_ax] = i + di
+                        g[v_ax] = j + dj
+                        return nodes.get(np.array(g, dtype=np.float64))
+                    a, b, c, d = key(0, 0), key(1, 0), key(1, 1), key(0, 1)
+                    tris.append((a, b, c))
+                    tris.append((a, c, d))
+    grid = np.array(nodes.xyz)
+    xyz = grid * (ext / np.array(n, dtype=np.float64))
+    return xyz, _orient_outward(xyz, np.array(tris, dtype=np.int32))
+
+
+#: the adjoint workload: 20 x 20 x 10 m box, 0.4 m grid (20,000 triangles,
+#: 10,002 nodes), Gaussian traction pulse on the top face, 64 receivers on
+#: the bottom face, N = 254 BDF2 steps of 4e-5 s (128 frequencies)
+BOX_ADJOINT = dict(lx=20.0, ly=20.0, lz=10.0, h=0.4, N=254, dt=4e-5, receivers=64, width=2.0, t0=2e-3, tw=5e-4)
+
+
+def box_receivers(xyz: np.ndarray, n: int, seed: int = 7) -> np.ndarray:
+    """n distinct node indices on the bottom face z = min z, in a seeded
+    order (splitmix64 keys)."""
+    z0 = xyz[:, 2].min()
+    cand = np.nonzero(np.abs(xyz[:, 2] - z0) <= 1e-9 * max(1.0, float(np.abs(xyz).max())))[0]
+    if n > len(cand):
+        raise ValueError("box_receivers: fewer bottom-face nodes than receivers")
+    order = np.argsort(splitmix64(seed, len(cand)), kind="stable")
+    return np.sort(cand[order[:n]]).astype(np.int32)
+
+
+def box_traction(xyz: np.ndarray, tri: np.ndarray, N: int, dt: float, width: float, t0: float, tw: float,
+                 seed: int = 11) -> np.ndarray:
+    """Traction samples g (N + 1, n_tris, 3), real: on the top-face
+    elements (centroid z = max z) a downward load exp(-|c - p|^2 / (2 w^2))
+    exp(-(t_n - t0)^2 / (2 tw^2)), p a seeded point of the top face; zero
+    elsewhere."""
+    c = xyz[tri].mean(axis=1)
+    zt = xyz[:, 2].max()
+    top = np.abs(c[:, 2] - zt) <= 1e-9 * max(1.0, float(np.abs(xyz).max()))
+    lo, hi = xyz[:, :2].min(0), xyz[:, :2].max(0)
+    u = uniform01(seed, 2)
+    p = lo + (0.25 + 0.5 * u) * (hi - lo)
+    space = np.exp(-((c[:, :2] - p) ** 2).sum(1) / (2.0 * width ** 2)) * top
+    t = dt * np.arange(N + 1)
+    time = np.exp(-((t - t0) ** 2) / (2.0 * tw ** 2))
+    g = np.zeros((N + 1, len(tri), 3))
+    g[:, :, 2] = -time[:, None] * space[None, :]
+    return g
 
 
 def batch_meshes(count: int = 32, n_max: int = 25):

@@ -79,3 +79,31 @@ def test_slotted_cylinder_is_closed_outward_and_counted(params):
 def test_slotted_cylinder_default_is_the_large_configuration_size():
     xyz, tri = syn.slotted_cylinder()
     assert len(tri) == 60048
+
+
+@pytest.mark.parametrize("dims", [(1.0, 1.0, 0.5, 0.5), (3.0, 2.0, 1.0, 0.5), (20.0, 20.0, 10.0, 0.4)])
+def test_box_counts_volume_and_closed_orientation(dims):
+    lx, ly, lz, h = dims
+    xyz, tri = syn.box(lx, ly, lz, h)
+    nx, ny, nz = (round(e / h) for e in (lx, ly, lz))
+    assert len(tri) == 4 * (nx * ny + nx * nz + ny * nz)
+    assert len(xyz) == len(tri) // 2 + 2                    # Euler: closed genus-0 triangulation
+    P = xyz[tri]
+    assert np.einsum("ij,ij->i", P[:, 0], np.cross(P[:, 1], P[:, 2])).sum() / 6.0 == pytest.approx(lx * ly * lz)
+    # every directed edge appears once and its reverse once: closed, consistently oriented
+    de = [(int(a), int(b)) for t in tri for a, b in ((t[0], t[1]), (t[1], t[2]), (t[2], t[0]))]
+    assert len(set(de)) == len(de) and all((b, a) in set(de) for a, b in de[:2000])
+    assert np.allclose(xyz.min(0), 0.0) and np.allclose(xyz.max(0), (lx, ly, lz))
+
+
+def test_box_adjoint_workload_inputs():
+    w = syn.BOX_ADJOINT
+    xyz, tri = syn.box(w["lx"], w["ly"], w["lz"], w["h"])
+    assert (len(tri), len(xyz)) == (20000, 10002)
+    rec = syn.box_receivers(xyz, w["receivers"])
+    assert len(np.unique(rec)) == 64 and np.allclose(xyz[rec, 2], 0.0)
+    g = syn.box_traction(xyz, tri, 20, w["dt"], w["width"], w["t0"], w["tw"])
+    loaded = np.abs(g).sum(axis=(0, 2)) > 0
+    c = xyz[tri].mean(axis=1)
+    assert loaded.any() and np.allclose(c[loaded, 2], w["lz"])   # top face only
+    assert np.all(g[:, :, :2] == 0.0) and np.all(g[:, :, 2] <= 0.0)
