@@ -205,24 +205,100 @@ def run_batch(count, n_max, n_streams):
         return out
     warm = trees()[:2]
     g.compress_batch(warm, 2)
+    del warm
     ts = trees()
     entries = sum(t.n_rows * t.n_cols * t.mesh.ctx.K for t in ts)
+    # one operator at a time, each released before the next (the 32
+    # compressed operators of the largest meshes do not fit together)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ops = [t.compress(stream=0) for t in ts]
+    for t in ts:
+        op = t.compress(stream=0)
+        del op
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
-    del ops
+    # the work list in waves that fit the device: an operator's faces and
+    # fibres during 3D-ACA take about 144 bytes per block entry and
+    # iteration; with up to K / 3 iterations assumed, waves of at most
+    # n_streams operators whose estimates sum to half the free memory
     ts = trees()
+    ts.sort(key=lambda t: -t.n_rows * t.n_cols * t.mesh.ctx.K)
+    budget = 0.5 * torch.cuda.mem_get_info()[0]
+    waves, cur, used = [], [], 0.0
+    for t in ts:
+        est = 144.0 * t.n_rows * t.n_cols * max(1, t.mesh.ctx.K // 3)
+        if cur and (len(cur) == n_streams or used + est > budget):
+            waves.append(cur)
+            cur, used = [], 0.0
+        cur.append(t)
+        used += est
+    waves.append(cur)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ops = g.compress_batch(ts, n_streams)
+    for wv in waves:
+        ops = g.compress_batch(wv, min(n_streams, len(wv)))
+        del ops
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     print(json.dumps({"case": "multi-mesh workload, single layer, node rows, MIXED", "meshes": len(ts),
                       "n_max": n_max, "triangles": int(sum(t.n_cols for t in ts)), "block_entries": int(entries),
                       "sequential_s": t_seq, "batch_s": t_batch, "n_streams": n_streams,
+                      "batch_form": f"{len(waves)} waves of at most {n_streams} operators (memory-bounded)",
                       "sequential_entries_per_s": entries / t_seq, "batch_entries_per_s": entries / t_batch}))
+
+
+# ---------------------------------------------------------------------------
+# adjoint workload: box, traction pulse, receiver energy gradient (not the
+# bench line)
+# ---------------------------------------------------------------------------
+
+def run_adjoint(h, steps):
+    """The box adjoint workload of synthetic.BOX_ADJOINT at grid spacing h
+    (0.4 m is the full 20,000-triangle size): MIXED compression of V, C + K
+    and their four wave-speed derivative operators (node rows), then the
+    receiver energy and its gradient in the traction and in c_p, c_s
+    (bem_receiver_energy_grad: forward solve, adjoint solve, CQ transforms)
+    timed over `steps` calls after one warm-up call; one JSON line."""
+    import torch
+    import paper_2607_15292_b300 as g
+    w = syn.BOX_ADJOINT
+    xyz, tri = syn.box(w["lx"], w["ly"], w["lz"], h)
+    N, dt = w["N"], w["dt"]
+    K = (N + 1) // 2 + 1
+    s = g.freqs_bdf2(N, dt, K)
+    ctx = g.Context(eps=1e-6, leaf=32, eta=2.0, precision=g.BEM_MIXED)
+    ctx.material(*syn.STEEL)
+    ctx.freqs(s)
+    mesh = ctx.mesh(xyz, tri)
+    kinds = (g.BEM_SL, g.BEM_DL, g.BEM_SL_DCP, g.BEM_SL_DCS, g.BEM_DL_DCP, g.BEM_DL_DCS)
+    trees = [mesh.tree(g.BEM_ROWS_NODES, k) for k in kinds]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ops = [t.compress() for t in trees]
+    torch.cuda.synchronize()
+    t_comp = time.perf_counter() - t0
+    V, A, dVp, dVs, dAp, dAs = ops
+    gt = torch.tensor(syn.box_traction(xyz, tri, N, dt, w["width"], w["t0"], w["tw"]), dtype=torch.float64,
+                      device="cuda")
+    rec = syn.box_receivers(xyz, w["receivers"])
+    args = dict(dV=(dVp, dVs), dA=(dAp, dAs), tol=1e-6, max_iter=500)
+    g.receiver_energy_grad(V, A, gt, rec, N, dt, **args)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        J, dg, dc, it = g.receiver_energy_grad(V, A, gt, rec, N, dt, **args)
+    torch.cuda.synchronize()
+    t_grad = (time.perf_counter() - t0) / steps
+    st = [o.stats() for o in ops]
+    print(json.dumps({
+        "case": "box adjoint workload (receiver energy and its gradient in traction and c_p, c_s)",
+        "box": [w["lx"], w["ly"], w["lz"]], "h": h, "triangles": len(tri), "nodes": len(xyz), "N": N, "dt": dt,
+        "K": K, "receivers": len(rec), "precision": "MIXED", "eps": 1e-6, "solve_tol": 1e-6,
+        "compress_s_six_operators": t_comp, "gradient_ms": t_grad * 1e3, "steps": steps,
+        "J": J, "dJ_dc": dc, "dJ_dg_max": float(dg.abs().max()),
+        "iters_forward_max": int(it[:K].max()), "iters_adjoint_max": int(it[K:].max()),
+        "stored_gb": [round(x.stored_bytes / 1e9, 3) for x in st],
+        "rank_mean": [round(x.rank_mean, 2) for x in st]}))
 
 
 # ---------------------------------------------------------------------------
@@ -245,6 +321,9 @@ def main():
                          "work list; prints both rates (not the bench line)")
     ap.add_argument("--batch-nmax", type=int, default=25, help="cap on the grid size n of --batch meshes")
     ap.add_argument("--batch-streams", type=int, default=4)
+    ap.add_argument("--adjoint", type=float, default=0.0, metavar="H",
+                    help="box adjoint workload at grid spacing H (0.4 = full size): compression of the six "
+                         "operators and the receiver-energy gradient; prints its statistics (not the bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -252,6 +331,8 @@ def main():
         return run_small()
     if args.batch:
         return run_batch(args.batch, args.batch_nmax, args.batch_streams)
+    if args.adjoint > 0:
+        return run_adjoint(args.adjoint, max(1, args.steps))
 
     import torch
     import paper_2607_15292_b300 as g
@@ -454,6 +535,11 @@ def main():
         torch.cuda.synchronize()
         ms64 = b0.elapsed_time(b1) / fp64_steps
         e64 = oV64.stats().entries_evaluated + oK64.stats().entries_evaluated
+        s64V, s64K = oV64.stats(), oK64.stats()
+        extra.update({"fp64_compression_rate_V": s64V.compression_rate, "fp64_compression_rate_K": s64K.compression_rate,
+                      "fp64_faces_lowrank_V": [int(s64V.n_faces_lowrank), int(s64V.n_faces)],
+                      "fp64_faces_lowrank_K": [int(s64K.n_faces_lowrank), int(s64K.n_faces)],
+                      "fp64_rank_mean_V": s64V.rank_mean, "fp64_rank_mean_K": s64K.rank_mean})
         oV.apply(XV, YV, g.BEM_APPLY_BATCHED, stream)
         oK.apply(XK, YK, g.BEM_APPLY_BATCHED, stream)
         torch.cuda.synchronize()

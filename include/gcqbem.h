@@ -262,6 +262,43 @@ bem_status bem_op_apply(bem_op* op, int32_t mode, int32_t transpose,
 bem_status bem_op_solve(bem_op* op, const void* B, void* X, double tol, int32_t max_iter,
                         int32_t* iters, double* relres, void* stream);
 
+/* The adjoint systems C(s_k)^H x_k = b_k for every k, by the same
+ * K-batched BiCGstab on the conjugate-transpose apply (the adjoint solve of
+ * the adjoint method: Sec. 3's Eq. (3.15) transposed).  Arguments, scratch,
+ * errors and stream behaviour as bem_op_solve. */
+bem_status bem_op_solve_adjoint(bem_op* op, const void* B, void* X, double tol, int32_t max_iter,
+                                int32_t* iters, double* relres, void* stream);
+
+/* Receiver energy of a traction-driven Neumann problem and its gradient by
+ * the adjoint method (time stepping by uniform-step CQ, Sec. 2.4; Neumann
+ * rows, Sec. 2.3, Eq. (2.12)):
+ *   g^_k = forward CQ transform of the traction samples g_n (k < K)
+ *   A_k u^_k = V_k g^_k                (K-batched BiCGstab)
+ *   u_n = inverse CQ transform (real; the frequencies above K are the
+ *         conjugates of the ones held: s_(L-k) = conj s_k)
+ *   J = dt sum_n sum_r |u_n[rec[r]]|^2
+ * and, by one adjoint solve with A^H, dJ/dg (every time level, element and
+ * component) and dJ/dc_p, dJ/dc_s at fixed density (through the derivative
+ * operators).  The context's K frequencies must be the half set
+ * k = 0 .. floor((N + 1) / 2) of bem_freqs_bdf2(N, dt) (checked to 1e-9).
+ * V: single layer (BEM_SL), A: double layer C + K (BEM_DL), both with node
+ * rows on one mesh.  dV[a], dA[a] (a < n_speeds <= 2): the kernels
+ * BEM_SL_DCP / BEM_DL_DCP (a = 0, c_p) and BEM_SL_DCS / BEM_DL_DCS (a = 1,
+ * c_s) on the same mesh and frequencies.  g: device, real FP64,
+ * (N + 1) x n_tris x 3.  rec: host, n_rec distinct node indices.  J: host
+ * double.  dJ_dg: device, real FP64, (N + 1) x n_tris x 3, or NULL.  dJ_dc:
+ * host double[n_speeds].  iters: host int32[2K], BiCGstab iterations of the
+ * forward (first K) and adjoint (last K) solves.  Transforms in FP64, vectors
+ * in the operators' complex type.  Allocates (K (6 n_tris + 12 n_nodes) + 3
+ * (N + 1) n_rec) values of device scratch plus the solves' scratch, and
+ * synchronises the stream.  Errors: BEM_ERR_ARG (kinds, meshes, frequencies,
+ * receivers, pointers), BEM_ERR_NOT_CONVERGED (a solve above tol),
+ * BEM_ERR_OOM, BEM_ERR_CUDA. */
+bem_status bem_receiver_energy_grad(bem_op* V, bem_op* A, bem_op* const* dV, bem_op* const* dA, int32_t n_speeds,
+                                    int32_t N, double dt, const double* g, const int32_t* rec, int64_t n_rec,
+                                    double tol, int32_t max_iter, double* J, double* dJ_dg, double* dJ_dc,
+                                    int32_t* iters, void* stream);
+
 /* Inner product <G, C X>: BATCHED, sum over k, rows i and components of
  * conj(G_k[i]) (C(s_k) X_k)[i]; CONTRACTED, sum over i of
  * conj(g[i]) (sum_k C(s_k) X_k)[i].  One complex number accumulated in FP64,

@@ -91,6 +91,9 @@ _SIGS = {
     "bem_op_face_ranks": (_i32, [_vp, _P(_i32)]),
     "bem_op_solve": (_i32, [_vp, _vp, _vp, _dbl, _i32, _P(_i32), _P(_dbl), _vp]),
     "bem_op_inner": (_i32, [_vp, _i32, _vp, _vp, _P(_dbl), _vp]),
+    "bem_op_solve_adjoint": (_i32, [_vp, _vp, _vp, _dbl, _i32, _P(_i32), _P(_dbl), _vp]),
+    "bem_receiver_energy_grad": (_i32, [_vp, _vp, _P(_vp), _P(_vp), _i32, _i32, _dbl, _vp, _P(_i32), _i64, _dbl,
+                                        _i32, _P(_dbl), _vp, _P(_dbl), _P(_i32), _vp]),
     "bem_op_compress_batch": (_i32, [_P(_vp), _i32, _i32, _P(_vp)]),
     "bem_op_set_apply_tile": (_i32, [_vp, _i32]),
     "bem_op_set_apply_kernel": (_i32, [_vp, _i32]),
@@ -239,6 +242,36 @@ def _cq_args(N, nvec, x, out):
         _device_tensor(name, t, torch.complex128, (N + 1, nvec), None)
     if x.data_ptr() == out.data_ptr():
         raise ValueError("cq: in and out must not overlap")
+
+
+def receiver_energy_grad(V: "Operator", A: "Operator", g, rec, N: int, dt: float, dV=(), dA=(),
+                         tol: float = 1e-8, max_iter: int = 500, grad_g: bool = True, stream=None):
+    """Receiver energy J of the traction-driven Neumann problem (V single
+    layer, A = C + K double layer, node rows, the context holding the half
+    set of the BDF2 frequencies of N, dt) and its adjoint gradient
+    (bem_receiver_energy_grad).  g: real float64 device tensor
+    (N + 1, n_tris, 3); rec: distinct node indices.  Returns (J, dJ/dg as a
+    (N + 1, n_tris, 3) float64 device tensor or None, [dJ/dc_p, dJ/dc_s][:len(dV)],
+    BiCGstab iterations of the forward and adjoint solves (2K))."""
+    import torch
+    ctx = V.ctx
+    _device_tensor("g", g, torch.float64, (N + 1, V.tree.n_cols, 3), ctx.device)
+    rec = np.ascontiguousarray(np.asarray(rec, dtype=np.int32))
+    if len(dV) != len(dA) or len(dV) > 2:
+        raise ValueError("receiver_energy_grad: dV and dA must be pairs, at most two")
+    dg = torch.empty((N + 1, V.tree.n_cols, 3), dtype=torch.float64, device=g.device) if grad_g else None
+    ns = len(dV)
+    pv = (_vp * max(1, ns))(*[o._p for o in dV]) if ns else None
+    pa = (_vp * max(1, ns))(*[o._p for o in dA]) if ns else None
+    J = np.zeros(1, dtype=np.float64)
+    dc = np.zeros(max(1, ns), dtype=np.float64)
+    it = np.zeros(2 * V.K, dtype=np.int32)
+    _check(_lib.bem_receiver_energy_grad(V._p, A._p, pv, pa, ns, int(N), float(dt), _dptr(g),
+                                         rec.ctypes.data_as(_P(_i32)), len(rec), float(tol), int(max_iter),
+                                         J.ctypes.data_as(_P(_dbl)), _dptr(dg) if dg is not None else None,
+                                         dc.ctypes.data_as(_P(_dbl)), it.ctypes.data_as(_P(_i32)),
+                                         _stream_ptr(stream)), ctx.ptr)
+    return float(J[0]), dg, [float(x) for x in dc[:ns]], it
 
 
 def cq_forward(N: int, nvec: int, x, out, stream=None):
@@ -464,10 +497,12 @@ class Operator:
         _device_tensor("output", Y, cdt, sout, self.ctx.device)
         _check(_lib.bem_op_apply(self._p, mode, transpose, _dptr(X), _dptr(Y), _stream_ptr(stream)), self.ctx.ptr)
 
-    def solve(self, B, X, tol: float = 1e-8, max_iter: int = 200, stream=None, check: bool = True):
-        """X_k = C(s_k)^{-1} B_k for all k (BiCGstab); returns (iterations,
-        relative residuals) per frequency.  With check=False a frequency that
-        did not converge is not an error (the residuals tell)."""
+    def solve(self, B, X, tol: float = 1e-8, max_iter: int = 200, stream=None, check: bool = True,
+              adjoint: bool = False):
+        """X_k = C(s_k)^{-1} B_k for all k (BiCGstab), or C(s_k)^{-H} B_k with
+        adjoint=True; returns (iterations, relative residuals) per frequency.
+        With check=False a frequency that did not converge is not an error
+        (the residuals tell)."""
         if self.tree.n_rows != self.tree.n_cols:
             raise ValueError("solve: the operator is not square")
         cdt = _cdtype(self.ctx.precision)
@@ -475,8 +510,9 @@ class Operator:
         _device_tensor("X", X, cdt, (self.K, self.tree.n_rows, 3), self.ctx.device)
         it = np.zeros(self.K, dtype=np.int32)
         rr = np.zeros(self.K, dtype=np.float64)
-        st = _lib.bem_op_solve(self._p, _dptr(B), _dptr(X), float(tol), int(max_iter),
-                               it.ctypes.data_as(_P(_i32)), rr.ctypes.data_as(_P(_dbl)), _stream_ptr(stream))
+        fn = _lib.bem_op_solve_adjoint if adjoint else _lib.bem_op_solve
+        st = fn(self._p, _dptr(B), _dptr(X), float(tol), int(max_iter),
+                it.ctypes.data_as(_P(_i32)), rr.ctypes.data_as(_P(_dbl)), _stream_ptr(stream))
         if check or st != BEM_ERR_NOT_CONVERGED:
             _check(st, self.ctx.ptr)
         return it, rr

@@ -15,7 +15,7 @@ from __future__ import annotations
 
 import torch
 
-from . import BEM_APPLY_BATCHED, BEM_APPLY_CONTRACTED, Operator
+from . import BEM_APPLY_BATCHED, BEM_APPLY_CONTRACTED, Operator, receiver_energy_grad
 
 
 class OperatorApply(torch.autograd.Function):
@@ -87,3 +87,33 @@ def apply_speeds(op: Operator, dops, X: torch.Tensor, c: torch.Tensor,
 
 __all__ = ["OperatorApply", "WaveSpeedApply", "apply", "apply_speeds", "BEM_APPLY_BATCHED",
            "BEM_APPLY_CONTRACTED"]
+
+
+class ReceiverEnergy(torch.autograd.Function):
+    """J(g, c) = dt sum_n sum_r |u_n[r]|^2 of the traction-driven Neumann
+    problem through CQ (bem_receiver_energy_grad), differentiable in the
+    traction samples g (real float64 (N + 1, n_tris, 3) on the device) and
+    the wave speeds c = (c_p, c_s) (real tensor of shape (2,), the speeds the
+    operators were compressed at; its value is not read).  The library
+    computes J and both gradients in one call (forward solve, adjoint
+    solve), so the backward only scales them by the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, g: torch.Tensor, c: torch.Tensor, V: Operator, A: Operator, dV, dA, rec, N: int, dt: float,
+                tol: float = 1e-8, max_iter: int = 500):
+        J, dg, dc, _ = receiver_energy_grad(V, A, g.contiguous(), rec, N, dt, dV=dV, dA=dA, tol=tol,
+                                            max_iter=max_iter, grad_g=True)
+        ctx.save_for_backward(dg)
+        ctx.dc = torch.tensor(dc + [0.0] * (2 - len(dc)), dtype=c.dtype, device=c.device)
+        return torch.tensor(J, dtype=torch.float64, device=g.device)
+
+    @staticmethod
+    def backward(ctx, gJ: torch.Tensor):
+        (dg,) = ctx.saved_tensors
+        return gJ * dg, gJ.to(ctx.dc.device) * ctx.dc, None, None, None, None, None, None, None, None, None
+
+
+def receiver_energy(g: torch.Tensor, c: torch.Tensor, V: Operator, A: Operator, dV, dA, rec, N: int, dt: float,
+                    tol: float = 1e-8, max_iter: int = 500) -> torch.Tensor:
+    """Differentiable receiver energy (see ReceiverEnergy)."""
+    return ReceiverEnergy.apply(g, c, V, A, tuple(dV), tuple(dA), rec, N, dt, tol, max_iter)

@@ -173,6 +173,130 @@ __device__ __forceinline__ T warp_transpose_sum(T* v) {
   return v[0];
 }
 
+// ---- device-side control of the iterations ------------------------------------
+// The host launches the iterations in batches and synchronises once per
+// batch; each iteration starts with k_compact, which builds the active list,
+// the tile list and the face and fibre storage of the blocks still active
+// from the block records, taking the storage from a pre-allocated pool.  An
+// iteration that does not fit the pool is flagged (and every later one in the
+// batch does nothing) until the host has added a larger pool chunk and
+// launches it again.
+struct LoopCtl {
+  int64_t n_active, n_tiles;    // of the iteration compacted last
+  int64_t pool_used;            // bytes taken from the pool chunk in use
+  int64_t overflow_slot;        // first iteration that did not fit, -1 none
+  int64_t need;                 // bytes that iteration needs
+  int64_t last_bytes;           // bytes of the iteration compacted last
+  int64_t entries;              // entries evaluated: m n + K per active block and iteration
+  double face_alg_bytes;        // (slot + 1) faces per entry of an active block
+};
+
+__device__ __forceinline__ int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
+
+// block-wide exclusive scan of three counters over 1024 threads
+__device__ __forceinline__ void scan3(int64_t (&v)[3], int64_t (&tot)[3], int64_t (*sh)[3]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t inc[3] = {v[0], v[1], v[2]};
+  for (int o = 1; o < 32; o <<= 1)
+    for (int c = 0; c < 3; ++c) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, inc[c], o);
+      if (lane >= o) inc[c] += y;
+    }
+  if (lane == 31)
+    for (int c = 0; c < 3; ++c) sh[wid][c] = inc[c];
+  __syncthreads();
+  if (wid == 0) {
+    int64_t w[3] = {sh[lane][0], sh[lane][1], sh[lane][2]};
+    for (int o = 1; o < 32; o <<= 1)
+      for (int c = 0; c < 3; ++c) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, w[c], o);
+        if (lane >= o) w[c] += y;
+      }
+    for (int c = 0; c < 3; ++c) sh[lane][c] = w[c];   // inclusive prefix of the warp totals
+  }
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) {
+    const int64_t before = wid > 0 ? sh[wid - 1][c] : 0;
+    tot[c] = sh[31][c];
+    v[c] = before + inc[c] - v[c];   // exclusive
+  }
+  __syncthreads();
+}
+
+template <typename S>
+__global__ void __launch_bounds__(1024) k_compact(BlkDev* __restrict__ blk, int64_t nb, int slot, int K,
+                                                  char* __restrict__ pool, int64_t pool_cap, LoopCtl* __restrict__ ctl,
+                                                  int32_t* __restrict__ active, Tile* __restrict__ tiles,
+                                                  void** __restrict__ face_tab, void** __restrict__ fib_tab,
+                                                  int64_t* __restrict__ slot_entries) {
+  __shared__ int64_t sh[32][3];
+  __shared__ int64_t run[3];          // active blocks, tiles, bytes so far
+  __shared__ double run_mn;
+  __shared__ int skip;
+  if (threadIdx.x == 0) {
+    skip = ctl->overflow_slot >= 0;
+    run[0] = run[1] = run[2] = 0;
+    run_mn = 0.0;
+  }
+  __syncthreads();
+  if (skip) {   // a previous iteration did not fit: nothing until the host relaunches it
+    if (threadIdx.x == 0) ctl->n_active = ctl->n_tiles = 0;
+    return;
+  }
+  const int64_t base = ctl->pool_used;
+  const int64_t fib_bytes = align256((int64_t)K * 9 * sizeof(S));
+  for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+    const int64_t b = b0 + threadIdx.x;
+    const bool on = b < nb && blk[b].status == ST_ACTIVE;
+    const int64_t mn = on ? blk[b].m * blk[b].n : 0;
+    int64_t v[3] = {on ? 1 : 0, (mn + kTile - 1) / kTile, on ? align256(mn * 9 * (int64_t)sizeof(S)) + fib_bytes : 0};
+    const int64_t mine[3] = {v[0], v[1], v[2]};
+    int64_t tot[3];
+    scan3(v, tot, sh);
+    if (on) {
+      const int64_t a = run[0] + v[0], t0 = run[1] + v[1], off = base + run[2] + v[2];
+      active[a] = (int32_t)b;
+      blk[b].t0 = (int32_t)t0;
+      blk[b].t1 = (int32_t)(t0 + mine[1]);
+      face_tab[(int64_t)slot * nb + b] = pool + off;
+      fib_tab[(int64_t)slot * nb + b] = pool + off + (mine[2] - fib_bytes);
+    }
+    // tile lists: the warp writes the tiles of its active blocks together
+    // (a large far block has thousands of tiles)
+    const int lane = threadIdx.x & 31;
+    const long long my_t0 = run[1] + v[1];
+    for (unsigned msk = __ballot_sync(0xffffffffu, on); msk; msk &= msk - 1) {
+      const int L = __ffs(msk) - 1;
+      const long long t0L = __shfl_sync(0xffffffffu, my_t0, L);
+      const long long ntL = __shfl_sync(0xffffffffu, (long long)mine[1], L);
+      const int32_t bL = (int32_t)__shfl_sync(0xffffffffu, (long long)b, L);
+      for (long long q = lane; q < ntL; q += 32) tiles[t0L + q] = Tile{bL, -1, (int64_t)q * kTile};
+    }
+    double smn = (double)mn;
+    for (int o = 16; o > 0; o >>= 1) smn += __shfl_down_sync(0xffffffffu, smn, o);
+    if ((threadIdx.x & 31) == 0 && smn > 0.0) atomicAdd(&run_mn, smn);
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 3; ++c) run[c] += tot[c];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (base + run[2] > pool_cap) {
+      ctl->overflow_slot = slot;
+      ctl->need = run[2];
+      ctl->n_active = ctl->n_tiles = 0;
+    } else {
+      ctl->pool_used = base + run[2];
+      ctl->last_bytes = run[2];
+      ctl->n_active = run[0];
+      ctl->n_tiles = run[1];
+      ctl->entries += (int64_t)run_mn + (int64_t)K * run[0];
+      ctl->face_alg_bytes += (double)(slot + 1) * sizeof(S) * 9.0 * run_mn;
+      slot_entries[slot] = (int64_t)run_mn;
+    }
+  }
+}
+
 // ---- face kernel -------------------------------------------------------------
 // FP64 mode: faces/fibres in c128, residual, pivot criterion and Gram products
 // in double.  MIXED mode: faces/fibres in complex float-float (float4), the
@@ -216,8 +340,10 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
                                                 const int32_t* __restrict__ col_perm, double* __restrict__ p_s3,
                                                 int64_t* __restrict__ p_idx, double* __restrict__ p_h2,
                                                 double2* __restrict__ p_M, const double* __restrict__ hn2, int K,
-                                                int* __restrict__ err, int dbg_fail) {
+                                                int* __restrict__ err, int dbg_fail,
+                                                const LoopCtl* __restrict__ ctl) {
   using W = typename WorkOf<S>::W;
+  if ((int64_t)blockIdx.x >= ctl->n_tiles) return;   // the grid is an upper bound of this iteration's tiles
   // Previous faces stream through shared memory: the tile's 256 entries of a
   // face are one contiguous range (256 x 9 x 16 B = 36 KB), copied by one
   // bulk TMA copy into one of two buffers.  Copy n (n = 0 .. 2 slot - 1)
@@ -228,7 +354,10 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   // entry evaluation.
   extern __shared__ __align__(128) unsigned char kf_dyn[];   // 2 x kTile x 9 S
   __shared__ __align__(8) uint64_t kf_bar[2];
-  __shared__ S sf[64 * 9];     // f_p[k_d] for p < slot, in chunks of 64
+  // f_p[k_d] for p < slot in chunks of 64 (residual pass), the staging of
+  // the new face and the Gram partials of the warps (Gram pass): one buffer
+  __shared__ __align__(16) unsigned char kf_u[64 * 9 * sizeof(S) + kTile / 32 * 16 * 18 * sizeof(W)];
+  S* const sf = reinterpret_cast<S*>(kf_u);
   __shared__ unsigned char ssmall[64];   // term p below 2^-10 of the first: plain FMA (MIXED)
   __shared__ double shv[32 * 18];
   __shared__ int64_t shi[32];
@@ -409,25 +538,45 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   }
   S* Hd = face_tab[(int64_t)slot * nb + t.blk];
   cx<W> H[9];   // working copy for the pivot criterion and the Gram
+  // the stored face entry c of this thread (MIXED: the small terms folded
+  // in, (h, l) renormalised)
+  auto face_val = [&](int c) -> float4 {
+    const float rh = fh[2 * c] + fl[2 * c];
+    const float rl = fl[2 * c] - (rh - fh[2 * c]);
+    const float ih = fh[2 * c + 1] + fl[2 * c + 1];
+    const float il = fl[2 * c + 1] - (ih - fh[2 * c + 1]);
+    return make_float4(rh, ih, rl, il);
+  };
   if (ok) {
     for (int c = 0; c < 9; ++c) {
       if constexpr (FF) {
-        // fold in the small terms, renormalise (h, l) and store
         fl[2 * c] -= fs[2 * c];
         fl[2 * c + 1] -= fs[2 * c + 1];
-        float rh = fh[2 * c] + fl[2 * c];
-        float rl = fl[2 * c] - (rh - fh[2 * c]);
-        float ih = fh[2 * c + 1] + fl[2 * c + 1];
-        float il = fl[2 * c + 1] - (ih - fh[2 * c + 1]);
-        reinterpret_cast<float4*>(Hd)[e * 9 + c] = make_float4(rh, ih, rl, il);
-        H[c] = {(W)rh, (W)ih};
+        const float4 x = face_val(c);
+        H[c] = {(W)x.x, (W)x.y};
       } else {
-        St<S>::st(Hd + e * 9 + c, Hd64[c]);
+        St<S>::st(Hd + e * 9 + c, Hd64[c]);   // FP64: stored directly
         H[c] = {(W)Hd64[c].x, (W)Hd64[c].y};
       }
     }
   } else {
     for (int c = 0; c < 9; ++c) H[c] = {W(0), W(0)};
+  }
+  // MIXED: the tile's face leaves through shared memory, two halves of 128
+  // entries (144 bytes each), as contiguous 16-byte stores: a thread's own
+  // 144 bytes stored directly are 9 stores 144 bytes apart per lane, whose
+  // partly written sectors the L2 may evict before the rest arrives
+  if constexpr (FF) {
+    float4* const stage = reinterpret_cast<float4*>(kf_u);   // 128 x 9 x 16 B = 18 KB
+    float4* const gdst = reinterpret_cast<float4*>(Hd) + t.start * 9;
+    for (int half = 0; half < 2; ++half) {
+      __syncthreads();   // kf_u free: residual pass (or the previous half) done
+      if (ok && (threadIdx.x >> 7) == half)
+        for (int c = 0; c < 9; ++c) stage[(threadIdx.x & 127) * 9 + c] = face_val(c);
+      __syncthreads();
+      const int cnt = (int)max((int64_t)0, min((int64_t)128, nval - half * 128)) * 9;
+      for (int q = threadIdx.x; q < cnt; q += blockDim.x) gdst[half * 128 * 9 + q] = stage[q];
+    }
   }
   double s3 = ok ? (double)sigma3<W>(H) : -1.0;
   int64_t idx = ok ? e : INT64_MAX;
@@ -457,7 +606,7 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   // shared memory, then a fixed-order sum over the warps.
   // p = slot is the face in registers; p < slot arrive as copies
   // n = 2 slot - 1 - p (the reverse of the residual pass's order).
-  __shared__ W gw[kTile / 32][16][18];
+  W(*const gw)[16][18] = reinterpret_cast<W(*)[16][18]>(kf_u + 64 * 9 * sizeof(S));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int p0 = 0; p0 <= slot; p0 += 16) {
     const int np = min(16, slot + 1 - p0);
@@ -521,7 +670,9 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
 __global__ void k_block_red(BlkDev* __restrict__ blk, const int32_t* __restrict__ active, int slot,
                             const double* __restrict__ p_s3, const int64_t* __restrict__ p_idx,
                             const double* __restrict__ p_h2, const double2* __restrict__ p_M,
-                            double2* __restrict__ M, double* __restrict__ hn2, int K) {
+                            double2* __restrict__ M, double* __restrict__ hn2, int K,
+                            const LoopCtl* __restrict__ ctl) {
+  if ((int64_t)blockIdx.x >= ctl->n_active) return;
   __shared__ double shv[32 * 18];
   __shared__ int64_t shi[32];
   const int b = active[blockIdx.x];
@@ -567,7 +718,8 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
                              S* const* __restrict__ fib_tab, int64_t nb, int slot,
                              const int32_t* __restrict__ row_perm, const int32_t* __restrict__ col_perm,
                              const double2* __restrict__ M, int32_t* __restrict__ ks, uint8_t* __restrict__ used,
-                             int K, double eps) {
+                             int K, double eps, const LoopCtl* __restrict__ ctl) {
+  if ((int64_t)blockIdx.x >= ctl->n_active) return;
   __shared__ double shv[32 * 18];
   __shared__ int64_t shi[32];
   __shared__ int decision;
@@ -618,17 +770,25 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
   if (heavy) {
     // a near/singular pivot entry is evaluated as k_face evaluates it
     // (warp-cooperative, same point split and reduction): bitwise the same
-    // value at k = k_d, so that f_d[k_d] = I holds exactly
-    const int lane = threadIdx.x & 31, w0 = threadIdx.x & ~31;
-    for (int kk = 0; kk < 32 && w0 + kk < K; ++kk) {
+    // value at k = k_d, so that f_d[k_d] = I holds exactly.  Every warp of
+    // the CTA takes frequencies kk = warp, warp + warps, ...; the values
+    // meet in the dynamic shared buffer (free until the fibre Gram below)
+    extern __shared__ double2 sfd_heavy[];
+    float* sE = reinterpret_cast<float*>(sfd_heavy);   // K x 18
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int kk = wid; kk < K; kk += nw) {
       cx<double> is2b;
-      const cx<double> s2 = freq(v, w0 + kk, is2b);
+      const cx<double> s2 = freq(v, kk, is2b);
       float part[18];
       entry_f_warp<KERN, ROWS>(v, i, j, cx<float>{(float)s2.x, (float)s2.y}, cx<float>{(float)is2b.x, (float)is2b.y},
-                               w0 + kk, part);
-      if (lane == kk)
-        for (int c = 0; c < 9; ++c) E[c] = {(double)part[2 * c], (double)part[2 * c + 1]};
+                               kk, part);
+      if (lane == 0)
+        for (int c = 0; c < 18; ++c) sE[kk * 18 + c] = part[c];
     }
+    __syncthreads();
+    if (ok)
+      for (int c = 0; c < 9; ++c) E[c] = {(double)sE[k * 18 + 2 * c], (double)sE[k * 18 + 2 * c + 1]};
+    __syncthreads();   // sE is overwritten by f_d below
   }
   if (ok) {
     if (!heavy) {
@@ -682,6 +842,10 @@ __global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
       }
     }
     mm3(Pi, E, f);
+    // Algorithm 1's fibre at the face's own frequency is the identity,
+    // f_d[k_d] = H_d[i_d, j_d]^-1 H_d[i_d, j_d]: stored exactly
+    if (k == B.k_cur)
+      for (int c = 0; c < 9; ++c) f[c] = {c % 4 == 0 ? 1.0 : 0.0, 0.0};
     for (int c = 0; c < 9; ++c) St<S>::st(fd + (int64_t)k * 9 + c, f[c]);
     for (int c = 0; c < 9; ++c) f[c] = St<S>::ld(fd + (int64_t)k * 9 + c);
   }
@@ -1160,82 +1324,94 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
   scratch_guard.evs = {ev0, ev1, evf};
   float t_ent = 0.f;
   std::vector<Tile> tiles;
-  std::vector<int32_t> active;
   std::vector<void*>& slot_chunks = chunk_guard.bufs;   // compression-time storage of faces and fibres
   bem_status result = BEM_OK;
-  for (int slot = 0; slot < K && result == BEM_OK; ++slot) {
-    active.clear();
-    tiles.clear();
-    size_t face_bytes = 0, fib_bytes = 0;
-    for (int64_t b = 0; b < nb; ++b) {
-      BlkDev& B = d->h_blk[b];
-      if (B.status != ST_ACTIVE) continue;
-      active.push_back((int32_t)b);
-      B.t0 = (int32_t)tiles.size();
-      for (int64_t s0 = 0; s0 < B.m * B.n; s0 += kTile) tiles.push_back(Tile{(int32_t)b, -1, s0});
-      B.t1 = (int32_t)tiles.size();
-      face_bytes += sizeof(S) * 9 * B.m * B.n;
-      fib_bytes += sizeof(S) * 9 * K;
+  // Iterations run in batches of kBatch with one host synchronisation per
+  // batch (k_compact builds every iteration's lists on the device).  The
+  // active set only shrinks, so the tile and block counts at the start of a
+  // batch bound the grids of all its iterations.
+  constexpr int kBatch = 8;
+  LoopCtl h_ctl{};
+  h_ctl.overflow_slot = -1;
+  LoopCtl* d_ctl = nullptr;
+  int64_t* d_slot_entries = nullptr;
+  GCQ_CUDA(ctx, dmalloc(&d_ctl, sizeof(LoopCtl), &scratch));
+  GCQ_CUDA(ctx, dmalloc(&d_slot_entries, sizeof(int64_t) * K, &scratch));
+  GCQ_CUDA(ctx, cudaMemsetAsync(d_slot_entries, 0, sizeof(int64_t) * K, st));
+  GCQ_CUDA(ctx, cudaMemcpyAsync(d_ctl, &h_ctl, sizeof(LoopCtl), cudaMemcpyHostToDevice, st));
+  std::vector<cudaEvent_t> evs(2 * kBatch + 2);
+  for (cudaEvent_t& e : evs) {
+    cudaEventCreate(&e);
+    scratch_guard.evs.push_back(e);
+  }
+  // bytes of one iteration over all blocks (the first iteration's need)
+  const auto al256 = [](int64_t x) { return (x + 255) & ~(int64_t)255; };
+  int64_t need = 0;
+  for (int64_t b = 0; b < nb; ++b)
+    need += al256(d->h_blk[b].m * d->h_blk[b].n * 9 * (int64_t)sizeof(S)) + al256((int64_t)K * 9 * sizeof(S));
+  int64_t n_active = nb, n_tiles = n_tiles_all;   // at the start of the batch
+  char* pool = nullptr;
+  int64_t pool_cap = 0;
+  std::vector<int64_t> batch_entries(kBatch);
+  int slot = 0;
+  while (slot < K && result == BEM_OK && n_active > 0) {
+    if (pool == nullptr) {
+      // a pool chunk for the iterations to come: kBatch iterations at the
+      // current need if it can be had, else fewer, else out of memory
+      for (int64_t f = std::min<int64_t>(kBatch, K - slot); f >= 1 && pool == nullptr; f /= 2)
+        if (dmalloc(&pool, (size_t)(need * f), &slot_chunks) == cudaSuccess) pool_cap = need * f;
+        else pool = nullptr;
+      if (pool == nullptr) {
+        cudaGetLastError();
+        result = set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for 3D-ACA faces");
+        break;
+      }
+      h_ctl.pool_used = 0;
+      h_ctl.overflow_slot = -1;
+      GCQ_CUDA(ctx, cudaMemcpyAsync(d_ctl, &h_ctl, sizeof(LoopCtl), cudaMemcpyHostToDevice, st));
     }
-    if (active.empty()) break;
-    // slot storage: one chunk for all faces + fibres of this slot
-    char* chunk = nullptr;
-    if (dmalloc(&chunk, face_bytes + fib_bytes, &slot_chunks) != cudaSuccess) {
-      result = set_err(ctx, BEM_ERR_OOM, "bem_op_compress: out of device memory for 3D-ACA faces");
-      break;
+    const int s0 = slot, s1 = std::min(K, slot + kBatch);
+    cudaEventRecord(evs[2 * kBatch], st);
+    for (int sl = s0; sl < s1; ++sl) {
+      k_compact<S><<<1, 1024, 0, st>>>(d->d_blk, nb, sl, K, pool, pool_cap, d_ctl, d_active, d_tiles, d->d_face,
+                                       d->d_fib, d_slot_entries);
+      GCQ_CUDA(ctx, cudaGetLastError());
+      cudaEventRecord(evs[2 * (sl - s0)], st);
+      // two face tiles of the TMA double buffer (the same size for every
+      // operator, so the process-wide attribute never changes)
+      const size_t kf_smem = 2 * (size_t)kTile * 9 * sizeof(SC);
+      GCQ_DISPATCH(d->kernel, d->rows,
+                   (cudaFuncSetAttribute(k_face<R, SC, KK, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kf_smem),
+                    k_face<R, SC, KK, RR><<<(unsigned)n_tiles, kTile, kf_smem, st>>>(
+                        v, d_tiles, d->d_blk, (S* const*)d->d_face, (S* const*)d->d_fib, nb, sl, d->d_row_perm,
+                        d->d_col_perm, p_s3, p_idx, p_h2, p_M, d->d_hn2, K, d_err, debug_face_wait_fail(), d_ctl)));
+      GCQ_CUDA(ctx, cudaGetLastError());
+      cudaEventRecord(evs[2 * (sl - s0) + 1], st);
+      k_block_red<<<(unsigned)n_active, 256, 0, st>>>(d->d_blk, d_active, sl, p_s3, p_idx, p_h2, p_M, d->d_M,
+                                                      d->d_hn2, K, d_ctl);
+      GCQ_CUDA(ctx, cudaGetLastError());
+      // 256 threads: thread k < K owns frequency k; the near/singular pivot
+      // entries (warp-cooperative) are spread over all eight warps
+      const int tb = 256;
+      // the function attribute is process-wide state: it is set to the size
+      // of the largest K (256) so that operators with other K compressed
+      // concurrently on other host threads never see a smaller limit
+      const size_t fsm = sizeof(double2) * 9 * (size_t)K, fsm_max = sizeof(double2) * 9 * 256;
+      GCQ_DISPATCH(d->kernel, d->rows,
+                   (cudaFuncSetAttribute(k_fibre_step<R, S, KK, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fsm_max),
+                    k_fibre_step<R, S, KK, RR><<<(unsigned)n_active, tb, fsm, st>>>(
+                        v, d->d_blk, d_active, (S* const*)d->d_face, (S* const*)d->d_fib, nb, sl, d->d_row_perm,
+                        d->d_col_perm, d->d_M, d->d_ks, d->d_used, K, ctx->opt.eps, d_ctl)));
+      GCQ_CUDA(ctx, cudaGetLastError());
+      d->launches += 4;
+      count_launches(4);
     }
-    size_t off = 0;
-    for (int32_t b : active) {
-      const BlkDev& B = d->h_blk[b];
-      d->h_face[(int64_t)slot * nb + b] = chunk + off;
-      off += sizeof(S) * 9 * B.m * B.n;
-    }
-    for (int32_t b : active) {
-      d->h_fib[(int64_t)slot * nb + b] = chunk + off;
-      off += sizeof(S) * 9 * K;
-    }
-    GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_face + (int64_t)slot * nb, d->h_face.data() + (int64_t)slot * nb,
-                                  sizeof(void*) * nb, cudaMemcpyHostToDevice, st));
-    GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_fib + (int64_t)slot * nb, d->h_fib.data() + (int64_t)slot * nb,
-                                  sizeof(void*) * nb, cudaMemcpyHostToDevice, st));
-    GCQ_CUDA(ctx, cudaMemcpyAsync(d->d_blk, d->h_blk.data(), sizeof(BlkDev) * nb, cudaMemcpyHostToDevice, st));
-    GCQ_CUDA(ctx, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, st));
-    GCQ_CUDA(ctx, cudaMemcpyAsync(d_active, active.data(), sizeof(int32_t) * active.size(), cudaMemcpyHostToDevice,
-                                  st));
-    cudaEventRecord(ev0, st);
-    // two face tiles of the TMA double buffer (the same size for every
-    // operator, so the process-wide attribute never changes)
-    const size_t kf_smem = 2 * (size_t)kTile * 9 * sizeof(SC);
-    GCQ_DISPATCH(d->kernel, d->rows,
-                 (cudaFuncSetAttribute(k_face<R, SC, KK, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kf_smem),
-                  k_face<R, SC, KK, RR><<<(unsigned)tiles.size(), kTile, kf_smem, st>>>(
-                     v, d_tiles, d->d_blk, (S* const*)d->d_face, (S* const*)d->d_fib, nb, slot, d->d_row_perm,
-                     d->d_col_perm, p_s3, p_idx, p_h2, p_M, d->d_hn2, K, d_err, debug_face_wait_fail())));
-    GCQ_CUDA(ctx, cudaGetLastError());
-    cudaEventRecord(evf, st);
-    d->face_launches++;
-    d->launches += 3;
-    count_launches(3);
-    for (int32_t b : active)
-      d->face_alg_bytes += (double)(slot + 1) * sizeof(SC) * 9.0 * (double)(d->h_blk[b].m * d->h_blk[b].n);
-    k_block_red<<<(unsigned)active.size(), 256, 0, st>>>(d->d_blk, d_active, slot, p_s3, p_idx, p_h2, p_M, d->d_M,
-                                                         d->d_hn2, K);
-    GCQ_CUDA(ctx, cudaGetLastError());
-    const int tb = std::max(32, ((K + 31) / 32) * 32);
-    // the function attribute is process-wide state: it is set to the size
-    // of the largest K (256) so that operators with other K compressed
-    // concurrently on other host threads never see a smaller limit
-    const size_t fsm = sizeof(double2) * 9 * (size_t)K, fsm_max = sizeof(double2) * 9 * 256;
-    GCQ_DISPATCH(d->kernel, d->rows,
-                 (cudaFuncSetAttribute(k_fibre_step<R, S, KK, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)fsm_max),
-                  k_fibre_step<R, S, KK, RR><<<(unsigned)active.size(), tb, fsm, st>>>(
-                     v, d->d_blk, d_active, (S* const*)d->d_face, (S* const*)d->d_fib, nb, slot, d->d_row_perm,
-                     d->d_col_perm, d->d_M, d->d_ks, d->d_used, K, ctx->opt.eps)));
-    GCQ_CUDA(ctx, cudaGetLastError());
-    cudaEventRecord(ev1, st);
-    GCQ_CUDA(ctx, cudaMemcpyAsync(d->h_blk.data(), d->d_blk, sizeof(BlkDev) * nb, cudaMemcpyDeviceToHost, st));
+    cudaEventRecord(evs[2 * kBatch + 1], st);
+    GCQ_CUDA(ctx, cudaMemcpyAsync(&h_ctl, d_ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, st));
+    GCQ_CUDA(ctx, cudaMemcpyAsync(batch_entries.data(), d_slot_entries + s0, sizeof(int64_t) * (s1 - s0),
+                                  cudaMemcpyDeviceToHost, st));
     GCQ_CUDA(ctx, cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     GCQ_CUDA(ctx, cudaStreamSynchronize(st));
     if (h_err) {
@@ -1243,16 +1419,49 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
       break;
     }
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventElapsedTime(&ms, evs[2 * kBatch], evs[2 * kBatch + 1]);
     t_ent += ms;
-    float fms = 0.f;
-    cudaEventElapsedTime(&fms, ev0, evf);
-    d->t_face_ms += fms;
-    int64_t slot_entries = 0;
-    for (int32_t b : active) slot_entries += d->h_blk[b].m * d->h_blk[b].n;
-    d->entries += slot_entries + (int64_t)K * (int64_t)active.size();
-    d->slot_face_ms.push_back(fms);
-    d->slot_entries.push_back(slot_entries);
+    // the iterations that ran: up to the first that did not fit or found no
+    // active block
+    const int s_end = h_ctl.overflow_slot >= 0 ? (int)h_ctl.overflow_slot : s1;
+    for (int sl = s0; sl < s_end; ++sl) {
+      if (batch_entries[sl - s0] == 0) break;
+      float fms = 0.f;
+      cudaEventElapsedTime(&fms, evs[2 * (sl - s0)], evs[2 * (sl - s0) + 1]);
+      d->t_face_ms += fms;
+      d->slot_face_ms.push_back(fms);
+      d->slot_entries.push_back(batch_entries[sl - s0]);
+      d->face_launches++;
+    }
+    n_active = h_ctl.n_active;
+    n_tiles = h_ctl.n_tiles;
+    if (h_ctl.overflow_slot >= 0) {
+      // iteration overflow_slot did not fit the pool: nothing from it on ran;
+      // it starts again in a new chunk sized from its own need
+      slot = (int)h_ctl.overflow_slot;
+      need = h_ctl.need;
+      n_active = nb;   // not known until it is compacted: the bounds of the batch before
+      n_tiles = n_tiles_all;
+      pool = nullptr;
+      continue;
+    }
+    slot = s1;
+    // the next batch needs at most kBatch times the last iteration's bytes
+    // (the active set only shrinks): a new chunk now if the rest of this one
+    // may not hold them, rather than an overflow and a relaunch
+    const int64_t next = h_ctl.last_bytes * std::min<int64_t>(kBatch, K - slot);
+    if (slot < K && n_active > 0 && pool_cap - h_ctl.pool_used < next) {
+      need = h_ctl.last_bytes;
+      pool = nullptr;
+    }
+  }
+  if (result == BEM_OK) {
+    GCQ_CUDA(ctx, cudaMemcpyAsync(d->h_blk.data(), d->d_blk, sizeof(BlkDev) * nb, cudaMemcpyDeviceToHost, st));
+    GCQ_CUDA(ctx, cudaMemcpyAsync(d->h_face.data(), d->d_face, sizeof(void*) * nb * K, cudaMemcpyDeviceToHost, st));
+    GCQ_CUDA(ctx, cudaMemcpyAsync(d->h_fib.data(), d->d_fib, sizeof(void*) * nb * K, cudaMemcpyDeviceToHost, st));
+    GCQ_CUDA(ctx, cudaStreamSynchronize(st));
+    d->entries += h_ctl.entries;
+    d->face_alg_bytes += h_ctl.face_alg_bytes;
   }
   // dense fallback blocks: all K faces
   if (result == BEM_OK) {

@@ -17,6 +17,53 @@ __device__ __forceinline__ void atomic_add_c(A* p, cx<A> v) {
   atomicAdd(p + 1, v.y);
 }
 
+// Output of one block's contribution to one row (column in the adjoint) and
+// frequency: in FP64 the three components go to the block's own slot of the
+// partial buffer (slot != null), and k_reduce_parts later sums the blocks of
+// each row in block order, so that the result does not depend on the order
+// in which CTAs finish; in MIXED they are added atomically in FP64.
+template <typename A>
+__device__ __forceinline__ void put3(double* y, double2* slot, const cx<A>* v) {
+  if (slot) {
+    for (int a = 0; a < 3; ++a) slot[a] = make_double2((double)v[a].x, (double)v[a].y);
+  } else {
+    for (int a = 0; a < 3; ++a) atomic_add_c<double>(y + 2 * a, cx<double>{(double)v[a].x, (double)v[a].y});
+  }
+}
+
+// slot of row (column) l of block b at frequency k: blocks own consecutive
+// ranges of off[b] .. off[b] + m (n) rows, each with K frequencies
+__device__ __forceinline__ double2* part_slot(double2* part, const int64_t* off, int b, int64_t l, int K, int k) {
+  return part ? part + ((off[b] + l) * K + k) * 3 : nullptr;
+}
+
+// out[pos(R)][k] = sum over the blocks e of R's list, in list order, of
+// part[off[e] + R - first(e)][k]; pos(R) = perm[R] if perm, else R.  The
+// lists hold the contributing blocks of each row (rows = 1) or column
+// (rows = 0) of cluster position R in increasing block order.  Thread per
+// (R, k).
+__global__ void k_reduce_parts(const BlkDev* __restrict__ blk, const int32_t* __restrict__ ptr,
+                               const int32_t* __restrict__ list, const int64_t* __restrict__ off,
+                               const double2* __restrict__ part, double2* __restrict__ out,
+                               const int32_t* __restrict__ perm, int64_t n, int K, int rows) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * K) return;
+  const int64_t R = t / K;
+  const int k = (int)(t - R * K);
+  double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int32_t e = ptr[R]; e < ptr[R + 1]; ++e) {
+    const int b = list[e];
+    const int64_t l = R - (rows ? blk[b].r0 : blk[b].c0);
+    const double2* q = part + ((off[b] + l) * K + k) * 3;
+    for (int a = 0; a < 3; ++a) {
+      acc[a].x += q[a].x;
+      acc[a].y += q[a].y;
+    }
+  }
+  double2* o = out + ((perm ? (int64_t)perm[R] : R) * K + k) * 3;
+  for (int a = 0; a < 3; ++a) o[a] = acc[a];
+}
+
 template <typename S, typename A>
 struct Ld;
 template <>
@@ -40,31 +87,31 @@ template <typename S, typename A>
 __global__ void k_apply_dense(const BlkDev* __restrict__ blk, const int32_t* __restrict__ list,
                               S* const* __restrict__ dense, const int32_t* __restrict__ row_perm,
                               const int32_t* __restrict__ col_perm, const S* __restrict__ X, double* __restrict__ Y,
-                              int K, int64_t n_cols) {
+                              int K, int64_t n_cols, double2* __restrict__ part, const int64_t* __restrict__ poff) {
+  // frequencies k = blockIdx.y, blockIdx.y + gridDim.y, ...: one per CTA
+  // (gridDim.y = K), or all of them in order (gridDim.y = 1, FP64 slots)
   const int b = list[blockIdx.x];
-  const int k = blockIdx.y;
   const BlkDev& B = blk[b];
-  const S* D = dense[b] + (int64_t)k * B.m * B.n * 9;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int64_t li = w; li < B.m; li += nw) {
     cx<A> acc[3] = {{0, 0}, {0, 0}, {0, 0}};
-    for (int64_t lj = lane; lj < B.n; lj += 32) {
-      const S* xp = X + ((int64_t)k * n_cols + col_perm[B.c0 + lj]) * 3;
-      cx<A> x[3];
-      for (int c = 0; c < 3; ++c) x[c] = Ld<S, A>::ld(xp + c);
-      const S* d = D + (li * B.n + lj) * 9;
-      for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) acc[a] = cfma(Ld<S, A>::ld(d + 3 * a + c), x[c], acc[a]);
+    for (int k = blockIdx.y; k < K; k += gridDim.y) {
+      const S* D = dense[b] + (int64_t)k * B.m * B.n * 9;
+      for (int64_t lj = lane; lj < B.n; lj += 32) {
+        const S* xp = X + ((int64_t)k * n_cols + col_perm[B.c0 + lj]) * 3;
+        cx<A> x[3];
+        for (int c = 0; c < 3; ++c) x[c] = Ld<S, A>::ld(xp + c);
+        const S* d = D + (li * B.n + lj) * 9;
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) acc[a] = cfma(Ld<S, A>::ld(d + 3 * a + c), x[c], acc[a]);
+      }
     }
     for (int a = 0; a < 3; ++a)
       for (int o = 16; o > 0; o >>= 1) {
         acc[a].x += __shfl_down_sync(0xffffffffu, acc[a].x, o);
         acc[a].y += __shfl_down_sync(0xffffffffu, acc[a].y, o);
       }
-    if (lane == 0) {
-      double* y = Y + (int64_t)row_perm[B.r0 + li] * 6;
-      for (int a = 0; a < 3; ++a) atomic_add_c<double>(y + 2 * a, cx<double>{(double)acc[a].x, (double)acc[a].y});
-    }
+    if (lane == 0) put3<A>(Y + (int64_t)row_perm[B.r0 + li] * 6, part_slot(part, poff, b, li, 1, 0), acc);
   }
 }
 
@@ -123,7 +170,8 @@ __global__ void k_contract_apply(const BlkDev* __restrict__ blk, const int32_t* 
                                  S* const* __restrict__ face_tab, const int32_t* __restrict__ frank,
                                  const int64_t* __restrict__ toff, const cx<A>* __restrict__ T, int64_t nb,
                                  const int64_t* __restrict__ zoff, const int32_t* __restrict__ row_perm,
-                                 const cx<A>* __restrict__ Z, double* __restrict__ Y) {
+                                 const cx<A>* __restrict__ Z, double* __restrict__ Y, double2* __restrict__ part,
+                                 const int64_t* __restrict__ poff) {
   const int ai = blockIdx.x;
   const int b = list[ai];
   const BlkDev& B = blk[b];
@@ -152,10 +200,7 @@ __global__ void k_contract_apply(const BlkDev* __restrict__ blk, const int32_t* 
         acc[a].x += __shfl_down_sync(0xffffffffu, acc[a].x, o);
         acc[a].y += __shfl_down_sync(0xffffffffu, acc[a].y, o);
       }
-    if (lane == 0) {
-      double* y = Y + (int64_t)row_perm[B.r0 + li] * 6;
-      for (int a = 0; a < 3; ++a) atomic_add_c<double>(y + 2 * a, cx<double>{(double)acc[a].x, (double)acc[a].y});
-    }
+    if (lane == 0) put3<A>(Y + (int64_t)row_perm[B.r0 + li] * 6, part_slot(part, poff, b, li, 1, 0), acc);
   }
 }
 
@@ -245,7 +290,8 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(A) == 4 ? 2 : 1) k_apply
                                                                const int64_t* __restrict__ toff,
                                                                const cx<A>* __restrict__ T, int64_t nb,
                                                                const S* __restrict__ Xp, double* __restrict__ Yp,
-                                                               int K) {
+                                                               int K, double2* __restrict__ part,
+                                                               const int64_t* __restrict__ poff) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<A>* sH = reinterpret_cast<cx<A>*>(smem_raw);       // [kBM][kBN * 9 + 1] (padded rows)
   cx<A>* sZ = sH + kBM * kSHR;                           // [kBN][3][BK]
@@ -311,10 +357,8 @@ __global__ void __launch_bounds__(kApplyThreads, sizeof(A) == 4 ? 2 : 1) k_apply
 #pragma unroll
     for (int t = 0; t < BK / kTPR; ++t) {
       const int kk = kq + kTPR * t;
-      if (kk < nk) {
-        double* y = Yp + (((B.r0 + gi) * K + k0 + kk) * 3) * 2;
-        for (int a = 0; a < 3; ++a) atomic_add_c<double>(y + 2 * a, cx<double>{(double)acc[t][a].x, (double)acc[t][a].y});
-      }
+      if (kk < nk)
+        put3<A>(Yp + (((B.r0 + gi) * K + k0 + kk) * 3) * 2, part_slot(part, poff, it.x, gi, K, k0 + kk), acc[t]);
     }
 }
 
@@ -395,7 +439,8 @@ __global__ void __launch_bounds__(kAN * kATPR) k_apply_faces_adj(const BlkDev* _
                                                                  const int64_t* __restrict__ toff,
                                                                  const cx<A>* __restrict__ T, int64_t nb,
                                                                  const S* __restrict__ Yq, double* __restrict__ Xacc,
-                                                                 int K) {
+                                                                 int K, double2* __restrict__ part,
+                                                                 const int64_t* __restrict__ qoff) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<A>* sH = reinterpret_cast<cx<A>*>(smem_raw);   // [col][row chunk x 9] or [col][rank chunk x 3]
   cx<A>* sY = sH + kAN * kASH;                      // [row x 3 | rank][freq]
@@ -502,10 +547,8 @@ __global__ void __launch_bounds__(kAN * kATPR) k_apply_faces_adj(const BlkDev* _
   if (gj < B.n)
     for (int t = 0; t < NT; ++t) {
       const int kk = kq + kATPR * t;
-      if (kk < nk) {
-        double* x = Xacc + (((B.c0 + gj) * K + k0 + kk) * 3) * 2;
-        for (int a = 0; a < 3; ++a) atomic_add_c<double>(x + 2 * a, cx<double>{(double)xacc[t][a].x, (double)xacc[t][a].y});
-      }
+      if (kk < nk)
+        put3<A>(Xacc + (((B.c0 + gj) * K + k0 + kk) * 3) * 2, part_slot(part, qoff, it.x, gj, K, k0 + kk), xacc[t]);
     }
 }
 
@@ -570,7 +613,7 @@ __global__ void __launch_bounds__(kAN * kATPR) k_apply_lr_t_adj(const BlkDev* __
 template <typename S, typename A>
 __global__ void k_apply_dense_adj(const BlkDev* __restrict__ blk, const int32_t* __restrict__ list,
                                   S* const* __restrict__ dense, const S* __restrict__ Yq, double* __restrict__ Xacc,
-                                  int K) {
+                                  int K, double2* __restrict__ part, const int64_t* __restrict__ qoff) {
   const int b = list[blockIdx.x];
   const int k = blockIdx.y;
   const BlkDev& B = blk[b];
@@ -591,10 +634,7 @@ __global__ void k_apply_dense_adj(const BlkDev* __restrict__ blk, const int32_t*
         acc[c].x += __shfl_down_sync(0xffffffffu, acc[c].x, o);
         acc[c].y += __shfl_down_sync(0xffffffffu, acc[c].y, o);
       }
-    if (lane == 0) {
-      double* x = Xacc + (((B.c0 + lj) * K + k) * 3) * 2;
-      for (int c = 0; c < 3; ++c) atomic_add_c<double>(x + 2 * c, cx<double>{(double)acc[c].x, (double)acc[c].y});
-    }
+    if (lane == 0) put3<A>(Xacc + (((B.c0 + lj) * K + k) * 3) * 2, part_slot(part, qoff, b, lj, K, k), acc);
   }
 }
 
@@ -645,7 +685,7 @@ __global__ void k_from_double(const double2* __restrict__ src, S* __restrict__ d
 template <typename S, typename A>
 __global__ void k_apply_dense_p(const BlkDev* __restrict__ blk, const int32_t* __restrict__ list,
                                 S* const* __restrict__ dense, const S* __restrict__ Xp, double* __restrict__ Yp,
-                                int K) {
+                                int K, double2* __restrict__ part, const int64_t* __restrict__ poff) {
   const int b = list[blockIdx.x];
   const int k = blockIdx.y;
   const BlkDev& B = blk[b];
@@ -666,10 +706,7 @@ __global__ void k_apply_dense_p(const BlkDev* __restrict__ blk, const int32_t* _
         acc[a].x += __shfl_down_sync(0xffffffffu, acc[a].x, o);
         acc[a].y += __shfl_down_sync(0xffffffffu, acc[a].y, o);
       }
-    if (lane == 0) {
-      double* y = Yp + (((B.r0 + li) * K + k) * 3) * 2;
-      for (int a = 0; a < 3; ++a) atomic_add_c<double>(y + 2 * a, cx<double>{(double)acc[a].x, (double)acc[a].y});
-    }
+    if (lane == 0) put3<A>(Yp + (((B.r0 + li) * K + k) * 3) * 2, part_slot(part, poff, b, li, K, k), acc);
   }
 }
 
@@ -710,6 +747,36 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
     }
   }
   std::vector<void*>* own = &d->allocs;
+  // FP64: slots and lists of the fixed-order accumulation
+  std::vector<int64_t> poff(nb, -1), qoff(nb, -1);
+  std::vector<int32_t> rptr, rlist, cptr, clist;
+  int64_t part_rows = 0, part_cols = 0;
+  if (d->prec == BEM_FP64) {
+    auto lists = [&](bool rows, std::vector<int32_t>& ptr, std::vector<int32_t>& list, std::vector<int64_t>& off,
+                     int64_t& total) {
+      const int64_t n = rows ? d->n_rows : d->n_cols;
+      ptr.assign(n + 1, 0);
+      for (int64_t b = 0; b < nb; ++b) {
+        const BlkDev& B = d->h_blk[b];
+        if (!(B.status == ST_DENSE || (B.status == ST_DONE && B.rank > 0))) continue;
+        const int64_t f = rows ? B.r0 : B.c0, len = rows ? B.m : B.n;
+        off[b] = total;
+        total += len;
+        for (int64_t l = 0; l < len; ++l) ptr[f + l + 1]++;
+      }
+      for (int64_t r = 0; r < n; ++r) ptr[r + 1] += ptr[r];
+      list.assign(ptr[n], 0);
+      std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+      for (int64_t b = 0; b < nb; ++b) {
+        if (off[b] < 0) continue;
+        const BlkDev& B = d->h_blk[b];
+        const int64_t f = rows ? B.r0 : B.c0, len = rows ? B.m : B.n;
+        for (int64_t l = 0; l < len; ++l) list[fill[f + l]++] = (int32_t)b;
+      }
+    };
+    lists(true, rptr, rlist, poff, part_rows);
+    lists(false, cptr, clist, qoff, part_cols);
+  }
   for (int v = 0; v < 3; ++v) {
     d->n_apply_items_v[v] = (int64_t)items_v[v].size();
     d->n_lr_items_v[v] = (int64_t)lr_items_v[v].size();
@@ -737,6 +804,15 @@ bem_status build_apply_lists(bem_ctx* ctx, OpData* d) {
       GCQ_CUDA(ctx, up((int4**)&d->d_tc_items_v[v], tci));
     }
     d->apply_kernel = 1;
+  }
+  if (d->prec == BEM_FP64) {
+    GCQ_CUDA(ctx, up(&d->d_poff, poff));
+    GCQ_CUDA(ctx, up(&d->d_qoff, qoff));
+    GCQ_CUDA(ctx, up(&d->d_rptr, rptr));
+    GCQ_CUDA(ctx, up(&d->d_rlist, rlist));
+    GCQ_CUDA(ctx, up(&d->d_cptr, cptr));
+    GCQ_CUDA(ctx, up(&d->d_clist, clist));
+    GCQ_CUDA(ctx, dmalloc(&d->d_part, sizeof(double2) * 3 * (size_t)d->K * std::max<int64_t>(1, std::max(part_rows, part_cols)), own));
   }
   GCQ_CUDA(ctx, dmalloc(&d->d_apply_err, sizeof(int), own));
   GCQ_CUDA(ctx, cudaMemset(d->d_apply_err, 0, sizeof(int)));
@@ -802,10 +878,24 @@ static bem_status apply_faces_bk(bem_ctx* ctx, OpData* d, int v, cudaStream_t st
     cudaFuncSetAttribute(k_apply_faces<S, A, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_apply_faces<S, A, BK><<<(unsigned)d->n_apply_items_v[v], kApplyThreads, smem, st>>>(
         d->d_blk, (const int4*)d->d_apply_items_v[v], (S* const*)d->d_face, (S* const*)d->d_fib, d->d_frank,
-        d->d_toff, (const cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_xp, (double*)d->d_yp, d->K);
+        d->d_toff, (const cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_xp, (double*)d->d_yp, d->K, d->d_part,
+        d->d_poff);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
   }
+  return BEM_OK;
+}
+
+// FP64: out = the per-block slots summed in block order (k_reduce_parts)
+static bem_status reduce_parts(bem_ctx* ctx, OpData* d, bool rows, int K, double2* out, const int32_t* perm,
+                               cudaStream_t st) {
+  const int64_t n = rows ? d->n_rows : d->n_cols, nt = n * K;
+  k_reduce_parts<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(d->d_blk, rows ? d->d_rptr : d->d_cptr,
+                                                               rows ? d->d_rlist : d->d_clist,
+                                                               rows ? d->d_poff : d->d_qoff, d->d_part, out, perm, n,
+                                                               K, rows ? 1 : 0);
+  GCQ_CUDA(ctx, cudaGetLastError());
+  count_launches(1);
   return BEM_OK;
 }
 
@@ -820,7 +910,8 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
     k_perm_x<S><<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(X, (S*)d->d_xp, d->d_col_perm, d->n_cols, d->K);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
-    GCQ_CUDA(ctx, cudaMemsetAsync(d->d_yp, 0, sizeof(double2) * 3 * nyp, st));
+    const bool det = d->d_part != nullptr;   // FP64: per-block slots, fixed-order sum
+    if (!det) GCQ_CUDA(ctx, cudaMemsetAsync(d->d_yp, 0, sizeof(double2) * 3 * nyp, st));
     bem_status rs = BEM_OK;
     switch (d->apply_bk) {
       case 16: rs = apply_faces_bk<S, A, 16>(ctx, d, 0, st); break;
@@ -831,9 +922,13 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
     if (d->n_dense > 0) {
       dim3 g((unsigned)d->n_dense, (unsigned)d->K);
       k_apply_dense_p<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense,
-                                               (const S*)d->d_xp, (double*)d->d_yp, d->K);
+                                               (const S*)d->d_xp, (double*)d->d_yp, d->K, d->d_part, d->d_poff);
       GCQ_CUDA(ctx, cudaGetLastError());
       count_launches(1);
+    }
+    if (det) {
+      rs = reduce_parts(ctx, d, true, d->K, (double2*)d->d_yp, nullptr, st);
+      if (rs != BEM_OK) return rs;
     }
     k_unperm_y<S><<<(unsigned)((nyp + 255) / 256), 256, 0, st>>>((const double2*)d->d_yp, Y, d->d_row_perm,
                                                                  d->n_rows, d->K);
@@ -843,7 +938,8 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
   }
   // contracted: accumulated in FP64 (d_yp, original row order), then converted
   double* yc = (double*)d->d_yp;
-  GCQ_CUDA(ctx, cudaMemsetAsync(yc, 0, sizeof(double2) * 3 * d->n_rows, st));
+  const bool det = d->d_part != nullptr;
+  if (!det) GCQ_CUDA(ctx, cudaMemsetAsync(yc, 0, sizeof(double2) * 3 * d->n_rows, st));
   if (d->n_zitems > 0) {
     k_contract_z<S, A><<<(unsigned)d->n_zitems, 128, 0, st>>>(d->d_blk, (const int4*)d->d_zitems,
                                                               (S* const*)d->d_fib, d->n_blocks, d->d_zoff,
@@ -860,16 +956,20 @@ static bem_status apply_t(bem_op* op, int mode, const void* Xv, void* Yv, cudaSt
     dim3 g((unsigned)d->n_aca, 8);
     k_contract_apply<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_aca_list, (S* const*)d->d_face, d->d_frank,
                                               d->d_toff, (const cx<A>*)d->d_t, d->n_blocks, d->d_zoff,
-                                              d->d_row_perm, (const cx<A>*)d->d_z, yc);
+                                              d->d_row_perm, (const cx<A>*)d->d_z, yc, d->d_part, d->d_poff);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
   }
   if (d->n_dense > 0) {
-    dim3 g((unsigned)d->n_dense, (unsigned)d->K);
+    dim3 g((unsigned)d->n_dense, det ? 1u : (unsigned)d->K);
     k_apply_dense<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense, d->d_row_perm,
-                                           d->d_col_perm, X, yc, d->K, d->n_cols);
+                                           d->d_col_perm, X, yc, d->K, d->n_cols, d->d_part, d->d_poff);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
+  }
+  if (det) {
+    bem_status rs = reduce_parts(ctx, d, true, 1, (double2*)yc, d->d_row_perm, st);
+    if (rs != BEM_OK) return rs;
   }
   const int64_t ny = 3 * d->n_rows;
   k_from_double<S><<<(unsigned)((ny + 255) / 256), 256, 0, st>>>((const double2*)yc, Y, ny);
@@ -894,7 +994,8 @@ static bem_status apply_adj_t(bem_op* op, int mode, const void* Yv, void* Xv, cu
     k_bcast_y<S><<<(unsigned)((nyq + 255) / 256), 256, 0, st>>>(Yin, (S*)d->d_yq, d->d_row_perm, d->n_rows, d->K);
   GCQ_CUDA(ctx, cudaGetLastError());
   count_launches(1);
-  GCQ_CUDA(ctx, cudaMemsetAsync(d->d_xacc, 0, sizeof(double2) * 3 * nxa, st));
+  const bool det = d->d_part != nullptr;
+  if (!det) GCQ_CUDA(ctx, cudaMemsetAsync(d->d_xacc, 0, sizeof(double2) * 3 * nxa, st));
   if (d->n_adj_lr_items > 0) {
     const size_t sm = sizeof(cx<A>) * (kAN * kASH + kAR * 3 * kAK);
     cudaFuncSetAttribute(k_apply_lr_t_adj<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -909,16 +1010,20 @@ static bem_status apply_adj_t(bem_op* op, int mode, const void* Yv, void* Xv, cu
     cudaFuncSetAttribute(k_apply_faces_adj<S, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_apply_faces_adj<S, A><<<(unsigned)d->n_adj_items, kAN * kATPR, sm, st>>>(
         d->d_blk, (const int4*)d->d_adj_items, (S* const*)d->d_face, (S* const*)d->d_fib, d->d_frank, d->d_toff,
-        (const cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_yq, (double*)d->d_xacc, d->K);
+        (const cx<A>*)d->d_t, d->n_blocks, (const S*)d->d_yq, (double*)d->d_xacc, d->K, d->d_part, d->d_qoff);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
   }
   if (d->n_dense > 0) {
     dim3 g((unsigned)d->n_dense, (unsigned)d->K);
     k_apply_dense_adj<S, A><<<g, 128, 0, st>>>(d->d_blk, d->d_dense_list, (S* const*)d->d_dense,
-                                               (const S*)d->d_yq, (double*)d->d_xacc, d->K);
+                                               (const S*)d->d_yq, (double*)d->d_xacc, d->K, d->d_part, d->d_qoff);
     GCQ_CUDA(ctx, cudaGetLastError());
     count_launches(1);
+  }
+  if (det) {
+    bem_status rs = reduce_parts(ctx, d, false, d->K, (double2*)d->d_xacc, nullptr, st);
+    if (rs != BEM_OK) return rs;
   }
   k_unperm_y<S><<<(unsigned)((nxa + 255) / 256), 256, 0, st>>>((const double2*)d->d_xacc, Xout, d->d_col_perm,
                                                                d->n_cols, d->K);

@@ -400,6 +400,7 @@ namespace gcq {}  // aca3d.cuh and apply.cuh reopen the namespace
 #include "aca3d.cuh"
 #include "apply.cuh"
 #include "solve.cuh"
+#include "receiver.cuh"
 #include "persist.cuh"
 
 extern "C" int64_t bem_kernel_launches(void) { return gcq::g_launches.load(); }

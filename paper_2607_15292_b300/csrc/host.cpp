@@ -2,6 +2,7 @@
 // PCA cluster trees and the block cluster tree (Sec. 3.1).
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <atomic>
 #include <mutex>
@@ -900,7 +901,22 @@ bem_status bem_op_solve(bem_op* op, const void* B, void* X, double tol, int32_t 
   if (((uintptr_t)B & 15) || ((uintptr_t)X & 15))
     return set_err(ctx, BEM_ERR_ARG, "bem_op_solve: B and X must be 16-byte aligned");
   GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
-  return solve(op, B, X, tol, max_iter, iters, relres, (cudaStream_t)stream);
+  return solve(op, 0, B, X, tol, max_iter, iters, relres, (cudaStream_t)stream);
+}
+
+bem_status bem_op_solve_adjoint(bem_op* op, const void* B, void* X, double tol, int32_t max_iter, int32_t* iters,
+                                double* relres, void* stream) {
+  gcq::NvtxRange nvtx("bem_op_solve_adjoint");
+  if (!op) return BEM_ERR_ARG;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  if (!B || !X || !iters || !relres || !(tol > 0 && tol < 1) || max_iter < 1 || B == X)
+    return set_err(ctx, BEM_ERR_ARG, "bem_op_solve_adjoint: bad arguments");
+  if (op->tree->n_rows != op->tree->n_cols)
+    return set_err(ctx, BEM_ERR_ARG, "bem_op_solve_adjoint: the operator is not square (rows != columns)");
+  if (((uintptr_t)B & 15) || ((uintptr_t)X & 15))
+    return set_err(ctx, BEM_ERR_ARG, "bem_op_solve_adjoint: B and X must be 16-byte aligned");
+  GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
+  return solve(op, 1, B, X, tol, max_iter, iters, relres, (cudaStream_t)stream);
 }
 
 bem_status bem_op_inner(bem_op* op, int32_t mode, const void* G, const void* X, double* out, void* stream) {
@@ -974,6 +990,50 @@ bem_status bem_op_slot_stats(const bem_op* op, int32_t cap, double* face_ms, int
     entries[s] = d->slot_entries[s];
   }
   return BEM_OK;
+}
+
+bem_status bem_receiver_energy_grad(bem_op* V, bem_op* A, bem_op* const* dV, bem_op* const* dA, int32_t n_speeds,
+                                    int32_t N, double dt, const double* g, const int32_t* rec, int64_t n_rec,
+                                    double tol, int32_t max_iter, double* J, double* dJ_dg, double* dJ_dc,
+                                    int32_t* iters, void* stream) {
+  gcq::NvtxRange nvtx("bem_receiver_energy_grad");
+  if (!V || !A) return BEM_ERR_ARG;
+  bem_ctx* ctx = V->tree->mesh->ctx;
+  const char* fn = "bem_receiver_energy_grad: ";
+  auto bad = [&](const char* why) { return set_err(ctx, BEM_ERR_ARG, std::string(fn) + why); };
+  if (A->tree->mesh != V->tree->mesh) return bad("V and A must be operators of one mesh");
+  if (V->tree->kernel != BEM_SL || A->tree->kernel != BEM_DL || V->tree->rows != BEM_ROWS_NODES ||
+      A->tree->rows != BEM_ROWS_NODES)
+    return bad("V must be the single layer and A the double layer, both with node rows");
+  if (!g || !rec || !J || !iters || n_rec < 1 || !(dt > 0) || N < 1 || !(tol > 0 && tol < 1) || max_iter < 1 ||
+      n_speeds < 0 || n_speeds > 2 || (n_speeds > 0 && (!dV || !dA || !dJ_dc)))
+    return bad("bad arguments");
+  if (((uintptr_t)g & 7) || (dJ_dg && ((uintptr_t)dJ_dg & 7))) return bad("g and dJ_dg must be 8-byte aligned");
+  const int kinds_v[2] = {BEM_SL_DCP, BEM_SL_DCS}, kinds_a[2] = {BEM_DL_DCP, BEM_DL_DCS};
+  for (int a = 0; a < n_speeds; ++a) {
+    if (!dV[a] || !dA[a] || dV[a]->tree->mesh != V->tree->mesh || dA[a]->tree->mesh != V->tree->mesh ||
+        dV[a]->tree->kernel != kinds_v[a] || dA[a]->tree->kernel != kinds_a[a] ||
+        dV[a]->tree->rows != BEM_ROWS_NODES || dA[a]->tree->rows != BEM_ROWS_NODES)
+      return bad("dV[a], dA[a] must be the c_p (a = 0) and c_s (a = 1) derivative operators of V and A");
+  }
+  // the context's frequencies must be the half set of BDF2 CQ with N, dt
+  const int L = N + 1, Kh = L / 2 + 1;
+  if (ctx->K != Kh) return bad("the context must hold the floor((N + 1) / 2) + 1 frequencies of the half set");
+  const double lam = std::pow(1e-10, 1.0 / (2.0 * N));
+  for (int k = 0; k < Kh; ++k) {
+    const std::complex<double> z = lam * std::exp(std::complex<double>(0.0, -2.0 * M_PI * k / L));
+    const std::complex<double> sk = ((1.0 - z) + 0.5 * (1.0 - z) * (1.0 - z)) / dt;
+    const std::complex<double> have(ctx->s[2 * k], ctx->s[2 * k + 1]);
+    if (std::abs(have - sk) > 1e-9 * std::abs(sk)) return bad("the context's frequencies are not BDF2 CQ with N, dt");
+  }
+  const int64_t nn = A->tree->n_rows;
+  std::vector<int32_t> sorted(rec, rec + n_rec);
+  std::sort(sorted.begin(), sorted.end());
+  if (sorted.front() < 0 || sorted.back() >= nn) return bad("receiver index out of range");
+  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return bad("receivers must be distinct");
+  GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
+  return receiver_energy_grad(V, A, dV, dA, n_speeds, N, dt, g, rec, n_rec, tol, max_iter, J, dJ_dg, dJ_dc, iters,
+                              (cudaStream_t)stream);
 }
 
 bem_status bem_cq_forward(int32_t N, int64_t nvec, const void* in, void* out, void* stream) {

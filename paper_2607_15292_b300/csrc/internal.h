@@ -5,6 +5,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
+#include <mutex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -179,8 +180,8 @@ bem_status op_dense(bem_op* op, void* out, cudaStream_t st);
 bem_status op_stats(const bem_op* op, bem_op_stats* st);
 bem_status op_blocks(const bem_op* op, int64_t* info);
 bem_status op_face_ranks(const bem_op* op, int32_t* ranks);
-bem_status solve(bem_op* op, const void* B, void* X, double tol, int max_iter, int32_t* iters, double* relres,
-                 cudaStream_t st);
+bem_status solve(bem_op* op, int transpose, const void* B, void* X, double tol, int max_iter, int32_t* iters,
+                 double* relres, cudaStream_t st);
 bem_status inner(bem_op* op, int mode, const void* G, const void* X, double* out, cudaStream_t st);
 bem_status autotune(bem_op* op, cudaStream_t st, int32_t* bk);
 bem_status op_save(const bem_op* op, const char* path);
@@ -190,5 +191,8 @@ bem_status set_apply_kernel(bem_op* op, int32_t kind);
 bem_status face_compress(bem_ctx* ctx, const void* H, int64_t m, int64_t n, double eps, int32_t* rank, void* out,
                          cudaStream_t st);
 bem_status cq_transform(int N, int64_t nvec, const void* in, void* out, bool inverse, cudaStream_t st);
+bem_status receiver_energy_grad(bem_op* V, bem_op* A, bem_op* const* dV, bem_op* const* dA, int ns, int N, double dt,
+                                const double* g, const int32_t* rec, int64_t n_rec, double tol, int max_iter,
+                                double* J, double* dJ_dg, double* dJ_dc, int32_t* iters, cudaStream_t st);
 
 }  // namespace gcq

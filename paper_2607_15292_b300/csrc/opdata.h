@@ -103,6 +103,14 @@ struct OpData {
   // (0 SIMT, 1 tensor cores); error word of its bounded waits
   int32_t* d_tc_items_v[3] = {nullptr, nullptr, nullptr};
   int64_t n_tc_items_v[3] = {0, 0, 0};
+  // FP64: fixed-order accumulation of the apply.  Every contributing block
+  // (dense, or 3D-ACA with rank > 0) owns slots for its rows (poff) and
+  // columns (qoff) in d_part; the row and column lists (CSR over cluster
+  // positions, blocks in increasing order) drive k_reduce_parts
+  double2* d_part = nullptr;
+  int64_t* d_poff = nullptr;
+  int64_t* d_qoff = nullptr;
+  int32_t *d_rptr = nullptr, *d_rlist = nullptr, *d_cptr = nullptr, *d_clist = nullptr;
   int32_t apply_kernel = 0;
   int* d_apply_err = nullptr;
   double apply_tensor_flops = 0;     // TF32 flops of one tensor-core batched apply

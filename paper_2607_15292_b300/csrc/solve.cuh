@@ -1,4 +1,5 @@
-// K independent linear systems, one per frequency: C(s_k) x_k = b_k, solved
+// K independent linear systems, one per frequency: C(s_k) x_k = b_k (or, for
+// the adjoint method, C(s_k)^H x_k = b_k on the conjugate-transpose apply), solved
 // together by BiCGstab without preconditioner (the solver of Sec. 5) on the
 // batched apply of the compressed operator.  Every iteration applies C to
 // all K vectors at once (two batched applies), forms the per-frequency inner
@@ -9,9 +10,11 @@
 
 namespace gcq {
 
-// out[k] += sum_e conj(a[k][e]) b[k][e] over the n complex values of vector k
+// part[k][blockIdx.x] = this CTA's share of sum_e conj(a[k][e]) b[k][e] over
+// the n complex values of vector k; k_bdot_fin adds the shares in CTA order
+// (no atomics: the same inputs give the same bits)
 template <typename S>
-__global__ void k_bdot(const S* __restrict__ a, const S* __restrict__ b, int64_t n, double2* __restrict__ out) {
+__global__ void k_bdot(const S* __restrict__ a, const S* __restrict__ b, int64_t n, double2* __restrict__ part) {
   const int k = blockIdx.y;
   const S* ak = a + (int64_t)k * n;
   const S* bk = b + (int64_t)k * n;
@@ -38,9 +41,20 @@ __global__ void k_bdot(const S* __restrict__ a, const S* __restrict__ b, int64_t
       tr += sr[q];
       ti += si[q];
     }
-    atomicAdd(&out[k].x, tr);
-    atomicAdd(&out[k].y, ti);
+    part[(int64_t)k * gridDim.x + blockIdx.x] = make_double2(tr, ti);
   }
+}
+
+// out[k] = sum over c < nc of part[k][c], in order; thread per k
+__global__ void k_bdot_fin(const double2* __restrict__ part, int nc, int K, double2* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double2 acc = {0.0, 0.0};
+  for (int c = 0; c < nc; ++c) {
+    acc.x += part[(int64_t)k * nc + c].x;
+    acc.y += part[(int64_t)k * nc + c].y;
+  }
+  out[k] = acc;
 }
 
 // y[k] = c[k][0] u[k] + c[k][1] v[k] + c[k][2] w[k] (elementwise; y may alias u, v or w)
@@ -57,8 +71,8 @@ __global__ void k_lin3(S* y, const S* u, const S* v, const S* w, const double2* 
 }
 
 template <typename S>
-static bem_status solve_t(bem_op* op, const void* Bv, void* Xv, double tol, int max_iter, int32_t* iters,
-                          double* relres, cudaStream_t st) {
+static bem_status solve_t(bem_op* op, int transpose, const void* Bv, void* Xv, double tol, int max_iter,
+                          int32_t* iters, double* relres, cudaStream_t st) {
   OpData* d = op->d;
   bem_ctx* ctx = op->tree->mesh->ctx;
   const int K = d->K;
@@ -68,7 +82,10 @@ static bem_status solve_t(bem_op* op, const void* Bv, void* Xv, double tol, int 
   double2* dots = nullptr;
   double2* coef = nullptr;
   GCQ_CUDA(ctx, cudaMalloc(&buf, 6 * vb));
-  if (cudaMalloc(&dots, sizeof(double2) * K) != cudaSuccess || cudaMalloc(&coef, sizeof(double2) * 3 * K) != cudaSuccess) {
+  const dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)K);
+  // dots: K results, then the K x grid.x CTA shares
+  if (cudaMalloc(&dots, sizeof(double2) * K * (1 + grid.x)) != cudaSuccess ||
+      cudaMalloc(&coef, sizeof(double2) * 3 * K) != cudaSuccess) {
     cudaFree(buf);
     cudaFree(dots);
     return set_err(ctx, BEM_ERR_OOM, "bem_op_solve: out of device memory");
@@ -77,7 +94,6 @@ static bem_status solve_t(bem_op* op, const void* Bv, void* Xv, double tol, int 
   const S* b = (const S*)Bv;
   S *r = buf, *rh = buf + n * K, *p = buf + 2 * n * K, *v = buf + 3 * n * K, *s = buf + 4 * n * K,
     *t = buf + 5 * n * K;
-  const dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)K);
   std::vector<double2> hd(K), hc(3 * K);
   using C = std::complex<double>;
   std::vector<C> rho(K, 1.0), alpha(K, 1.0), omega(K, 1.0), rho_new(K);
@@ -86,11 +102,11 @@ static bem_status solve_t(bem_op* op, const void* Bv, void* Xv, double tol, int 
   cudaError_t e = cudaSuccess;
   bem_status res = BEM_OK;
   auto dot = [&](const S* a, const S* c) -> cudaError_t {
-    cudaError_t q = cudaMemsetAsync(dots, 0, sizeof(double2) * K, st);
+    k_bdot<S><<<grid, 256, 0, st>>>(a, c, n, dots + K);
+    k_bdot_fin<<<(K + 127) / 128, 128, 0, st>>>(dots + K, (int)grid.x, K, dots);
+    count_launches(2);
+    cudaError_t q = cudaGetLastError();
     if (q != cudaSuccess) return q;
-    k_bdot<S><<<grid, 256, 0, st>>>(a, c, n, dots);
-    count_launches(1);
-    if ((q = cudaGetLastError()) != cudaSuccess) return q;
     q = cudaMemcpyAsync(hd.data(), dots, sizeof(double2) * K, cudaMemcpyDeviceToHost, st);
     if (q != cudaSuccess) return q;
     return cudaStreamSynchronize(st);
@@ -142,7 +158,7 @@ static bem_status solve_t(bem_op* op, const void* Bv, void* Xv, double tol, int 
       setc(k, one, beta, zero - beta * omega[k]);   // p = r + beta (p - omega v)
     }
     if ((e = lin3(p, r, p, v)) != cudaSuccess) break;
-    if ((res = apply(op, BEM_APPLY_BATCHED, 0, p, v, st)) != BEM_OK) break;
+    if ((res = apply(op, BEM_APPLY_BATCHED, transpose, p, v, st)) != BEM_OK) break;
     if ((e = dot(rh, v)) != cudaSuccess) break;
     for (int k = 0; k < K; ++k) {
       const C rv(hd[k].x, hd[k].y);
@@ -155,7 +171,7 @@ static bem_status solve_t(bem_op* op, const void* Bv, void* Xv, double tol, int 
     std::vector<int> early(K, 0);
     for (int k = 0; k < K; ++k)
       if (!done[k] && std::sqrt(std::max(hd[k].x, 0.0)) <= tol * bn[k]) early[k] = 1;
-    if ((res = apply(op, BEM_APPLY_BATCHED, 0, s, t, st)) != BEM_OK) break;
+    if ((res = apply(op, BEM_APPLY_BATCHED, transpose, s, t, st)) != BEM_OK) break;
     if ((e = dot(t, s)) != cudaSuccess) break;
     std::vector<C> ts(K);
     for (int k = 0; k < K; ++k) ts[k] = C(hd[k].x, hd[k].y);
@@ -205,7 +221,8 @@ static bem_status inner_t(bem_op* op, int mode, const void* G, const void* X, do
   S* Y = nullptr;
   double2* dot = nullptr;
   GCQ_CUDA(ctx, cudaMalloc(&Y, sizeof(S) * (size_t)n));
-  if (cudaMalloc(&dot, sizeof(double2)) != cudaSuccess) {
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1184));
+  if (cudaMalloc(&dot, sizeof(double2) * (1 + gx)) != cudaSuccess) {   // result, then the CTA shares
     cudaFree(Y);
     return set_err(ctx, BEM_ERR_OOM, "bem_op_inner: out of device memory");
   }
@@ -213,13 +230,10 @@ static bem_status inner_t(bem_op* op, int mode, const void* G, const void* X, do
   cudaError_t e = cudaSuccess;
   double2 h = {0.0, 0.0};
   if (res == BEM_OK) {
-    e = cudaMemsetAsync(dot, 0, sizeof(double2), st);
-    if (e == cudaSuccess) {
-      const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1184));
-      k_bdot<S><<<dim3(gx, 1), 256, 0, st>>>((const S*)G, Y, n, dot);
-      count_launches(1);
-      e = cudaGetLastError();
-    }
+    k_bdot<S><<<dim3(gx, 1), 256, 0, st>>>((const S*)G, Y, n, dot + 1);
+    k_bdot_fin<<<1, 32, 0, st>>>(dot + 1, (int)gx, 1, dot);
+    count_launches(2);
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dot, sizeof(double2), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
@@ -237,10 +251,10 @@ bem_status inner(bem_op* op, int mode, const void* G, const void* X, double* out
                                  : inner_t<float2>(op, mode, G, X, out, st);
 }
 
-bem_status solve(bem_op* op, const void* B, void* X, double tol, int max_iter, int32_t* iters, double* relres,
-                 cudaStream_t st) {
-  return op->d->prec == BEM_FP64 ? solve_t<double2>(op, B, X, tol, max_iter, iters, relres, st)
-                                 : solve_t<float2>(op, B, X, tol, max_iter, iters, relres, st);
+bem_status solve(bem_op* op, int transpose, const void* B, void* X, double tol, int max_iter, int32_t* iters,
+                 double* relres, cudaStream_t st) {
+  return op->d->prec == BEM_FP64 ? solve_t<double2>(op, transpose, B, X, tol, max_iter, iters, relres, st)
+                                 : solve_t<float2>(op, transpose, B, X, tol, max_iter, iters, relres, st);
 }
 
 }  // namespace gcq

@@ -353,11 +353,11 @@ def box_receivers(xyz: np.ndarray, n: int, seed: int = 7) -> np.ndarray:
 
 
 def box_traction(xyz: np.ndarray, tri: np.ndarray, N: int, dt: float, width: float, t0: float, tw: float,
-                 seed: int = 11) -> np.ndarray:
-    """Traction samples g (N + 1, n_tris, 3), real: on the top-face
-    elements (centroid z = max z) a downward load exp(-|c - p|^2 / (2 w^2))
-    exp(-(t_n - t0)^2 / (2 tw^2)), p a seeded point of the top face; zero
-    elsewhere."""
+                 seed: int = 11, amp: float = 1e6) -> np.ndarray:
+    """Traction samples g (N + 1, n_tris, 3) in Pa, real: on the top-face
+    elements (centroid z = max z) a downward load
+    amp exp(-|c - p|^2 / (2 w^2)) exp(-(t_n - t0)^2 / (2 tw^2)), p a seeded
+    point of the top face; zero elsewhere."""
     c = xyz[tri].mean(axis=1)
     zt = xyz[:, 2].max()
     top = np.abs(c[:, 2] - zt) <= 1e-9 * max(1.0, float(np.abs(xyz).max()))
@@ -368,7 +368,7 @@ def box_traction(xyz: np.ndarray, tri: np.ndarray, N: int, dt: float, width: flo
     t = dt * np.arange(N + 1)
     time = np.exp(-((t - t0) ** 2) / (2.0 * tw ** 2))
     g = np.zeros((N + 1, len(tri), 3))
-    g[:, :, 2] = -time[:, None] * space[None, :]
+    g[:, :, 2] = -amp * time[:, None] * space[None, :]
     return g
 
 
