@@ -33,11 +33,14 @@ WORKLOAD = dict(workload="sphere-5120-K64", mesh="icosphere level 4, radius 1 m,
                 material="steel rho=7850 E=210GPa nu=0.3", N=64, dt=2e-5, K=64, leaf=32, eta=2.0, eps=1e-6,
                 rows="nodes (Neumann)", operators="V (SL) + C+K (DL)")
 METRIC = "3D-ACA tensor entries/s"
-# k_face DRAM traffic / algorithmic bytes, measured with ncu on the
-# icosphere-3 single layer (all face launches of one compression); None
-# until the counters are taken on the current kernel (one pass over the
-# previous faces per iteration)
-FACE_TRAFFIC_RATIO = None
+# k_face DRAM traffic / algorithmic bytes of one launch at this workload's
+# size (ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass, launch
+# 11 = iteration 10 of the single layer), None until the counters are taken
+# on the current kernel
+FACE_TRAFFIC_RATIO = 37.38e9 / (11 * 144 * 13117440)
+FACE_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one bench-size launch (iteration 10 of "
+                       "the single layer: 31.91 + 5.47 GB in 16.75 ms against 20.78 GB algorithmic, ratio 1.80), "
+                       "times each launch's algorithmic bytes")
 UNIT = "block entries/s"
 
 
@@ -158,10 +161,10 @@ def run_reference(args):
 # small case for profiler captures (not a bench line)
 # ---------------------------------------------------------------------------
 
-def run_small():
+def run_small(level=3):
     import torch
     import paper_2607_15292_b300 as g
-    xyz, tri = syn.icosphere(3)
+    xyz, tri = syn.icosphere(level)
     s = g.freqs_bdf2(WORKLOAD["N"], WORKLOAD["dt"], WORKLOAD["K"])
     ctx = g.Context(eps=WORKLOAD["eps"], leaf=WORKLOAD["leaf"], eta=WORKLOAD["eta"], precision=g.BEM_MIXED)
     ctx.material(*syn.STEEL)
@@ -173,7 +176,7 @@ def run_small():
     op.apply(X, Y)
     torch.cuda.synchronize()
     st = op.stats()
-    print(json.dumps({"case": "icosphere-3 single layer, node rows, K=64, MIXED", "face_launches": st.face_launches,
+    print(json.dumps({"case": f"icosphere-{level} single layer, node rows, K=64, MIXED", "face_launches": st.face_launches,
                       "face_alg_bytes": st.face_alg_bytes, "t_face_ms": st.t_face_ms,
                       "t_compress_ms": st.t_compress_ms, "apply_bytes": st.apply_bytes}))
 
@@ -316,6 +319,8 @@ def main():
     ap.add_argument("--small", action="store_true",
                     help="one MIXED compression and batched apply of the icosphere-3 single layer "
                          "(1,280 triangles, K = 64), for profiler captures; prints its statistics")
+    ap.add_argument("--small-level", type=int, default=3, metavar="L",
+                    help="icosphere level of --small (4: the bench mesh, for a bench-size capture of one kernel)")
     ap.add_argument("--batch", type=int, default=0, metavar="COUNT",
                     help="multi-mesh workload: compress the first COUNT meshes one by one and from one "
                          "work list; prints both rates (not the bench line)")
@@ -328,7 +333,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.small:
-        return run_small()
+        return run_small(args.small_level)
     if args.batch:
         return run_batch(args.batch, args.batch_nmax, args.batch_streams)
     if args.adjoint > 0:
@@ -583,15 +588,14 @@ def main():
     hbm = peaks.get("hbm_gbs") or 6400.0
     face_gbs = face["bytes"] / (face["ms"] / 1e3) / 1e9 if face["ms"] > 0 else None
     alg_per_launch = face["bytes"] / max(1, face["launches"])
-    roofline = {"kernel": "k_face (3D-ACA face: entries + residual + Gram in one pass), MIXED",
+    roofline = {"kernel": "k_face (3D-ACA face: FP32 entries, float-float residual pass and FP32 Gram pass over the "
+                          "TMA-staged previous faces), MIXED",
                 "bound": "hbm", "achieved": face_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": (face_gbs / hbm) if face_gbs else None,
                 # DRAM read + write per launch: the ratio to the algorithmic bytes
-                # measured by ncu on all face launches of the icosphere-3 case
-                # (`python bench.py --small`), times this workload's bytes per launch
+                # of one bench-size launch (ncu), times the bytes per launch
                 "traffic": FACE_TRAFFIC_RATIO * alg_per_launch if FACE_TRAFFIC_RATIO else None,
-                "traffic_source": ("ncu dram__bytes_read+write, icosphere-3 (bench.py --small), ratio "
-                                   f"{FACE_TRAFFIC_RATIO} to algorithmic bytes, scaled") if FACE_TRAFFIC_RATIO
+                "traffic_source": FACE_TRAFFIC_SOURCE if FACE_TRAFFIC_RATIO
                 else "not yet captured for this kernel version",
                 "launches": face["launches"],
                 "avg_launch_ms": face["ms"] / max(1, face["launches"]),

@@ -354,10 +354,7 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   // entry evaluation.
   extern __shared__ __align__(128) unsigned char kf_dyn[];   // 2 x kTile x 9 S
   __shared__ __align__(8) uint64_t kf_bar[2];
-  // f_p[k_d] for p < slot in chunks of 64 (residual pass), the staging of
-  // the new face and the Gram partials of the warps (Gram pass): one buffer
-  __shared__ __align__(16) unsigned char kf_u[64 * 9 * sizeof(S) + kTile / 32 * 16 * 18 * sizeof(W)];
-  S* const sf = reinterpret_cast<S*>(kf_u);
+  __shared__ S sf[64 * 9];     // f_p[k_d] for p < slot, in chunks of 64
   __shared__ unsigned char ssmall[64];   // term p below 2^-10 of the first: plain FMA (MIXED)
   __shared__ double shv[32 * 18];
   __shared__ int64_t shi[32];
@@ -538,45 +535,25 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   }
   S* Hd = face_tab[(int64_t)slot * nb + t.blk];
   cx<W> H[9];   // working copy for the pivot criterion and the Gram
-  // the stored face entry c of this thread (MIXED: the small terms folded
-  // in, (h, l) renormalised)
-  auto face_val = [&](int c) -> float4 {
-    const float rh = fh[2 * c] + fl[2 * c];
-    const float rl = fl[2 * c] - (rh - fh[2 * c]);
-    const float ih = fh[2 * c + 1] + fl[2 * c + 1];
-    const float il = fl[2 * c + 1] - (ih - fh[2 * c + 1]);
-    return make_float4(rh, ih, rl, il);
-  };
   if (ok) {
     for (int c = 0; c < 9; ++c) {
       if constexpr (FF) {
+        // fold in the small terms, renormalise (h, l) and store
         fl[2 * c] -= fs[2 * c];
         fl[2 * c + 1] -= fs[2 * c + 1];
-        const float4 x = face_val(c);
-        H[c] = {(W)x.x, (W)x.y};
+        float rh = fh[2 * c] + fl[2 * c];
+        float rl = fl[2 * c] - (rh - fh[2 * c]);
+        float ih = fh[2 * c + 1] + fl[2 * c + 1];
+        float il = fl[2 * c + 1] - (ih - fh[2 * c + 1]);
+        reinterpret_cast<float4*>(Hd)[e * 9 + c] = make_float4(rh, ih, rl, il);
+        H[c] = {(W)rh, (W)ih};
       } else {
-        St<S>::st(Hd + e * 9 + c, Hd64[c]);   // FP64: stored directly
+        St<S>::st(Hd + e * 9 + c, Hd64[c]);
         H[c] = {(W)Hd64[c].x, (W)Hd64[c].y};
       }
     }
   } else {
     for (int c = 0; c < 9; ++c) H[c] = {W(0), W(0)};
-  }
-  // MIXED: the tile's face leaves through shared memory, two halves of 128
-  // entries (144 bytes each), as contiguous 16-byte stores: a thread's own
-  // 144 bytes stored directly are 9 stores 144 bytes apart per lane, whose
-  // partly written sectors the L2 may evict before the rest arrives
-  if constexpr (FF) {
-    float4* const stage = reinterpret_cast<float4*>(kf_u);   // 128 x 9 x 16 B = 18 KB
-    float4* const gdst = reinterpret_cast<float4*>(Hd) + t.start * 9;
-    for (int half = 0; half < 2; ++half) {
-      __syncthreads();   // kf_u free: residual pass (or the previous half) done
-      if (ok && (threadIdx.x >> 7) == half)
-        for (int c = 0; c < 9; ++c) stage[(threadIdx.x & 127) * 9 + c] = face_val(c);
-      __syncthreads();
-      const int cnt = (int)max((int64_t)0, min((int64_t)128, nval - half * 128)) * 9;
-      for (int q = threadIdx.x; q < cnt; q += blockDim.x) gdst[half * 128 * 9 + q] = stage[q];
-    }
   }
   double s3 = ok ? (double)sigma3<W>(H) : -1.0;
   int64_t idx = ok ? e : INT64_MAX;
@@ -606,7 +583,7 @@ __global__ void __launch_bounds__(kTile, sizeof(S) == 16 && sizeof(R) == 4 ? 2 :
   // shared memory, then a fixed-order sum over the warps.
   // p = slot is the face in registers; p < slot arrive as copies
   // n = 2 slot - 1 - p (the reverse of the residual pass's order).
-  W(*const gw)[16][18] = reinterpret_cast<W(*)[16][18]>(kf_u + 64 * 9 * sizeof(S));
+  __shared__ W gw[kTile / 32][16][18];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int p0 = 0; p0 <= slot; p0 += 16) {
     const int np = min(16, slot + 1 - p0);
