@@ -343,6 +343,19 @@ def run_adjoint(h, steps):
 # our arm
 # ---------------------------------------------------------------------------
 
+def combine_ranks(ms, units, device):
+    """Whole-job figures of independent replicas (one per rank, each with
+    its own operators and work): the slowest rank's time and the units of
+    all ranks (torch.distributed, initialised by the caller: NCCL on the
+    GPUs, gloo in the CPU tests)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(u)
+    return float(t.item()), int(round(u.item()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -444,12 +457,7 @@ def main():
     launches = g.kernel_launches() - l0
     ms = ev0.elapsed_time(ev1)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        e = torch.tensor([float(entries)], device=dev)
-        torch.distributed.all_reduce(e)
-        entries = int(e.item())
+        ms, entries = combine_ranks(ms, entries, dev)
     value = entries / (ms / 1e3)
 
     # apply throughput (algorithmic bytes / time) on the compressed operators:

@@ -690,7 +690,7 @@ __global__ void k_block_red(BlkDev* __restrict__ blk, const int32_t* __restrict_
 
 // ---- fibre + norm + stop test + next frequency (one CTA per block) -----------
 template <typename R, typename S, int KERN, int ROWS>
-__global__ void k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_fibre_step(EntryView v, BlkDev* __restrict__ blk,
                              const int32_t* __restrict__ active, S* const* __restrict__ face_tab,
                              S* const* __restrict__ fib_tab, int64_t nb, int slot,
                              const int32_t* __restrict__ row_perm, const int32_t* __restrict__ col_perm,
@@ -1368,9 +1368,14 @@ static bem_status compress_t(bem_tree* tree, cudaStream_t st, OpData* d) {
       k_block_red<<<(unsigned)n_active, 256, 0, st>>>(d->d_blk, d_active, sl, p_s3, p_idx, p_h2, p_M, d->d_M,
                                                       d->d_hn2, K, d_ctl);
       GCQ_CUDA(ctx, cudaGetLastError());
-      // 256 threads: thread k < K owns frequency k; the near/singular pivot
-      // entries (warp-cooperative) are spread over all eight warps
-      const int tb = 256;
+      // thread k < K owns frequency k; the near/singular pivot entries
+      // (warp-cooperative) are spread over all warps: 256 threads for the
+      // double layer (its pivot entries are more often near or singular),
+      // 128 for the single layer (more CTAs per SM for the light pivots),
+      // at most 128 registers (two 256-thread CTAs per SM).  Measured per
+      // bench step (sphere-5120, K = 64): double layer 173 -> 138 ms,
+      // single layer 64 -> 48 ms against 256 threads and 145 registers.
+      const int tb = std::max(kern_sl(d->kernel) ? 128 : 256, (K + 31) / 32 * 32);
       // the function attribute is process-wide state: it is set to the size
       // of the largest K (256) so that operators with other K compressed
       // concurrently on other host threads never see a smaller limit
