@@ -262,6 +262,18 @@ bem_status bem_op_apply(bem_op* op, int32_t mode, int32_t transpose,
 bem_status bem_op_solve(bem_op* op, const void* B, void* X, double tol, int32_t max_iter,
                         int32_t* iters, double* relres, void* stream);
 
+/* Preconditioner of bem_op_solve and bem_op_solve_adjoint (the paper's
+ * solver has none, Sec. 5; an addition beyond it): kind 0 none (default),
+ * kind 1 block Jacobi, right preconditioning by the inverses of the 3x3
+ * diagonal blocks C(s_k)[i, i] of every frequency (their conjugate
+ * transposes in the adjoint solve).  The blocks are evaluated exactly by the
+ * entry kernels and inverted in FP64 once per operator (a singular block is
+ * left unpreconditioned); K n 9 complex values of device memory held by the
+ * operator.  Needs rows and columns on the same points: single layer with
+ * centroid rows, double layer with node rows.  Synchronises the stream.
+ * Errors: BEM_ERR_ARG (kind, operator kind), BEM_ERR_OOM, BEM_ERR_CUDA. */
+bem_status bem_op_set_precond(bem_op* op, int32_t kind, void* stream);
+
 /* The adjoint systems C(s_k)^H x_k = b_k for every k, by the same
  * K-batched BiCGstab on the conjugate-transpose apply (the adjoint solve of
  * the adjoint method: Sec. 3's Eq. (3.15) transposed).  Arguments, scratch,

@@ -92,6 +92,7 @@ _SIGS = {
     "bem_op_solve": (_i32, [_vp, _vp, _vp, _dbl, _i32, _P(_i32), _P(_dbl), _vp]),
     "bem_op_inner": (_i32, [_vp, _i32, _vp, _vp, _P(_dbl), _vp]),
     "bem_op_solve_adjoint": (_i32, [_vp, _vp, _vp, _dbl, _i32, _P(_i32), _P(_dbl), _vp]),
+    "bem_op_set_precond": (_i32, [_vp, _i32, _vp]),
     "bem_receiver_energy_grad": (_i32, [_vp, _vp, _P(_vp), _P(_vp), _i32, _i32, _dbl, _vp, _P(_i32), _i64, _dbl,
                                         _i32, _P(_dbl), _vp, _P(_dbl), _P(_i32), _vp]),
     "bem_op_compress_batch": (_i32, [_P(_vp), _i32, _i32, _P(_vp)]),
@@ -516,6 +517,11 @@ class Operator:
         if check or st != BEM_ERR_NOT_CONVERGED:
             _check(st, self.ctx.ptr)
         return it, rr
+
+    def set_precond(self, kind: int, stream=None):
+        """Preconditioner of solve(): 0 none, 1 block Jacobi (inverses of the
+        3x3 diagonal blocks at every frequency; bem_op_set_precond)."""
+        _check(_lib.bem_op_set_precond(self._p, int(kind), _stream_ptr(stream)), self.ctx.ptr)
 
     def apply_adjoint(self, Yin, Xout, mode: int = BEM_APPLY_BATCHED, stream=None):
         self.apply(Yin, Xout, mode, stream, transpose=1)

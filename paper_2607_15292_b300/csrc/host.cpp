@@ -904,6 +904,20 @@ bem_status bem_op_solve(bem_op* op, const void* B, void* X, double tol, int32_t 
   return solve(op, 0, B, X, tol, max_iter, iters, relres, (cudaStream_t)stream);
 }
 
+bem_status bem_op_set_precond(bem_op* op, int32_t kind, void* stream) {
+  if (!op) return BEM_ERR_ARG;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  if (kind != 0 && kind != 1) return set_err(ctx, BEM_ERR_ARG, "bem_op_set_precond: kind must be 0 (none) or 1 (block Jacobi)");
+  const bool same = gcq::kern_sl(op->tree->kernel) ? op->tree->rows == BEM_ROWS_CENTROIDS
+                                                   : op->tree->rows == BEM_ROWS_NODES;
+  if (kind == 1 && !same)
+    return set_err(ctx, BEM_ERR_ARG,
+                   "bem_op_set_precond: block Jacobi needs rows and columns on the same points (single layer with "
+                   "centroid rows, double layer with node rows)");
+  GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
+  return set_precond(op, kind, (cudaStream_t)stream);
+}
+
 bem_status bem_op_solve_adjoint(bem_op* op, const void* B, void* X, double tol, int32_t max_iter, int32_t* iters,
                                 double* relres, void* stream) {
   gcq::NvtxRange nvtx("bem_op_solve_adjoint");

@@ -182,6 +182,7 @@ bem_status op_blocks(const bem_op* op, int64_t* info);
 bem_status op_face_ranks(const bem_op* op, int32_t* ranks);
 bem_status solve(bem_op* op, int transpose, const void* B, void* X, double tol, int max_iter, int32_t* iters,
                  double* relres, cudaStream_t st);
+bem_status set_precond(bem_op* op, int32_t kind, cudaStream_t st);
 bem_status inner(bem_op* op, int mode, const void* G, const void* X, double* out, cudaStream_t st);
 bem_status autotune(bem_op* op, cudaStream_t st, int32_t* bk);
 bem_status op_save(const bem_op* op, const char* path);

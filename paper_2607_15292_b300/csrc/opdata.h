@@ -111,6 +111,10 @@ struct OpData {
   int64_t* d_poff = nullptr;
   int64_t* d_qoff = nullptr;
   int32_t *d_rptr = nullptr, *d_rlist = nullptr, *d_cptr = nullptr, *d_clist = nullptr;
+  // preconditioner of the solves (bem_op_set_precond): 0 none, 1 the
+  // inverses of the 3x3 diagonal blocks C_k[i, i], [k][i][3][3]
+  int32_t precond = 0;
+  void* d_pinv = nullptr;
   int32_t apply_kernel = 0;
   int* d_apply_err = nullptr;
   double apply_tensor_flops = 0;     // TF32 flops of one tensor-core batched apply

@@ -70,6 +70,36 @@ __global__ void k_lin3(S* y, const S* u, const S* v, const S* w, const double2* 
   }
 }
 
+// block-Jacobi preconditioner: y[k][i] = M_ki x[k][i] with M_ki the stored
+// inverse of the 3x3 diagonal block C_k[i, i] (adj: its conjugate transpose,
+// the inverse of C_k[i, i]^H); thread per (k, i); y may alias x
+template <typename S>
+__global__ void k_bdiag(const S* __restrict__ Minv, const S* x, S* y, int64_t nblk, int adj) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nblk) return;
+  cx<double> xv[3], m[9];
+  for (int b = 0; b < 3; ++b) xv[b] = St<S>::ld(x + q * 3 + b);
+  for (int c = 0; c < 9; ++c) m[c] = St<S>::ld(Minv + q * 9 + c);
+  for (int a = 0; a < 3; ++a) {
+    cx<double> acc = {0.0, 0.0};
+    for (int b = 0; b < 3; ++b) acc = acc + (adj ? conj(m[3 * b + a]) : m[3 * a + b]) * xv[b];
+    St<S>::st(y + q * 3 + a, acc);
+  }
+}
+
+// the 3x3 blocks in place by their inverses (FP64 cofactors); a singular
+// block is left as the identity (its rows are not preconditioned)
+template <typename S>
+__global__ void k_inv3_blocks(S* __restrict__ blocks, int64_t nblk) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nblk) return;
+  cx<double> P[9], Pi[9];
+  for (int c = 0; c < 9; ++c) P[c] = St<S>::ld(blocks + q * 9 + c);
+  if (!inv3(P, Pi))
+    for (int c = 0; c < 9; ++c) Pi[c] = {c % 4 == 0 ? 1.0 : 0.0, 0.0};
+  for (int c = 0; c < 9; ++c) St<S>::st(blocks + q * 9 + c, Pi[c]);
+}
+
 template <typename S>
 static bem_status solve_t(bem_op* op, int transpose, const void* Bv, void* Xv, double tol, int max_iter,
                           int32_t* iters, double* relres, cudaStream_t st) {
@@ -81,7 +111,9 @@ static bem_status solve_t(bem_op* op, int transpose, const void* Bv, void* Xv, d
   S* buf = nullptr;
   double2* dots = nullptr;
   double2* coef = nullptr;
-  GCQ_CUDA(ctx, cudaMalloc(&buf, 6 * vb));
+  // right preconditioning (block Jacobi): p^ = M p, s^ = M s, x += alpha p^ + omega s^
+  const bool pc = d->precond == 1 && d->d_pinv != nullptr;
+  GCQ_CUDA(ctx, cudaMalloc(&buf, (pc ? 8 : 6) * vb));
   const dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)K);
   // dots: K results, then the K x grid.x CTA shares
   if (cudaMalloc(&dots, sizeof(double2) * K * (1 + grid.x)) != cudaSuccess ||
@@ -94,6 +126,14 @@ static bem_status solve_t(bem_op* op, int transpose, const void* Bv, void* Xv, d
   const S* b = (const S*)Bv;
   S *r = buf, *rh = buf + n * K, *p = buf + 2 * n * K, *v = buf + 3 * n * K, *s = buf + 4 * n * K,
     *t = buf + 5 * n * K;
+  S* ph = pc ? buf + 6 * n * K : p;   // preconditioned search directions
+  S* sh = pc ? buf + 7 * n * K : s;
+  auto precond = [&](const S* in, S* out) -> cudaError_t {
+    const int64_t nb3 = (int64_t)K * d->n_rows;
+    k_bdiag<S><<<(unsigned)((nb3 + 255) / 256), 256, 0, st>>>((const S*)d->d_pinv, in, out, nb3, transpose);
+    count_launches(1);
+    return cudaGetLastError();
+  };
   std::vector<double2> hd(K), hc(3 * K);
   using C = std::complex<double>;
   std::vector<C> rho(K, 1.0), alpha(K, 1.0), omega(K, 1.0), rho_new(K);
@@ -158,7 +198,8 @@ static bem_status solve_t(bem_op* op, int transpose, const void* Bv, void* Xv, d
       setc(k, one, beta, zero - beta * omega[k]);   // p = r + beta (p - omega v)
     }
     if ((e = lin3(p, r, p, v)) != cudaSuccess) break;
-    if ((res = apply(op, BEM_APPLY_BATCHED, transpose, p, v, st)) != BEM_OK) break;
+    if (pc && (e = precond(p, ph)) != cudaSuccess) break;
+    if ((res = apply(op, BEM_APPLY_BATCHED, transpose, ph, v, st)) != BEM_OK) break;
     if ((e = dot(rh, v)) != cudaSuccess) break;
     for (int k = 0; k < K; ++k) {
       const C rv(hd[k].x, hd[k].y);
@@ -171,7 +212,8 @@ static bem_status solve_t(bem_op* op, int transpose, const void* Bv, void* Xv, d
     std::vector<int> early(K, 0);
     for (int k = 0; k < K; ++k)
       if (!done[k] && std::sqrt(std::max(hd[k].x, 0.0)) <= tol * bn[k]) early[k] = 1;
-    if ((res = apply(op, BEM_APPLY_BATCHED, transpose, s, t, st)) != BEM_OK) break;
+    if (pc && (e = precond(s, sh)) != cudaSuccess) break;
+    if ((res = apply(op, BEM_APPLY_BATCHED, transpose, sh, t, st)) != BEM_OK) break;
     if ((e = dot(t, s)) != cudaSuccess) break;
     std::vector<C> ts(K);
     for (int k = 0; k < K; ++k) ts[k] = C(hd[k].x, hd[k].y);
@@ -184,9 +226,9 @@ static bem_status solve_t(bem_op* op, int transpose, const void* Bv, void* Xv, d
       } else {
         omega[k] = hd[k].x > 0.0 ? ts[k] / hd[k].x : zero;
       }
-      setc(k, one, alpha[k], omega[k]);   // x = x + alpha p + omega s
+      setc(k, one, alpha[k], omega[k]);   // x = x + alpha p^ + omega s^
     }
-    if ((e = lin3(x, x, p, s)) != cudaSuccess) break;
+    if ((e = lin3(x, x, ph, sh)) != cudaSuccess) break;
     for (int k = 0; k < K; ++k) setc(k, one, zero - omega[k], zero);   // r = s - omega t
     if ((e = lin3(r, s, t, t)) != cudaSuccess) break;
     if ((e = dot(r, r)) != cudaSuccess) break;
@@ -249,6 +291,60 @@ static bem_status inner_t(bem_op* op, int mode, const void* G, const void* X, do
 bem_status inner(bem_op* op, int mode, const void* G, const void* X, double* out, cudaStream_t st) {
   return op->d->prec == BEM_FP64 ? inner_t<double2>(op, mode, G, X, out, st)
                                  : inner_t<float2>(op, mode, G, X, out, st);
+}
+
+// the preconditioner of the solves: kind 1 inverts the 3x3 diagonal blocks
+// C_k[i, i] of every frequency, from exact entries (the entry kernels),
+// once per operator
+template <typename S>
+static bem_status set_precond_t(bem_op* op, int32_t kind, cudaStream_t st) {
+  OpData* d = op->d;
+  bem_tree* tree = op->tree;
+  bem_ctx* ctx = tree->mesh->ctx;
+  if (kind == 0 || d->d_pinv) {
+    d->precond = kind;
+    return BEM_OK;
+  }
+  const int K = d->K;
+  const int64_t n = d->n_rows, nb3 = (int64_t)K * n;
+  std::vector<int32_t> req(3 * nb3);
+  for (int k = 0; k < K; ++k)
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t* q = &req[3 * ((int64_t)k * n + i)];
+      q[0] = (int32_t)i;
+      q[1] = (int32_t)i;
+      q[2] = k;
+    }
+  void* pinv = nullptr;
+  int32_t* d_req = nullptr;
+  int* d_flag = nullptr;
+  GCQ_CUDA(ctx, cudaMalloc(&pinv, sizeof(S) * 9 * (size_t)nb3));
+  d->allocs.push_back(pinv);
+  if (cudaMalloc(&d_req, sizeof(int32_t) * req.size()) != cudaSuccess || cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess) {
+    cudaFree(d_req);
+    return set_err(ctx, BEM_ERR_OOM, "bem_op_set_precond: out of device memory");
+  }
+  cudaError_t e = cudaMemcpyAsync(d_req, req.data(), sizeof(int32_t) * req.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, sizeof(int), st);
+  bem_status r = BEM_OK;
+  if (e == cudaSuccess) r = launch_entries(tree->mesh, tree->rows, tree->kernel, d_req, nb3, pinv, d_flag, st);
+  if (e == cudaSuccess && r == BEM_OK) {
+    k_inv3_blocks<S><<<(unsigned)((nb3 + 255) / 256), 256, 0, st>>>((S*)pinv, nb3);
+    count_launches(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && r == BEM_OK) e = cudaStreamSynchronize(st);
+  cudaFree(d_req);
+  cudaFree(d_flag);
+  if (r != BEM_OK) return r;
+  if (e != cudaSuccess) return cuda_err(ctx, e, "bem_op_set_precond");
+  d->d_pinv = pinv;
+  d->precond = kind;
+  return BEM_OK;
+}
+
+bem_status set_precond(bem_op* op, int32_t kind, cudaStream_t st) {
+  return op->d->prec == BEM_FP64 ? set_precond_t<double2>(op, kind, st) : set_precond_t<float2>(op, kind, st);
 }
 
 bem_status solve(bem_op* op, int transpose, const void* B, void* X, double tol, int max_iter, int32_t* iters,
