@@ -26,19 +26,19 @@ def lam_c(N: int) -> float:
     return (1e-10) ** (1.0 / (2 * N))
 
 
-def forward(g: np.ndarray, N: int) -> np.ndarray:
-    """g (L, ...) time samples g_0..g_N -> g^ (L, ...)."""
+def forward(g: np.ndarray, N: int, lam: float | None = None) -> np.ndarray:
+    """g (L, ...) time samples g_0..g_N -> g^ (L, ...); lam defaults to lam_c(N)."""
     L = N + 1
-    lam = lam_c(N)
+    lam = lam_c(N) if lam is None else lam
     j = np.arange(L)
     W = np.exp(-2j * np.pi * np.outer(np.arange(L), j) / L) * lam ** j[None, :]
     return np.tensordot(W, g, axes=(1, 0))
 
 
-def inverse(yh: np.ndarray, N: int) -> np.ndarray:
+def inverse(yh: np.ndarray, N: int, lam: float | None = None) -> np.ndarray:
     """y^ (L, ...) -> y (L, ...), y_n = lam^-n / L sum_k y^_k e^{2 pi i n k / L}."""
     L = N + 1
-    lam = lam_c(N)
+    lam = lam_c(N) if lam is None else lam
     n = np.arange(L)
     W = np.exp(2j * np.pi * np.outer(n, np.arange(L)) / L) * (lam ** (-n.astype(float)))[:, None] / L
     return np.tensordot(W, yh, axes=(1, 0))
