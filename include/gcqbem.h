@@ -130,6 +130,16 @@ bem_status bem_material_set(bem_ctx* ctx, double rho, double lambda, double mu,
  * k = 0..K-1, written to s_re_im (host, 2K doubles).  N >= 1, dt > 0,
  * 1 <= K <= N + 1. */
 bem_status bem_freqs_bdf2(int32_t N, double dt, int32_t K, double* s_re_im);
+/* Frequencies of constant-step Runge-Kutta CQ with the 2-stage Radau IIA
+ * method (Sec. 2.4, the paper's time stepping with constant steps):
+ * s_(2l+j) = mu_lj / dt, mu_l0, mu_l1 the eigenvalues of
+ * Delta(zeta_l) = (A + zeta_l / (1 - zeta_l) 1 b^T)^-1, zeta_l =
+ * lam exp(-2 pi i l / L), L = N + 1, lam = (1e-10)^(1/(2N)), ordered by
+ * imaginary part (then real part); written to s_re_im (host, 4L doubles).
+ * sym (host, 16L doubles, may be NULL) receives per l the eigenvector
+ * matrix P_l (2 x 2 complex, row-major, unit columns) then P_l^-1, so that
+ * Delta(zeta_l) = P_l diag(mu_l) P_l^-1.  N >= 1, dt > 0. */
+bem_status bem_freqs_radau2(int32_t N, double dt, double* s_re_im, double* sym);
 /* Sets the K frequencies (host array of 2K doubles) used by every later
  * entry evaluation and compression on ctx.  Re(s) > 0 and 1 <= K <= 256
  * required (one CTA of K threads evaluates a fibre). */
@@ -481,6 +491,22 @@ bem_status bem_debug_set(int32_t what, int64_t value);
 /* Number of CUDA kernels this library has launched in the process so far
  * (all contexts); used to count the device work of a timed region. */
 int64_t bem_kernel_launches(void);
+
+/* Runge-Kutta CQ (2-stage Radau IIA, constant step dt) of the operator:
+ * y = (C * g) at the stage times t_n + c_i dt (c = (1/3, 1)), n = 0..N:
+ * stage-wise scaled DFT of g, mixing of the two stages of each frequency l
+ * into the eigen-coordinates of Delta(zeta_l), one batched apply at the 2L
+ * frequencies s_k of bem_freqs_radau2, mixing back, inverse DFT (real part).
+ * g: device, real FP64, (N + 1) x 2 x n_cols x 3 (level, stage, column,
+ * component) with g[n][i] = g(t_n + c_i dt); y: device, real FP64,
+ * (N + 1) x 2 x n_rows x 3.  The context must hold exactly the 2 (N + 1)
+ * frequencies of bem_freqs_radau2(N, dt) in that order (checked to 1e-9;
+ * bem_freqs_set caps K at 256, so N <= 127).  Transforms and mixing in FP64,
+ * the frequency-domain vectors in the operator's precision.  Allocates its
+ * device scratch (about 2L x (n_cols + 3 n_rows) x 3 complex values) and
+ * releases it before returning; synchronises the stream.  g and y must not
+ * overlap. */
+bem_status bem_rkcq_apply(bem_op* op, int32_t N, double dt, const double* g, double* y, void* stream);
 
 /* Uniform-step CQ (BDF2) transforms over L = N + 1 time levels for nvec
  * complex128 values per level (device, L x nvec):

@@ -108,6 +108,8 @@ _SIGS = {
     "bem_face_compress": (_i32, [_vp, _vp, _i64, _i64, _dbl, _P(_i32), _vp, _vp]),
     "bem_kernel_launches": (_i64, []),
     "bem_debug_set": (_i32, [_i32, _i64]),
+    "bem_freqs_radau2": (_i32, [_i32, _dbl, _P(_dbl), _P(_dbl)]),
+    "bem_rkcq_apply": (_i32, [_vp, _i32, _dbl, _vp, _vp, _vp]),
     "bem_cq_forward": (_i32, [_i32, _i64, _vp, _vp, _vp]),
     "bem_cq_inverse": (_i32, [_i32, _i64, _vp, _vp, _vp]),
 }
@@ -235,6 +237,28 @@ def freqs_bdf2(N: int, dt: float, K: int) -> np.ndarray:
     out = np.zeros(2 * K, dtype=np.float64)
     _check(_lib.bem_freqs_bdf2(N, dt, K, out.ctypes.data_as(_P(_dbl))))
     return out[0::2] + 1j * out[1::2]
+
+
+def freqs_radau2(N: int, dt: float):
+    """Frequencies of constant-step 2-stage Radau IIA RK-CQ (2 (N + 1),
+    complex128, k = 2 l + j) and the symbols (N + 1, 2, 2, 2) complex128:
+    [l, 0] = P_l, [l, 1] = P_l^-1 with Delta(zeta_l) = P_l diag(mu_l) P_l^-1
+    (computed by the library)."""
+    L = N + 1
+    s = np.zeros(4 * L, dtype=np.float64)
+    sym = np.zeros(16 * L, dtype=np.float64)
+    _check(_lib.bem_freqs_radau2(N, dt, s.ctypes.data_as(_P(_dbl)), sym.ctypes.data_as(_P(_dbl))))
+    return s[0::2] + 1j * s[1::2], (sym[0::2] + 1j * sym[1::2]).reshape(L, 2, 2, 2)
+
+
+def rkcq_apply(op: "Operator", g, y, N: int, dt: float, stream=None):
+    """y = RK-CQ (2-stage Radau IIA) convolution of op with the stage data g
+    (bem_rkcq_apply): g real float64 device tensor (N + 1, 2, n_cols, 3),
+    y (N + 1, 2, n_rows, 3); the context holds freqs_radau2(N, dt)[0]."""
+    import torch
+    _device_tensor("g", g, torch.float64, (N + 1, 2, op.tree.n_cols, 3), op.ctx.device)
+    _device_tensor("y", y, torch.float64, (N + 1, 2, op.tree.n_rows, 3), op.ctx.device)
+    _check(_lib.bem_rkcq_apply(op._p, int(N), float(dt), _dptr(g), _dptr(y), _stream_ptr(stream)), op.ctx.ptr)
 
 
 def _cq_args(N, nvec, x, out):

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgcqbem.so")
 SOURCES = ["host.cpp", "gcqbem.cu", "apply_tc.cu", "peaks.cu"]
 DEPS = ["internal.h", "opdata.h", "entry.cuh", "entryf.cuh", "tma.cuh", "tc.cuh", "aca3d.cuh", "faceaca.cuh",
-        "apply.cuh", "solve.cuh", "receiver.cuh", "persist.cuh"]
+        "apply.cuh", "solve.cuh", "receiver.cuh", "rkcq.cuh", "persist.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

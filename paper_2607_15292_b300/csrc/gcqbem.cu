@@ -401,6 +401,7 @@ namespace gcq {}  // aca3d.cuh and apply.cuh reopen the namespace
 #include "apply.cuh"
 #include "solve.cuh"
 #include "receiver.cuh"
+#include "rkcq.cuh"
 #include "persist.cuh"
 
 extern "C" int64_t bem_kernel_launches(void) { return gcq::g_launches.load(); }

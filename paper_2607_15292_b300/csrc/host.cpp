@@ -350,6 +350,69 @@ bem_status build_trees(bem_tree* t) {
   return BEM_OK;
 }
 
+// Delta(zeta) = (A + zeta / (1 - zeta) 1 b^T)^-1 of the 2-stage Radau IIA
+// tableau (A = [5/12 -1/12; 3/4 1/4], b = (3/4, 1/4)) and its
+// eigendecomposition P diag(mu) P^-1: eigenvalues from the characteristic
+// quadratic (larger root first in the cancellation-free form, the other as
+// det / root), ordered by imaginary part, then by real part when the two are
+// equal to rounding; eigenvectors from the row with the larger entries,
+// unit length.
+static void radau2_symbol(std::complex<double> zeta, std::complex<double> mu[2], std::complex<double> P[4],
+                          std::complex<double> Pi[4]) {
+  using cd = std::complex<double>;
+  const double a[4] = {5.0 / 12.0, -1.0 / 12.0, 3.0 / 4.0, 1.0 / 4.0}, b[2] = {3.0 / 4.0, 1.0 / 4.0};
+  const cd r = zeta / (1.0 - zeta);
+  const cd M[4] = {a[0] + r * b[0], a[1] + r * b[1], a[2] + r * b[0], a[3] + r * b[1]};
+  const cd dm = M[0] * M[3] - M[1] * M[2];
+  const cd D[4] = {M[3] / dm, -M[1] / dm, -M[2] / dm, M[0] / dm};
+  const cd tr = D[0] + D[3], det = D[0] * D[3] - D[1] * D[2];
+  cd sq = std::sqrt(tr * tr - 4.0 * det);
+  if (std::real(std::conj(tr) * sq) < 0) sq = -sq;
+  cd m0 = 0.5 * (tr + sq), m1 = det / m0;
+  const double tol = 1e-12 * std::max(std::abs(m0), std::abs(m1));
+  const bool swap01 = std::abs(m0.imag() - m1.imag()) > tol ? m1.imag() < m0.imag() : m1.real() < m0.real();
+  if (swap01) std::swap(m0, m1);
+  mu[0] = m0;
+  mu[1] = m1;
+  for (int j = 0; j < 2; ++j) {
+    cd v0 = D[1], v1 = mu[j] - D[0];
+    const cd w0 = mu[j] - D[3], w1 = D[2];
+    if (std::norm(w0) + std::norm(w1) > std::norm(v0) + std::norm(v1)) {
+      v0 = w0;
+      v1 = w1;
+    }
+    const double nv = std::sqrt(std::norm(v0) + std::norm(v1));
+    P[j] = v0 / nv;        // column j
+    P[2 + j] = v1 / nv;
+  }
+  const cd dp = P[0] * P[3] - P[1] * P[2];
+  Pi[0] = P[3] / dp;
+  Pi[1] = -P[1] / dp;
+  Pi[2] = -P[2] / dp;
+  Pi[3] = P[0] / dp;
+}
+
+void radau2_symbols(int N, double dt, double* s, double* sym) {
+  const int L = N + 1;
+  const double lam = std::pow(1e-10, 1.0 / (2.0 * N));
+  for (int l = 0; l < L; ++l) {
+    const std::complex<double> z = lam * std::exp(std::complex<double>(0.0, -2.0 * M_PI * l / L));
+    std::complex<double> mu[2], P[4], Pi[4];
+    radau2_symbol(z, mu, P, Pi);
+    for (int j = 0; j < 2; ++j) {
+      s[4 * l + 2 * j] = mu[j].real() / dt;
+      s[4 * l + 2 * j + 1] = mu[j].imag() / dt;
+    }
+    if (sym)
+      for (int q = 0; q < 4; ++q) {
+        sym[16 * l + 2 * q] = P[q].real();
+        sym[16 * l + 2 * q + 1] = P[q].imag();
+        sym[16 * l + 8 + 2 * q] = Pi[q].real();
+        sym[16 * l + 8 + 2 * q + 1] = Pi[q].imag();
+      }
+  }
+}
+
 }  // namespace gcq
 
 using namespace gcq;
@@ -469,6 +532,12 @@ bem_status bem_freqs_bdf2(int32_t N, double dt, int32_t K, double* s) {
     s[2 * k] = sr / dt;
     s[2 * k + 1] = si / dt;
   }
+  return BEM_OK;
+}
+
+bem_status bem_freqs_radau2(int32_t N, double dt, double* s, double* sym) {
+  if (N < 1 || !(dt > 0) || !s) return BEM_ERR_ARG;
+  radau2_symbols(N, dt, s, sym);
   return BEM_OK;
 }
 
@@ -1048,6 +1117,31 @@ bem_status bem_receiver_energy_grad(bem_op* V, bem_op* A, bem_op* const* dV, bem
   GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
   return receiver_energy_grad(V, A, dV, dA, n_speeds, N, dt, g, rec, n_rec, tol, max_iter, J, dJ_dg, dJ_dc, iters,
                               (cudaStream_t)stream);
+}
+
+bem_status bem_rkcq_apply(bem_op* op, int32_t N, double dt, const double* g, double* y, void* stream) {
+  gcq::NvtxRange nvtx("bem_rkcq_apply");
+  if (!op) return BEM_ERR_ARG;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  const char* fn = "bem_rkcq_apply: ";
+  auto bad = [&](const char* why) { return set_err(ctx, BEM_ERR_ARG, std::string(fn) + why); };
+  if (N < 1 || !(dt > 0) || !g || !y) return bad("bad arguments");
+  if (((uintptr_t)g & 7) || ((uintptr_t)y & 7)) return bad("g and y must be 8-byte aligned");
+  const int L = N + 1;
+  if (ctx->K != 2 * L) return bad("the context must hold the 2 (N + 1) Radau IIA frequencies of N, dt");
+  std::vector<double> s(4 * (size_t)L);
+  radau2_symbols(N, dt, s.data(), nullptr);
+  for (int k = 0; k < 2 * L; ++k) {
+    const std::complex<double> want(s[2 * k], s[2 * k + 1]), have(ctx->s[2 * k], ctx->s[2 * k + 1]);
+    if (std::abs(have - want) > 1e-9 * std::abs(want))
+      return bad("the context's frequencies are not the Radau IIA RK-CQ frequencies of N, dt");
+  }
+  const int64_t nin = 3 * op->tree->n_cols, nout = 3 * op->tree->n_rows;
+  const uintptr_t g0 = (uintptr_t)g, g1 = g0 + sizeof(double) * 2 * L * nin;
+  const uintptr_t y0 = (uintptr_t)y, y1 = y0 + sizeof(double) * 2 * L * nout;
+  if (g0 < y1 && y0 < g1) return bad("g and y must not overlap");
+  GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
+  return rkcq_apply(op, N, dt, g, y, (cudaStream_t)stream);
 }
 
 bem_status bem_cq_forward(int32_t N, int64_t nvec, const void* in, void* out, void* stream) {

@@ -195,5 +195,10 @@ bem_status cq_transform(int N, int64_t nvec, const void* in, void* out, bool inv
 bem_status receiver_energy_grad(bem_op* V, bem_op* A, bem_op* const* dV, bem_op* const* dA, int ns, int N, double dt,
                                 const double* g, const int32_t* rec, int64_t n_rec, double tol, int max_iter,
                                 double* J, double* dJ_dg, double* dJ_dc, int32_t* iters, cudaStream_t st);
+// 2-stage Radau IIA RK-CQ: the 2L frequencies s (2 doubles each, k = 2l + j)
+// and per l the eigenvector matrices P_l then P_l^-1 of Delta(zeta_l)
+// (2 x 2 complex row-major each, 16 doubles per l)
+void radau2_symbols(int N, double dt, double* s, double* sym);
+bem_status rkcq_apply(bem_op* op, int N, double dt, const double* g, double* y, cudaStream_t st);
 
 }  // namespace gcq

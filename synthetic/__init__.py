@@ -353,11 +353,13 @@ def box_receivers(xyz: np.ndarray, n: int, seed: int = 7) -> np.ndarray:
 
 
 def box_traction(xyz: np.ndarray, tri: np.ndarray, N: int, dt: float, width: float, t0: float, tw: float,
-                 seed: int = 11, amp: float = 1e6) -> np.ndarray:
+                 seed: int = 11, amp: float = 1e6, offsets=None) -> np.ndarray:
     """Traction samples g (N + 1, n_tris, 3) in Pa, real: on the top-face
     elements (centroid z = max z) a downward load
     amp exp(-|c - p|^2 / (2 w^2)) exp(-(t_n - t0)^2 / (2 tw^2)), p a seeded
-    point of the top face; zero elsewhere."""
+    point of the top face; zero elsewhere.  With offsets (m values, in
+    units of dt) the samples are taken at t = (n + offsets_i) dt instead:
+    g (N + 1, m, n_tris, 3)."""
     c = xyz[tri].mean(axis=1)
     zt = xyz[:, 2].max()
     top = np.abs(c[:, 2] - zt) <= 1e-9 * max(1.0, float(np.abs(xyz).max()))
@@ -365,10 +367,13 @@ def box_traction(xyz: np.ndarray, tri: np.ndarray, N: int, dt: float, width: flo
     u = uniform01(seed, 2)
     p = lo + (0.25 + 0.5 * u) * (hi - lo)
     space = np.exp(-((c[:, :2] - p) ** 2).sum(1) / (2.0 * width ** 2)) * top
-    t = dt * np.arange(N + 1)
+    if offsets is None:
+        t = dt * np.arange(N + 1)
+    else:
+        t = dt * (np.arange(N + 1)[:, None] + np.asarray(offsets, dtype=float)[None, :])
     time = np.exp(-((t - t0) ** 2) / (2.0 * tw ** 2))
-    g = np.zeros((N + 1, len(tri), 3))
-    g[:, :, 2] = -amp * time[:, None] * space[None, :]
+    g = np.zeros(t.shape + (len(tri), 3))
+    g[..., 2] = -amp * time[..., None] * space
     return g
 
 

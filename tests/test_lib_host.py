@@ -35,6 +35,32 @@ def test_freqs_match_oracle():
         np.testing.assert_allclose(s, bem.freqs_bdf2(N, dt, K), rtol=1e-14, atol=0)
 
 
+@pytest.mark.parametrize("N,dt", [(1, 1e-3), (10, 4e-5), (31, 1e-4), (127, 2e-6)])
+def test_radau2_freqs_and_symbols_match_oracle(N, dt):
+    """The library's RK-CQ frequencies are the oracle's as a set (each of
+    the two eigenvalues per l, whichever order), and its symbols
+    reassemble the oracle's Delta(zeta_l): P_l diag(s_l dt) P_l^-1 =
+    Delta(zeta_l), P_l^-1 P_l = I."""
+    from oracle import cq, rkcq
+    s, sym = g.freqs_radau2(N, dt)
+    L = N + 1
+    ref = rkcq.freqs_radau2(N, dt).reshape(L, 2)
+    lam = cq.lam_c(N)
+    for l in range(L):
+        mine = s[2 * l: 2 * l + 2]
+        d = min(np.abs(mine - ref[l]).max(), np.abs(mine[::-1] - ref[l]).max())
+        assert d <= 1e-11 * np.abs(ref[l]).max(), (l, mine, ref[l])
+        assert mine[0].imag <= mine[1].imag + 1e-12 * np.abs(mine).max()
+        P, Pi = sym[l, 0], sym[l, 1]
+        Dl = rkcq.delta(lam * np.exp(-2j * np.pi * l / L))
+        np.testing.assert_allclose(P @ np.diag(mine * dt) @ Pi, Dl, rtol=0, atol=1e-11 * np.abs(Dl).max())
+        np.testing.assert_allclose(Pi @ P, np.eye(2), rtol=0, atol=1e-12)
+    with pytest.raises(g.BemError):
+        g.freqs_radau2(0, dt)
+    with pytest.raises(g.BemError):
+        g.freqs_radau2(N, -dt)
+
+
 def _perturbed_sphere(level, seed):
     xyz, tri = syn.icosphere(level)
     rng = np.random.default_rng(seed)
