@@ -88,3 +88,23 @@ def convolve(apply_k, g: np.ndarray, N: int, dt: float, lam: float | None = None
         f = np.stack([np.asarray(apply_k(2 * l + j, mus[l, j] / dt, e[j])) for j in range(2)])
         yh.append(np.tensordot(Ps[l], f, axes=(1, 0)))
     return cq.inverse(np.stack(yh), N, lam)
+
+
+def stage_times(N: int, dt: float) -> np.ndarray:
+    """t_n + c_i dt for n = 0..N (step n covers (t_n, t_n + dt]), shape (L, 2)."""
+    return dt * (np.arange(N + 1)[:, None] + C_RADAU2[None, :])
+
+
+def dirichlet_traction(xyz, tri, material, u: np.ndarray, N: int, dt: float) -> np.ndarray:
+    """The Dirichlet problem of collocation BEM (Sec. 2.3, Eq. (2.15) at the
+    element midpoints): V t = (C + K) u in time, by RK-CQ with the dense
+    oracle operators at the oracle's frequencies: per frequency
+    t^ = V(s)^-1 (C + K)(s) u^.  u: stage data at the nodes (L, 2, n_nodes, 3);
+    returns the traction stage data at the elements (L, 2, n_tris, 3)."""
+    from . import bem
+    s = freqs_radau2(N, dt)
+    Vd = bem.Operator(xyz, tri, material, bem.ROWS_CENTROIDS, bem.KERNEL_SL).dense(s)
+    Ad = bem.Operator(xyz, tri, material, bem.ROWS_CENTROIDS, bem.KERNEL_DL).dense(s)
+    V = [bem.to_matrix(Vd[:, :, k]) for k in range(len(s))]
+    A = [bem.to_matrix(Ad[:, :, k]) for k in range(len(s))]
+    return convolve(lambda k, sk, x: np.linalg.solve(V[k], A[k] @ x.reshape(-1)).reshape(-1, 3), u, N, dt).real
