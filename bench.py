@@ -343,6 +343,60 @@ def run_adjoint(h, steps):
         "rank_mean": [round(x.rank_mean, 2) for x in st]}))
 
 
+def run_rkcq(h, steps, N=127):
+    """Runge-Kutta CQ (2-stage Radau IIA) of the box single layer at grid
+    spacing h (the box of synthetic.BOX_ADJOINT; 0.4 m is 20,000 triangles):
+    N + 1 steps of dt = 2 x BOX_ADJOINT's dt over the same time span, so
+    K = 2 (N + 1) = 256 frequencies; MIXED compression, then
+    bem_rkcq_apply (stage DFT + eigen-mixing, batched apply, unmix, inverse
+    DFT) timed over `steps` calls after one warm-up call, beside the
+    batched apply alone at the same K; one JSON line."""
+    import torch
+    import paper_2607_15292_b300 as g
+    w = syn.BOX_ADJOINT
+    xyz, tri = syn.box(w["lx"], w["ly"], w["lz"], h)
+    dt = 2.0 * w["dt"]
+    s, _ = g.freqs_radau2(N, dt)
+    ctx = g.Context(eps=1e-6, leaf=32, eta=2.0, precision=g.BEM_MIXED)
+    ctx.material(*syn.STEEL)
+    ctx.freqs(s)
+    mesh = ctx.mesh(xyz, tri)
+    tree = mesh.tree(g.BEM_ROWS_NODES, g.BEM_SL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    V = tree.compress()
+    torch.cuda.synchronize()
+    t_comp = time.perf_counter() - t0
+    gs = torch.tensor(syn.box_traction(xyz, tri, N, dt, w["width"], w["t0"], w["tw"], offsets=(1.0 / 3.0, 1.0)),
+                      dtype=torch.float64, device="cuda")
+    y = torch.empty((N + 1, 2, tree.n_rows, 3), dtype=torch.float64, device="cuda")
+    g.rkcq_apply(V, gs, y, N, dt)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(steps):
+        g.rkcq_apply(V, gs, y, N, dt)
+    ev[1].record()
+    X = torch.zeros((len(s), tree.n_cols, 3), dtype=torch.complex64, device="cuda")
+    Y = torch.empty((len(s), tree.n_rows, 3), dtype=torch.complex64, device="cuda")
+    V.apply(X, Y)
+    ev[2].record()
+    for _ in range(steps):
+        V.apply(X, Y)
+    ev[3].record()
+    torch.cuda.synchronize()
+    t_rk = ev[0].elapsed_time(ev[1]) / steps
+    t_ap = ev[2].elapsed_time(ev[3]) / steps
+    st = V.stats()
+    print(json.dumps({
+        "case": "box single layer, RK-CQ with 2-stage Radau IIA (constant steps)",
+        "box": [w["lx"], w["ly"], w["lz"]], "h": h, "triangles": len(tri), "nodes": len(xyz), "N": N, "dt": dt,
+        "K": len(s), "precision": "MIXED", "eps": 1e-6, "compress_s": t_comp, "rkcq_ms": t_rk,
+        "batched_apply_ms": t_ap, "transforms_and_mixing_ms": t_rk - t_ap, "steps": steps,
+        "y_max": float(y.abs().max()), "stored_gb": round(st.stored_bytes / 1e9, 3),
+        "rank_mean": round(st.rank_mean, 2)}))
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -381,6 +435,9 @@ def main():
     ap.add_argument("--adjoint", type=float, default=0.0, metavar="H",
                     help="box adjoint workload at grid spacing H (0.4 = full size): compression of the six "
                          "operators and the receiver-energy gradient; prints its statistics (not the bench line)")
+    ap.add_argument("--rkcq", type=float, default=0.0, metavar="H",
+                    help="box single layer through Runge-Kutta CQ (2-stage Radau IIA, K = 256) at grid spacing "
+                         "H (0.4 = full size); prints its statistics (not the bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -390,6 +447,8 @@ def main():
         return run_batch(args.batch, args.batch_nmax, args.batch_streams)
     if args.adjoint > 0:
         return run_adjoint(args.adjoint, max(1, args.steps))
+    if args.rkcq > 0:
+        return run_rkcq(args.rkcq, max(1, args.steps))
 
     import torch
     import paper_2607_15292_b300 as g

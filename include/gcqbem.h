@@ -508,6 +508,18 @@ int64_t bem_kernel_launches(void);
  * overlap. */
 bem_status bem_rkcq_apply(bem_op* op, int32_t N, double dt, const double* g, double* y, void* stream);
 
+/* Runge-Kutta CQ of the inverse of a square operator: x = C(d_t)^-1 b at
+ * the stage times, i.e. the same transforms as bem_rkcq_apply around a
+ * K-batched BiCGstab solve C(s_k) f_k = e_k (bem_op_solve's iteration and
+ * preconditioner) instead of the apply.  b, x: device, real FP64,
+ * (N + 1) x 2 x n x 3, n = n_rows = n_cols.  iters, relres: host, 2 (N + 1)
+ * entries each (per frequency).  Returns BEM_ERR_NOT_CONVERGED (after
+ * completing x) when a frequency reached max_iter; otherwise as
+ * bem_rkcq_apply.  The Dirichlet problem of Sec. 2.3 (V t = (C + K) u at the
+ * element midpoints) is bem_rkcq_apply of C + K followed by this call on V. */
+bem_status bem_rkcq_solve(bem_op* op, int32_t N, double dt, const double* b, double* x, double tol, int32_t max_iter,
+                          int32_t* iters, double* relres, void* stream);
+
 /* Uniform-step CQ (BDF2) transforms over L = N + 1 time levels for nvec
  * complex128 values per level (device, L x nvec):
  *   forward: g^_k = sum_j lam^j g_j exp(-2 pi i j k / L)

@@ -110,6 +110,7 @@ _SIGS = {
     "bem_debug_set": (_i32, [_i32, _i64]),
     "bem_freqs_radau2": (_i32, [_i32, _dbl, _P(_dbl), _P(_dbl)]),
     "bem_rkcq_apply": (_i32, [_vp, _i32, _dbl, _vp, _vp, _vp]),
+    "bem_rkcq_solve": (_i32, [_vp, _i32, _dbl, _vp, _vp, _dbl, _i32, _P(_i32), _P(_dbl), _vp]),
     "bem_cq_forward": (_i32, [_i32, _i64, _vp, _vp, _vp]),
     "bem_cq_inverse": (_i32, [_i32, _i64, _vp, _vp, _vp]),
 }
@@ -259,6 +260,28 @@ def rkcq_apply(op: "Operator", g, y, N: int, dt: float, stream=None):
     _device_tensor("g", g, torch.float64, (N + 1, 2, op.tree.n_cols, 3), op.ctx.device)
     _device_tensor("y", y, torch.float64, (N + 1, 2, op.tree.n_rows, 3), op.ctx.device)
     _check(_lib.bem_rkcq_apply(op._p, int(N), float(dt), _dptr(g), _dptr(y), _stream_ptr(stream)), op.ctx.ptr)
+
+
+def rkcq_solve(op: "Operator", b, x, N: int, dt: float, tol: float = 1e-8, max_iter: int = 300,
+               stream=None, check: bool = True):
+    """x = RK-CQ (2-stage Radau IIA) of op^-1 applied to the stage data b
+    (bem_rkcq_solve): b, x real float64 device tensors (N + 1, 2, n, 3) of
+    a square operator; returns (iterations, relative residuals) per
+    frequency.  With check=False a frequency that did not converge is not
+    an error."""
+    import torch
+    n = op.tree.n_rows
+    if n != op.tree.n_cols:
+        raise ValueError("rkcq_solve: the operator is not square")
+    _device_tensor("b", b, torch.float64, (N + 1, 2, n, 3), op.ctx.device)
+    _device_tensor("x", x, torch.float64, (N + 1, 2, n, 3), op.ctx.device)
+    it = np.zeros(2 * (N + 1), dtype=np.int32)
+    rr = np.zeros(2 * (N + 1), dtype=np.float64)
+    st = _lib.bem_rkcq_solve(op._p, int(N), float(dt), _dptr(b), _dptr(x), float(tol), int(max_iter),
+                             it.ctypes.data_as(_P(_i32)), rr.ctypes.data_as(_P(_dbl)), _stream_ptr(stream))
+    if st != BEM_ERR_NOT_CONVERGED or check:
+        _check(st, op.ctx.ptr)
+    return it, rr
 
 
 def _cq_args(N, nvec, x, out):

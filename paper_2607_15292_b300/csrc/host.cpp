@@ -1119,14 +1119,14 @@ bem_status bem_receiver_energy_grad(bem_op* V, bem_op* A, bem_op* const* dV, bem
                               (cudaStream_t)stream);
 }
 
-bem_status bem_rkcq_apply(bem_op* op, int32_t N, double dt, const double* g, double* y, void* stream) {
-  gcq::NvtxRange nvtx("bem_rkcq_apply");
-  if (!op) return BEM_ERR_ARG;
+// common checks of bem_rkcq_apply / bem_rkcq_solve: the context holds the
+// Radau IIA frequencies of N, dt; the buffers are aligned and disjoint
+static bem_status rkcq_check(bem_op* op, int32_t N, double dt, const void* in, int64_t nin, const void* out,
+                             int64_t nout, const char* fn) {
   bem_ctx* ctx = op->tree->mesh->ctx;
-  const char* fn = "bem_rkcq_apply: ";
   auto bad = [&](const char* why) { return set_err(ctx, BEM_ERR_ARG, std::string(fn) + why); };
-  if (N < 1 || !(dt > 0) || !g || !y) return bad("bad arguments");
-  if (((uintptr_t)g & 7) || ((uintptr_t)y & 7)) return bad("g and y must be 8-byte aligned");
+  if (N < 1 || !(dt > 0) || !in || !out) return bad("bad arguments");
+  if (((uintptr_t)in & 7) || ((uintptr_t)out & 7)) return bad("the stage buffers must be 8-byte aligned");
   const int L = N + 1;
   if (ctx->K != 2 * L) return bad("the context must hold the 2 (N + 1) Radau IIA frequencies of N, dt");
   std::vector<double> s(4 * (size_t)L);
@@ -1136,12 +1136,35 @@ bem_status bem_rkcq_apply(bem_op* op, int32_t N, double dt, const double* g, dou
     if (std::abs(have - want) > 1e-9 * std::abs(want))
       return bad("the context's frequencies are not the Radau IIA RK-CQ frequencies of N, dt");
   }
-  const int64_t nin = 3 * op->tree->n_cols, nout = 3 * op->tree->n_rows;
-  const uintptr_t g0 = (uintptr_t)g, g1 = g0 + sizeof(double) * 2 * L * nin;
-  const uintptr_t y0 = (uintptr_t)y, y1 = y0 + sizeof(double) * 2 * L * nout;
-  if (g0 < y1 && y0 < g1) return bad("g and y must not overlap");
+  const uintptr_t a0 = (uintptr_t)in, a1 = a0 + sizeof(double) * 2 * L * nin;
+  const uintptr_t b0 = (uintptr_t)out, b1 = b0 + sizeof(double) * 2 * L * nout;
+  if (a0 < b1 && b0 < a1) return bad("the input and output stage buffers must not overlap");
+  return BEM_OK;
+}
+
+bem_status bem_rkcq_apply(bem_op* op, int32_t N, double dt, const double* g, double* y, void* stream) {
+  gcq::NvtxRange nvtx("bem_rkcq_apply");
+  if (!op) return BEM_ERR_ARG;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  bem_status r = rkcq_check(op, N, dt, g, 3 * op->tree->n_cols, y, 3 * op->tree->n_rows, "bem_rkcq_apply: ");
+  if (r != BEM_OK) return r;
   GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
   return rkcq_apply(op, N, dt, g, y, (cudaStream_t)stream);
+}
+
+bem_status bem_rkcq_solve(bem_op* op, int32_t N, double dt, const double* b, double* x, double tol, int32_t max_iter,
+                          int32_t* iters, double* relres, void* stream) {
+  gcq::NvtxRange nvtx("bem_rkcq_solve");
+  if (!op) return BEM_ERR_ARG;
+  bem_ctx* ctx = op->tree->mesh->ctx;
+  if (op->tree->n_rows != op->tree->n_cols)
+    return set_err(ctx, BEM_ERR_ARG, "bem_rkcq_solve: the operator is not square (rows != columns)");
+  if (!iters || !relres || !(tol > 0 && tol < 1) || max_iter < 1)
+    return set_err(ctx, BEM_ERR_ARG, "bem_rkcq_solve: bad arguments");
+  bem_status r = rkcq_check(op, N, dt, b, 3 * op->tree->n_rows, x, 3 * op->tree->n_cols, "bem_rkcq_solve: ");
+  if (r != BEM_OK) return r;
+  GCQ_CUDA(ctx, cudaSetDevice(ctx->device));
+  return rkcq_solve(op, N, dt, b, x, tol, max_iter, iters, relres, (cudaStream_t)stream);
 }
 
 bem_status bem_cq_forward(int32_t N, int64_t nvec, const void* in, void* out, void* stream) {

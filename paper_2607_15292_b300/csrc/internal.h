@@ -200,5 +200,7 @@ bem_status receiver_energy_grad(bem_op* V, bem_op* A, bem_op* const* dV, bem_op*
 // (2 x 2 complex row-major each, 16 doubles per l)
 void radau2_symbols(int N, double dt, double* s, double* sym);
 bem_status rkcq_apply(bem_op* op, int N, double dt, const double* g, double* y, cudaStream_t st);
+bem_status rkcq_solve(bem_op* op, int N, double dt, const double* b, double* x, double tol, int max_iter,
+                      int32_t* iters, double* relres, cudaStream_t st);
 
 }  // namespace gcq

@@ -82,12 +82,18 @@ __global__ void k_rk_inv(int L, double lnlam, int64_t nvec, const double2* __res
   y[(int64_t)(2 * n + 1) * nvec + v] = sc * acc1;
 }
 
+// RK-CQ of the operator (f_k = C(s_k) e_k) or of its inverse (f_k solves
+// C(s_k) f_k = e_k by the K-batched BiCGstab; g then lives on the rows and
+// y on the columns).  A solve that does not converge still completes the
+// transforms and its status is returned last.
 template <typename S>
-static bem_status rkcq_apply_t(bem_op* op, int N, double dt, const double* g, double* y, cudaStream_t st) {
+static bem_status rkcq_run_t(bem_op* op, int N, double dt, const double* g, double* y, bool inverse_op, double tol,
+                             int max_iter, int32_t* iters, double* relres, cudaStream_t st) {
   bem_ctx* ctx = op->tree->mesh->ctx;
   const int L = N + 1, K = 2 * L;
   const double lnlam = std::log(1e-10) / (2.0 * N);
-  const int64_t nin = 3 * op->tree->n_cols, nout = 3 * op->tree->n_rows;
+  const int64_t nin = 3 * (inverse_op ? op->tree->n_rows : op->tree->n_cols);
+  const int64_t nout = 3 * (inverse_op ? op->tree->n_cols : op->tree->n_rows);
   std::vector<double> s(2 * K), sym_h(16 * (size_t)L);
   radau2_symbols(N, dt, s.data(), sym_h.data());
   struct Bufs {
@@ -106,26 +112,33 @@ static bem_status rkcq_apply_t(bem_op* op, int N, double dt, const double* g, do
   if (!get(&sym, sizeof(double) * sym_h.size()) || !get(&e, sizeof(S) * K * nin) || !get(&f, sizeof(S) * K * nout) ||
       !get(&z, sizeof(double2) * K * nout)) {
     cudaGetLastError();
-    return set_err(ctx, BEM_ERR_OOM, "bem_rkcq_apply: out of device memory");
+    return set_err(ctx, BEM_ERR_OOM, "RK-CQ: out of device memory");
   }
   GCQ_CUDA(ctx, cudaMemcpyAsync(sym, sym_h.data(), sizeof(double) * sym_h.size(), cudaMemcpyHostToDevice, st));
   const size_t tab = sizeof(double2) * L;
   k_rk_fwd<S><<<dim3((unsigned)((nin + 127) / 128), L), 128, tab, st>>>(L, lnlam, nin, sym, g, e);
   GCQ_CUDA(ctx, cudaGetLastError());
   count_launches(1);
-  bem_status r = apply(op, BEM_APPLY_BATCHED, 0, e, f, st);
-  if (r != BEM_OK) return r;
+  const bem_status r = inverse_op ? solve(op, 0, e, f, tol, max_iter, iters, relres, st)
+                                  : apply(op, BEM_APPLY_BATCHED, 0, e, f, st);
+  if (r != BEM_OK && r != BEM_ERR_NOT_CONVERGED) return r;
   k_rk_unmix<S><<<dim3((unsigned)((nout + 127) / 128), L), 128, 0, st>>>(L, nout, sym, f, z);
   k_rk_inv<<<dim3((unsigned)((nout + 127) / 128), L), 128, tab, st>>>(L, lnlam, nout, z, y);
   GCQ_CUDA(ctx, cudaGetLastError());
   count_launches(2);
   GCQ_CUDA(ctx, cudaStreamSynchronize(st));
-  return BEM_OK;
+  return r;
 }
 
 bem_status rkcq_apply(bem_op* op, int N, double dt, const double* g, double* y, cudaStream_t st) {
-  return op->d->prec == BEM_FP64 ? rkcq_apply_t<double2>(op, N, dt, g, y, st)
-                                 : rkcq_apply_t<float2>(op, N, dt, g, y, st);
+  return op->d->prec == BEM_FP64 ? rkcq_run_t<double2>(op, N, dt, g, y, false, 0.0, 0, nullptr, nullptr, st)
+                                 : rkcq_run_t<float2>(op, N, dt, g, y, false, 0.0, 0, nullptr, nullptr, st);
+}
+
+bem_status rkcq_solve(bem_op* op, int N, double dt, const double* b, double* x, double tol, int max_iter,
+                      int32_t* iters, double* relres, cudaStream_t st) {
+  return op->d->prec == BEM_FP64 ? rkcq_run_t<double2>(op, N, dt, b, x, true, tol, max_iter, iters, relres, st)
+                                 : rkcq_run_t<float2>(op, N, dt, b, x, true, tol, max_iter, iters, relres, st);
 }
 
 }  // namespace gcq
