@@ -346,8 +346,9 @@ def run_adjoint(h, steps):
 def run_rkcq(h, steps, N=127):
     """Runge-Kutta CQ (2-stage Radau IIA) of the box single layer at grid
     spacing h (the box of synthetic.BOX_ADJOINT; 0.4 m is 20,000 triangles):
-    N + 1 steps of dt = 2 x BOX_ADJOINT's dt over the same time span, so
-    K = 2 (N + 1) = 256 frequencies; MIXED compression, then
+    N + 1 steps of dt = 2 x BOX_ADJOINT's dt over the same time span, the
+    half frequency set (K = 2 (floor((N + 1) / 2) + 1) = 130 of the 256:
+    conjugate pairs of real data); MIXED compression, then
     bem_rkcq_apply (stage DFT + eigen-mixing, batched apply, unmix, inverse
     DFT) timed over `steps` calls after one warm-up call, beside the
     batched apply alone at the same K; one JSON line."""
@@ -356,7 +357,7 @@ def run_rkcq(h, steps, N=127):
     w = syn.BOX_ADJOINT
     xyz, tri = syn.box(w["lx"], w["ly"], w["lz"], h)
     dt = 2.0 * w["dt"]
-    s, _ = g.freqs_radau2(N, dt)
+    s, _ = g.freqs_radau2(N, dt, half=True)
     ctx = g.Context(eps=1e-6, leaf=32, eta=2.0, precision=g.BEM_MIXED)
     ctx.material(*syn.STEEL)
     ctx.freqs(s)
@@ -391,7 +392,8 @@ def run_rkcq(h, steps, N=127):
     print(json.dumps({
         "case": "box single layer, RK-CQ with 2-stage Radau IIA (constant steps)",
         "box": [w["lx"], w["ly"], w["lz"]], "h": h, "triangles": len(tri), "nodes": len(xyz), "N": N, "dt": dt,
-        "K": len(s), "precision": "MIXED", "eps": 1e-6, "compress_s": t_comp, "rkcq_ms": t_rk,
+        "K": len(s), "frequency_set": "half (conjugate pairs)", "precision": "MIXED", "eps": 1e-6,
+        "compress_s": t_comp, "rkcq_ms": t_rk,
         "batched_apply_ms": t_ap, "transforms_and_mixing_ms": t_rk - t_ap, "steps": steps,
         "y_max": float(y.abs().max()), "stored_gb": round(st.stored_bytes / 1e9, 3),
         "rank_mean": round(st.rank_mean, 2)}))
@@ -436,7 +438,7 @@ def main():
                     help="box adjoint workload at grid spacing H (0.4 = full size): compression of the six "
                          "operators and the receiver-energy gradient; prints its statistics (not the bench line)")
     ap.add_argument("--rkcq", type=float, default=0.0, metavar="H",
-                    help="box single layer through Runge-Kutta CQ (2-stage Radau IIA, K = 256) at grid spacing "
+                    help="box single layer through Runge-Kutta CQ (2-stage Radau IIA, half set K = 130) at grid spacing "
                          "H (0.4 = full size); prints its statistics (not the bench line)")
     args = ap.parse_args()
     if args.impl == "reference":

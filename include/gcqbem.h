@@ -499,9 +499,13 @@ int64_t bem_kernel_launches(void);
  * frequencies s_k of bem_freqs_radau2, mixing back, inverse DFT (real part).
  * g: device, real FP64, (N + 1) x 2 x n_cols x 3 (level, stage, column,
  * component) with g[n][i] = g(t_n + c_i dt); y: device, real FP64,
- * (N + 1) x 2 x n_rows x 3.  The context must hold exactly the 2 (N + 1)
- * frequencies of bem_freqs_radau2(N, dt) in that order (checked to 1e-9;
- * bem_freqs_set caps K at 256, so N <= 127).  Transforms and mixing in FP64,
+ * (N + 1) x 2 x n_rows x 3.  The context must hold the 2 (N + 1)
+ * frequencies of bem_freqs_radau2(N, dt) in that order, or only their
+ * first 2 (floor((N + 1) / 2) + 1) (the half set: real data makes the
+ * frequency indices l and N + 1 - l conjugate, so the inverse transform
+ * takes 2 Re of the pairs and the apply runs at about half the
+ * frequencies); checked to 1e-9; bem_freqs_set caps K at 256, so the full
+ * set allows N <= 127 and the half set N <= 253.  Transforms and mixing in FP64,
  * the frequency-domain vectors in the operator's precision.  Allocates its
  * device scratch (about 2L x (n_cols + 3 n_rows) x 3 complex values) and
  * releases it before returning; synchronises the stream.  g and y must not
@@ -512,8 +516,8 @@ bem_status bem_rkcq_apply(bem_op* op, int32_t N, double dt, const double* g, dou
  * the stage times, i.e. the same transforms as bem_rkcq_apply around a
  * K-batched BiCGstab solve C(s_k) f_k = e_k (bem_op_solve's iteration and
  * preconditioner) instead of the apply.  b, x: device, real FP64,
- * (N + 1) x 2 x n x 3, n = n_rows = n_cols.  iters, relres: host, 2 (N + 1)
- * entries each (per frequency).  Returns BEM_ERR_NOT_CONVERGED (after
+ * (N + 1) x 2 x n x 3, n = n_rows = n_cols.  iters, relres: host, one
+ * entry per frequency of the context (full or half set).  Returns BEM_ERR_NOT_CONVERGED (after
  * completing x) when a frequency reached max_iter; otherwise as
  * bem_rkcq_apply.  The Dirichlet problem of Sec. 2.3 (V t = (C + K) u at the
  * element midpoints) is bem_rkcq_apply of C + K followed by this call on V. */

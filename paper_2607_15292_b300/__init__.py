@@ -240,16 +240,20 @@ def freqs_bdf2(N: int, dt: float, K: int) -> np.ndarray:
     return out[0::2] + 1j * out[1::2]
 
 
-def freqs_radau2(N: int, dt: float):
+def freqs_radau2(N: int, dt: float, half: bool = False):
     """Frequencies of constant-step 2-stage Radau IIA RK-CQ (2 (N + 1),
-    complex128, k = 2 l + j) and the symbols (N + 1, 2, 2, 2) complex128:
-    [l, 0] = P_l, [l, 1] = P_l^-1 with Delta(zeta_l) = P_l diag(mu_l) P_l^-1
-    (computed by the library)."""
+    complex128, k = 2 l + j; with half=True the first 2 (floor((N + 1) / 2)
+    + 1) of them, the half set that real data needs) and the symbols
+    (N + 1, 2, 2, 2) complex128: [l, 0] = P_l, [l, 1] = P_l^-1 with
+    Delta(zeta_l) = P_l diag(mu_l) P_l^-1 (computed by the library)."""
     L = N + 1
     s = np.zeros(4 * L, dtype=np.float64)
     sym = np.zeros(16 * L, dtype=np.float64)
     _check(_lib.bem_freqs_radau2(N, dt, s.ctypes.data_as(_P(_dbl)), sym.ctypes.data_as(_P(_dbl))))
-    return s[0::2] + 1j * s[1::2], (sym[0::2] + 1j * sym[1::2]).reshape(L, 2, 2, 2)
+    freqs = s[0::2] + 1j * s[1::2]
+    if half:
+        freqs = freqs[:2 * (L // 2 + 1)]
+    return freqs, (sym[0::2] + 1j * sym[1::2]).reshape(L, 2, 2, 2)
 
 
 def rkcq_apply(op: "Operator", g, y, N: int, dt: float, stream=None):
@@ -267,8 +271,8 @@ def rkcq_solve(op: "Operator", b, x, N: int, dt: float, tol: float = 1e-8, max_i
     """x = RK-CQ (2-stage Radau IIA) of op^-1 applied to the stage data b
     (bem_rkcq_solve): b, x real float64 device tensors (N + 1, 2, n, 3) of
     a square operator; returns (iterations, relative residuals) per
-    frequency.  With check=False a frequency that did not converge is not
-    an error."""
+    frequency of the context (full or half set).  With check=False a
+    frequency that did not converge is not an error."""
     import torch
     n = op.tree.n_rows
     if n != op.tree.n_cols:
@@ -281,7 +285,7 @@ def rkcq_solve(op: "Operator", b, x, N: int, dt: float, tol: float = 1e-8, max_i
                              it.ctypes.data_as(_P(_i32)), rr.ctypes.data_as(_P(_dbl)), _stream_ptr(stream))
     if st != BEM_ERR_NOT_CONVERGED or check:
         _check(st, op.ctx.ptr)
-    return it, rr
+    return it[:op.K], rr[:op.K]
 
 
 def _cq_args(N, nvec, x, out):

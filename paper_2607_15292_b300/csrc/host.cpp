@@ -1128,10 +1128,11 @@ static bem_status rkcq_check(bem_op* op, int32_t N, double dt, const void* in, i
   if (N < 1 || !(dt > 0) || !in || !out) return bad("bad arguments");
   if (((uintptr_t)in & 7) || ((uintptr_t)out & 7)) return bad("the stage buffers must be 8-byte aligned");
   const int L = N + 1;
-  if (ctx->K != 2 * L) return bad("the context must hold the 2 (N + 1) Radau IIA frequencies of N, dt");
+  if (ctx->K != 2 * L && ctx->K != 2 * (L / 2 + 1))
+    return bad("the context must hold the 2 (N + 1) Radau IIA frequencies of N, dt or their first 2 (floor((N + 1) / 2) + 1)");
   std::vector<double> s(4 * (size_t)L);
   radau2_symbols(N, dt, s.data(), nullptr);
-  for (int k = 0; k < 2 * L; ++k) {
+  for (int k = 0; k < ctx->K; ++k) {
     const std::complex<double> want(s[2 * k], s[2 * k + 1]), have(ctx->s[2 * k], ctx->s[2 * k + 1]);
     if (std::abs(have - want) > 1e-9 * std::abs(want))
       return bad("the context's frequencies are not the Radau IIA RK-CQ frequencies of N, dt");

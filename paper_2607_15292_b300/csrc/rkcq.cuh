@@ -12,6 +12,12 @@
 //   y_n,i  = lam^-n / L Re sum_l w^nl z_l,i    (real data: the set is closed
 //                                              under conjugation)
 //
+// With real data z_(L-l) = conj z_l, so the operator is needed only for
+// l = 0 .. floor(L/2) (the half set, K = 2 (floor(L/2) + 1) frequencies,
+// a prefix of the full list k = 2l + j): y_n,i = lam^-n / L Re sum_(l in
+// half) c_l w^nl z_l,i with c_l = 1 for l = 0 and 2l = L, 2 otherwise.  The
+// context's frequency count selects the full or the half set.
+//
 // Stage data g (L x 2 x nvec) and results y (L x 2 x nvec) real FP64; the
 // frequency-domain vectors in the operator's complex type, the transforms
 // and the mixing in FP64.  The symbols P_l, P_l^-1 come from the host
@@ -63,19 +69,23 @@ __global__ void k_rk_unmix(int L, int64_t nvec, const double2* __restrict__ sym,
   }
 }
 
-// y_(n,i)[v] = lam^-n / L Re sum_l w^nl z_(l,i)[v]
-__global__ void k_rk_inv(int L, double lnlam, int64_t nvec, const double2* __restrict__ z, double* __restrict__ y) {
+// y_(n,i)[v] = lam^-n / L Re sum_(l < Lc) c_l w^nl z_(l,i)[v]; Lc = L (full
+// set, c_l = 1) or floor(L/2) + 1 (half set, c_l = half_weight(l, L))
+__global__ void k_rk_inv(int L, int Lc, double lnlam, int64_t nvec, const double2* __restrict__ z,
+                         double* __restrict__ y) {
   extern __shared__ double2 tab_ri[];
   const int n = blockIdx.y;
-  phase_table(tab_ri, L, n, L, 0.0, 1.0);
+  phase_table(tab_ri, Lc, n, L, 0.0, 1.0);
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v >= nvec) return;
+  const bool half = Lc != L;
   double acc0 = 0.0, acc1 = 0.0;
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; l < Lc; ++l) {
     const double2 t = tab_ri[l];
+    const double c = half ? half_weight(l, L) : 1.0;
     const double2 z0 = z[(int64_t)(2 * l) * nvec + v], z1 = z[(int64_t)(2 * l + 1) * nvec + v];
-    acc0 += t.x * z0.x - t.y * z0.y;
-    acc1 += t.x * z1.x - t.y * z1.y;
+    acc0 += c * (t.x * z0.x - t.y * z0.y);
+    acc1 += c * (t.x * z1.x - t.y * z1.y);
   }
   const double sc = exp(-lnlam * n) / L;
   y[(int64_t)(2 * n) * nvec + v] = sc * acc0;
@@ -90,11 +100,11 @@ template <typename S>
 static bem_status rkcq_run_t(bem_op* op, int N, double dt, const double* g, double* y, bool inverse_op, double tol,
                              int max_iter, int32_t* iters, double* relres, cudaStream_t st) {
   bem_ctx* ctx = op->tree->mesh->ctx;
-  const int L = N + 1, K = 2 * L;
+  const int L = N + 1, K = ctx->K, Lc = K / 2;   // full set (Lc = L) or half set (Lc = floor(L/2) + 1)
   const double lnlam = std::log(1e-10) / (2.0 * N);
   const int64_t nin = 3 * (inverse_op ? op->tree->n_rows : op->tree->n_cols);
   const int64_t nout = 3 * (inverse_op ? op->tree->n_cols : op->tree->n_rows);
-  std::vector<double> s(2 * K), sym_h(16 * (size_t)L);
+  std::vector<double> s(4 * (size_t)L), sym_h(16 * (size_t)L);
   radau2_symbols(N, dt, s.data(), sym_h.data());
   struct Bufs {
     std::vector<void*> p;
@@ -116,14 +126,14 @@ static bem_status rkcq_run_t(bem_op* op, int N, double dt, const double* g, doub
   }
   GCQ_CUDA(ctx, cudaMemcpyAsync(sym, sym_h.data(), sizeof(double) * sym_h.size(), cudaMemcpyHostToDevice, st));
   const size_t tab = sizeof(double2) * L;
-  k_rk_fwd<S><<<dim3((unsigned)((nin + 127) / 128), L), 128, tab, st>>>(L, lnlam, nin, sym, g, e);
+  k_rk_fwd<S><<<dim3((unsigned)((nin + 127) / 128), Lc), 128, tab, st>>>(L, lnlam, nin, sym, g, e);
   GCQ_CUDA(ctx, cudaGetLastError());
   count_launches(1);
   const bem_status r = inverse_op ? solve(op, 0, e, f, tol, max_iter, iters, relres, st)
                                   : apply(op, BEM_APPLY_BATCHED, 0, e, f, st);
   if (r != BEM_OK && r != BEM_ERR_NOT_CONVERGED) return r;
-  k_rk_unmix<S><<<dim3((unsigned)((nout + 127) / 128), L), 128, 0, st>>>(L, nout, sym, f, z);
-  k_rk_inv<<<dim3((unsigned)((nout + 127) / 128), L), 128, tab, st>>>(L, lnlam, nout, z, y);
+  k_rk_unmix<S><<<dim3((unsigned)((nout + 127) / 128), Lc), 128, 0, st>>>(L, nout, sym, f, z);
+  k_rk_inv<<<dim3((unsigned)((nout + 127) / 128), L), 128, sizeof(double2) * Lc, st>>>(L, Lc, lnlam, nout, z, y);
   GCQ_CUDA(ctx, cudaGetLastError());
   count_launches(2);
   GCQ_CUDA(ctx, cudaStreamSynchronize(st));

@@ -28,10 +28,10 @@ def case():
     return dict(xyz=xyz, tri=tri, g=gs, y=y.real)
 
 
-def _op(c, precision, eps, freqs=None):
+def _op(c, precision, eps, freqs=None, half=False):
     ctx = g.Context(eps=eps, precision=precision, leaf=12, eta=2.0)
     ctx.material(*syn.STEEL)
-    ctx.freqs(g.freqs_radau2(N, DT)[0] if freqs is None else freqs)
+    ctx.freqs(g.freqs_radau2(N, DT, half)[0] if freqs is None else freqs)
     mesh = ctx.mesh(c["xyz"], c["tri"])
     return ctx, mesh.tree(g.BEM_ROWS_NODES, g.BEM_SL).compress()
 
@@ -40,10 +40,14 @@ def _op(c, precision, eps, freqs=None):
 # lam^-N = 1e5 (lam = (1e-10)^(1/(2N))) at the last level: FP64 (compression
 # eps 1e-10) keeps 1e-7 of the largest value; MIXED carries complex64
 # frequency-domain vectors (2^-24 ~ 6e-8, times 1e5) and eps 1e-6 entries.
+@pytest.mark.parametrize("half", [False, True])
 @pytest.mark.parametrize("precision,eps,tol", [(0, 1e-10, 1e-7), (1, 1e-6, 6e-3)])
-def test_rkcq_apply_vs_oracle(case, record, precision, eps, tol):
+def test_rkcq_apply_vs_oracle(case, record, precision, eps, tol, half):
+    """Full set (2L frequencies) and half set (2 (floor(L/2) + 1)): the same
+    result, the half set through the conjugate pairs."""
     c = case
-    ctx, V = _op(c, precision, eps)
+    ctx, V = _op(c, precision, eps, half=half)
+    assert V.K == (2 * (N + 1) if not half else 2 * ((N + 1) // 2 + 1))
     gt = torch.tensor(c["g"], dtype=torch.float64, device="cuda")
     y = torch.full((N + 1, 2, V.tree.n_rows, 3), float("nan"), dtype=torch.float64, device="cuda")
     g.rkcq_apply(V, gt, y, N, DT)
@@ -65,5 +69,8 @@ def test_rkcq_refusals(case):
     ctx, V = _op(c, 0, 1e-8)
     with pytest.raises(g.BemError):                # another dt
         g.rkcq_apply(V, gt, y, N, 2 * DT)
+    ctx, V = _op(c, 0, 1e-8, freqs=g.freqs_radau2(N, DT)[0][:2 * ((N + 1) // 2)])
+    with pytest.raises(g.BemError):                # neither the full nor the half set
+        g.rkcq_apply(V, gt, y, N, DT)
     with pytest.raises(ValueError):                # stage data of the wrong shape
         g.rkcq_apply(V, gt[:, :1], y, N, DT)
