@@ -7,9 +7,11 @@ V t = (C + K) u by RK-CQ with 2-stage Radau IIA (bem_rkcq_apply of C + K,
 then bem_rkcq_solve of V), FP64, the convergence run on the half
 frequency set (conjugate pairs).  Parity with the oracle's dense RK-CQ
 pipeline on level 1; the error against the analytic traction on levels 1
-to 3 and its order (first order expected for the piecewise constant
-traction).  Level 4 (6,144 elements, K = 162) does not fit the device in
-FP64 with this storage and is not run here."""
+to 4 and its order (first order expected for the piecewise constant
+traction).  Level 4 (6,144 elements, half set K = 82) runs in MIXED: its
+FP64 operators (~140 GB with the half set) do not fit beside the
+compression's working storage; FP32 entry rounding (~1e-7) is far below
+its discretisation error (~2e-2 relative)."""
 import time
 
 import numpy as np
@@ -62,7 +64,7 @@ def _library(lev, u, eps, precision=0, half=False):
     b = torch.empty((N + 1, 2, len(tri), 3), dtype=torch.float64, device="cuda")
     g.rkcq_apply(A, ud, b, N, dt)
     t = torch.empty_like(b)
-    it, rr = g.rkcq_solve(V, b, t, N, dt, tol=1e-10, max_iter=1000)
+    it, rr = g.rkcq_solve(V, b, t, N, dt, tol=1e-10 if precision == 0 else 1e-7, max_iter=1000)
     t2 = time.perf_counter()
     st = [V.stats(), A.stats()]
     return t.cpu().numpy(), it, (t1 - t0, t2 - t1, [x.stored_bytes / 1e9 for x in st], [x.rank_mean for x in st])
@@ -89,9 +91,9 @@ def test_cube_dirichlet_level1_vs_oracle(record, half):
 
 def test_cube_dirichlet_convergence(record):
     errs = []
-    for lev in (1, 2, 3):
+    for lev in (1, 2, 3, 4):
         u, t = _analytic(lev)
-        th, it, (tc, ts, gb, rk) = _library(lev, u, LEVELS[lev][2], half=True)
+        th, it, (tc, ts, gb, rk) = _library(lev, u, LEVELS[lev][2], precision=0 if lev < 4 else 1, half=True)
         area = _geometry(lev)[4]
         e = _lmax(th, t, area)
         errs.append(e)
@@ -103,8 +105,8 @@ def test_cube_dirichlet_convergence(record):
         for name, a, b in (("stored_gb", *gb), ("rank_mean", *rk)):
             record(f"cube_l{lev}_{name}_V", a)
             record(f"cube_l{lev}_{name}_A", b)
-    eoc = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    eoc = [np.log2(errs[i] / errs[i + 1]) for i in range(3)]
     for i, e in enumerate(eoc):
         record(f"cube_eoc_{i + 1}{i + 2}", e)
-    assert errs[1] < errs[0] and errs[2] < errs[1], errs
+    assert all(errs[i + 1] < errs[i] for i in range(3)), errs
     assert min(eoc) > 1.0, (errs, eoc)
