@@ -439,6 +439,14 @@ bem_status bem_op_autotune(bem_op* op, void* stream, int32_t* bk);
  * block's faces stored low rank.  Blocks in bem_tree_export order. */
 bem_status bem_op_blocks(const bem_op* op, int64_t* info);
 
+/* The frequency of every face (host, n_blocks x K int32, [block][slot]):
+ * k_d, the frequency index at which Algorithm 1 took face d of the block
+ * (k_1 = 0; each index at most once per block), for d < the block's rank;
+ * -1 for the remaining slots and for dense and rank-0 blocks.  Blocks in
+ * bem_tree_export order.  Counting the indices over the blocks gives which
+ * frequencies the 3D-ACA keeps (Sec. 4.1, the frequencies used per block). */
+bem_status bem_op_pivot_freqs(const bem_op* op, int32_t* ks);
+
 /* Storage of every face (host, K x n_blocks int32, [slot][block]): the rank
  * k >= 0 of a face stored as U' W'^T by the face ACA + QR/SVD recompression
  * of Sec. 3.1 (Eq. (3.12); far blocks only, tolerance eps_aca, in MIXED

@@ -108,6 +108,7 @@ _SIGS = {
     "bem_face_compress": (_i32, [_vp, _vp, _i64, _i64, _dbl, _P(_i32), _vp, _vp]),
     "bem_kernel_launches": (_i64, []),
     "bem_debug_set": (_i32, [_i32, _i64]),
+    "bem_op_pivot_freqs": (_i32, [_vp, _P(_i32)]),
     "bem_freqs_radau2": (_i32, [_i32, _dbl, _P(_dbl), _P(_dbl)]),
     "bem_rkcq_apply": (_i32, [_vp, _i32, _dbl, _vp, _vp, _vp]),
     "bem_rkcq_solve": (_i32, [_vp, _i32, _dbl, _vp, _vp, _dbl, _i32, _P(_i32), _P(_dbl), _vp]),
@@ -641,6 +642,13 @@ class Operator:
         _check(_lib.bem_op_slot_stats(self._p, n.value, ms.ctypes.data_as(_P(_dbl)), en.ctypes.data_as(_P(_i64)),
                                       ctypes.byref(n)))
         return ms, en
+
+    def pivot_freqs(self) -> np.ndarray:
+        """(n_blocks, K) int32: frequency index k_d of face d of each block
+        (d < rank), -1 elsewhere and for dense and rank-0 blocks."""
+        out = np.zeros((self.tree.n_blocks, self.K), dtype=np.int32)
+        _check(_lib.bem_op_pivot_freqs(self._p, out.ctypes.data_as(_P(_i32))))
+        return out
 
     def face_ranks(self) -> np.ndarray:
         """(K, n_blocks) int32: rank of each low-rank face, -1 dense face, -2 no face."""

@@ -1241,6 +1241,19 @@ bem_status op_blocks(const bem_op* op, int64_t* info) {
   return BEM_OK;
 }
 
+bem_status op_pivot_freqs(const bem_op* op, int32_t* out) {
+  const OpData* d = op->d;
+  const size_t n = (size_t)d->n_blocks * d->K;
+  cudaError_t e = cudaMemcpy(out, d->d_ks, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(op->tree->mesh->ctx, e, "bem_op_pivot_freqs");
+  for (int64_t b = 0; b < d->n_blocks; ++b) {
+    const BlkDev& B = d->h_blk[b];
+    const int keep = B.status == ST_DONE ? B.rank : 0;
+    for (int p = keep; p < d->K; ++p) out[(size_t)b * d->K + p] = -1;
+  }
+  return BEM_OK;
+}
+
 bem_status op_face_ranks(const bem_op* op, int32_t* out) {
   const OpData* d = op->d;
   std::memcpy(out, d->h_frank.data(), sizeof(int32_t) * d->h_frank.size());

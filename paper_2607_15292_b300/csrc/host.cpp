@@ -1059,6 +1059,11 @@ bem_status bem_op_autotune(bem_op* op, void* stream, int32_t* bk) {
   return autotune(op, (cudaStream_t)stream, bk);
 }
 
+bem_status bem_op_pivot_freqs(const bem_op* op, int32_t* ks) {
+  if (!op || !ks) return BEM_ERR_ARG;
+  return op_pivot_freqs(op, ks);
+}
+
 bem_status bem_op_face_ranks(const bem_op* op, int32_t* ranks) {
   if (!op || !ranks) return BEM_ERR_ARG;
   return op_face_ranks(op, ranks);

@@ -179,6 +179,7 @@ bem_status apply(bem_op* op, int mode, int transpose, const void* X, void* Y, cu
 bem_status op_dense(bem_op* op, void* out, cudaStream_t st);
 bem_status op_stats(const bem_op* op, bem_op_stats* st);
 bem_status op_blocks(const bem_op* op, int64_t* info);
+bem_status op_pivot_freqs(const bem_op* op, int32_t* out);
 bem_status op_face_ranks(const bem_op* op, int32_t* ranks);
 bem_status solve(bem_op* op, int transpose, const void* B, void* X, double tol, int max_iter, int32_t* iters,
                  double* relres, cudaStream_t st);

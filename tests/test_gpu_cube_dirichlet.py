@@ -110,3 +110,42 @@ def test_cube_dirichlet_convergence(record):
         record(f"cube_eoc_{i + 1}{i + 2}", e)
     assert all(errs[i + 1] < errs[i] for i in range(3)), errs
     assert min(eoc) > 1.0, (errs, eoc)
+
+
+def test_cube_pivot_frequencies(record):
+    """The frequencies Algorithm 1 keeps (bem_op_pivot_freqs) on level 2 of
+    the cube, half set, both operators: valid (k_1 = 0, one index per face,
+    each at most once per block, in range, -1 beyond the rank and for
+    dense and rank-0 blocks); the share of blocks using each frequency and
+    the mean Re(s) of the kept frequencies against the set's are recorded
+    (the paper observes that small Re(s) is preferred)."""
+    xyz, tri, _, _, _ = _geometry(2)
+    dt, N, eps = LEVELS[2]
+    s = g.freqs_radau2(N, dt, True)[0]
+    ctx = g.Context(eps=eps, precision=0, leaf=16, eta=2.0)
+    ctx.material(*MAT)
+    ctx.freqs(s)
+    mesh = ctx.mesh(xyz, tri)
+    K = len(s)
+    for name, kern in (("V", g.BEM_SL), ("A", g.BEM_DL)):
+        op = mesh.tree(g.BEM_ROWS_CENTROIDS, kern).compress()
+        ks, info = op.pivot_freqs(), op.blocks()
+        aca = (info[:, 0] == 0) & (info[:, 1] > 0)
+        assert aca.any()
+        for b in np.nonzero(aca)[0]:
+            r = int(info[b, 1])
+            row = ks[b]
+            assert row[0] == 0 and row[0] == info[b, 2]
+            assert ((row[:r] >= 0) & (row[:r] < K)).all() and len(set(row[:r].tolist())) == r
+            assert (row[r:] == -1).all()
+        assert (ks[~aca] == -1).all()
+        counts = np.bincount(ks[ks >= 0], minlength=K)
+        share = counts / aca.sum()
+        top = np.argsort(-counts)[:4]
+        for i, k in enumerate(top):
+            record(f"pivot_{name}_top{i}_k", int(k))
+            record(f"pivot_{name}_top{i}_share", float(share[k]))
+            record(f"pivot_{name}_top{i}_re_s", float(s[k].real))
+        record(f"pivot_{name}_mean_re_s_kept", float((counts * s.real).sum() / counts.sum()))
+        record(f"pivot_{name}_mean_re_s_set", float(s.real.mean()))
+        record(f"pivot_{name}_unused", int((counts == 0).sum()))
