@@ -113,3 +113,31 @@ def test_cq_refuses_wrong_buffers():
     x = FakeCuda((N + 1, nvec), torch.complex128)
     with pytest.raises(ValueError, match="overlap"):
         g.cq_forward(N, nvec, x, x)
+
+
+def test_rkcq_refuses_wrong_buffers(mesh):
+    """RK-CQ apply and solve: stage buffers of the wrong dtype, shape or
+    level count, and a solve on a non-square operator, are refused before
+    the library is called; the C entry points refuse NULL handles."""
+    tree = mesh.tree(g.BEM_ROWS_NODES, g.BEM_SL)      # 8 node rows x 12 element columns
+    op = g.Operator.__new__(g.Operator)
+    op.tree, op.ctx, op.K, op._p = tree, mesh.ctx, mesh.ctx.K, None
+    mesh.ctx.device = 0
+    N, nr, nc = 3, tree.n_rows, tree.n_cols
+    f = torch.float64
+    with pytest.raises(ValueError, match="dtype"):
+        g.rkcq_apply(op, FakeCuda((N + 1, 2, nc, 3), torch.float32), FakeCuda((N + 1, 2, nr, 3), f), N, 1e-3)
+    with pytest.raises(ValueError, match="shape"):
+        g.rkcq_apply(op, FakeCuda((N + 1, 2, nr, 3), f), FakeCuda((N + 1, 2, nr, 3), f), N, 1e-3)   # rows in
+    with pytest.raises(ValueError, match="shape"):
+        g.rkcq_apply(op, FakeCuda((N, 2, nc, 3), f), FakeCuda((N + 1, 2, nr, 3), f), N, 1e-3)       # one level short
+    with pytest.raises(ValueError, match="shape"):
+        g.rkcq_apply(op, FakeCuda((N + 1, 1, nc, 3), f), FakeCuda((N + 1, 2, nr, 3), f), N, 1e-3)   # one stage
+    with pytest.raises(ValueError, match="square"):
+        g.rkcq_solve(op, FakeCuda((N + 1, 2, nr, 3), f), FakeCuda((N + 1, 2, nr, 3), f), N, 1e-3)
+    assert g._lib.bem_rkcq_apply(None, N, 1e-3, None, None, None) == g.BEM_ERR_ARG
+    it = np.zeros(8, dtype=np.int32)
+    rr = np.zeros(8)
+    assert g._lib.bem_rkcq_solve(None, N, 1e-3, None, None, 1e-8, 10, it.ctypes.data_as(g._P(g._i32)),
+                                 rr.ctypes.data_as(g._P(g._dbl)), None) == g.BEM_ERR_ARG
+    assert g._lib.bem_op_pivot_freqs(None, it.ctypes.data_as(g._P(g._i32))) == g.BEM_ERR_ARG

@@ -102,3 +102,34 @@ def test_frequencies_come_in_conjugate_pairs_and_lie_right():
     assert (s.real > 0).all()
     for v in s:                                # closed under conjugation (l <-> L - l)
         assert np.abs(s - np.conj(v)).min() < 1e-9 * np.abs(v)
+
+
+def test_matrix_valued_kernel_equals_radau_system_stepping():
+    """The operator case (what the library's RK-CQ computes with a BEM
+    operator): K(s) = B (s I + M)^-1 with M non-symmetric, positive real
+    eigenvalues, and B rectangular (the output has another trailing shape
+    than the input).  RK-CQ equals B times the Radau IIA stage values of
+    the system y' = -M y + g, y(0) = 0."""
+    rng = np.random.default_rng(5)
+    Q = rng.normal(size=(3, 3))
+    M = Q @ np.diag([0.5, 2.0, 7.0]) @ np.linalg.inv(Q)
+    Bm = rng.normal(size=(2, 3))
+    N = 30
+    dt = 1.0 / (N + 1)
+    t = _stage_times(N, dt)
+    g = np.stack([np.sin(3 * t), t ** 2, np.cos(t) - 1.0], axis=-1)          # (L, 2, 3)
+    y = rkcq.convolve(lambda k, s, x: Bm @ np.linalg.solve(s * np.eye(3) + M, x), g, N, dt, _lam(N))
+    # stage system per step: Y_i = y_n + dt sum_j a_ij (-M Y_j + g_j)
+    Y = np.zeros((N + 1, 2, 3))
+    yn = np.zeros(3)
+    big = np.eye(6) + dt * np.kron(A, M)
+    for n in range(N + 1):
+        rhs = np.concatenate([yn + dt * (A[0, 0] * g[n, 0] + A[0, 1] * g[n, 1]),
+                              yn + dt * (A[1, 0] * g[n, 0] + A[1, 1] * g[n, 1])])
+        st = np.linalg.solve(big, rhs).reshape(2, 3)
+        Y[n] = st
+        yn = st[1]
+    ref = Y @ Bm.T
+    assert y.shape == (N + 1, 2, 2)
+    assert np.abs(y.imag).max() < 1e-7
+    assert np.abs(y.real - ref).max() < 2e-8 * np.abs(ref).max(), np.abs(y.real - ref).max()
